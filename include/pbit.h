@@ -1,0 +1,208 @@
+/*
+ * pbit.h -- C ABI of the GB300 (sm_103a) graph-coloured parallel p-bit annealer.
+ *
+ * Method: "Probabilistic Computing Optimization of Complex Spin-Glass
+ * Topologies" (arXiv 2510.23419).  For every colour class (update group,
+ * Sec. 1.2.2) in turn, every p-bit i of the class takes the local field
+ * F_i = sum_j J_ij m_j + h_i (Eq. 3) and sets m_i = +1 with probability
+ * 1/2 + tanh(beta F_i)/2 (Eq. 2, bipolar form), under a beta schedule
+ * (classical annealing, Sec. 1.3.1), for many independent replicas.
+ *
+ * Conventions that hold for every call:
+ *  - Energy (Eq. 1 with the sign that Eqs. 2-3 sample):
+ *      E(m) = - sum_{edges (i,j)} J_ij m_i m_j - sum_i h_i m_i.
+ *    A coupling J > 0 favours aligned spins.  (The paper writes
+ *    H = +sum J s s; its J is the negative of the J here.)
+ *  - Decision rule: one uint32 word r per update;
+ *      T = min(floor((0.5 + 0.5*tanh(beta*F)) * 2^32), 2^32 - 1) in FP64,
+ *      m = +1 iff r < T.
+ *    For +-1 couplings with integer fields T comes from a table built in FP64
+ *    on the host, so results are bit-exact and reproducible.  For FP32
+ *    couplings the kernels evaluate T in FP32 (see the per-call notes).
+ *  - Random words: Philox4x32-10 (Salmon et al., SC'11), key = (seed lo,
+ *    seed hi), counter = (k, s, r >> 2, (tag << 24) | c), word r & 3, where k
+ *    is the rank of spin i inside its colour class c, s the sweep, r the
+ *    replica; tag 0 = decisions, 1 = initial state (s = 0), 2 = instance
+ *    generation.
+ *  - Initial state: m_i = +1 iff the tag-1 word < 2^31.
+ *  - One sweep updates colour 0, then colour 1.  After every sweep the energy
+ *    is evaluated; the best (running lowest, Fig. 1A) state starts as the
+ *    initial state with best sweep -1 and is replaced when E < best strictly.
+ *  - Host arrays are read during the call and not kept.  Device memory is
+ *    owned by the handles.  Output buffers are caller-owned host memory with
+ *    an explicit size; a size that is too small gives PB_EINVAL.
+ *  - Streams cross as void* (a cudaStream_t; NULL = the legacy default stream).
+ *  - No C++ exception crosses this interface.  Every failing call returns a
+ *    status and leaves a message for pb_last_error() (thread-local).
+ *  - Lattice site index: i = x + L*(y + L*z); EA colour = (x + y + z) & 1
+ *    (needs an even L).  Biclique: left spins 0..n-1 (colour 0), right spins
+ *    n..2n-1 (colour 1).
+ */
+#ifndef PBIT_H
+#define PBIT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum pb_status {
+    PB_OK = 0,
+    PB_EINVAL = 1,        /* bad argument: null pointer, size, type or value out of range */
+    PB_ECOLOUR = 2,       /* colouring has an edge inside a class, or the checkerboard needs an even L */
+    PB_ENOMEM = 3,        /* host or device allocation failed */
+    PB_EDEVICE = 4,       /* a CUDA call failed; pb_last_error() has the CUDA message */
+    PB_ETIMEOUT = 5,      /* a wait ran out of time */
+    PB_EBUSY = 6,         /* pb_query: the run has not finished */
+    PB_EUNSUPPORTED = 7   /* valid request outside what this library implements */
+} pb_status;
+
+typedef enum pb_topology { PB_TOPO_EA3D = 0, PB_TOPO_BICLIQUE = 1 } pb_topology;
+
+/* Coupling storage of an instance.
+ * PB_J_PM1_I8: int8 couplings in {-1, +1}; h (if any) int8, |h| <= 64.  Fields are
+ *              integers and decisions use the FP64-built threshold table (bit-exact).
+ * PB_J_F32:    float couplings and float h; fields in FP32 (EA) or tensor-core
+ *              split-BF16 with FP32 accumulation (biclique). */
+typedef enum pb_jtype { PB_J_PM1_I8 = 0, PB_J_F32 = 1 } pb_jtype;
+
+/* Coupling laws of the seeded generators (Sec. 2 random cubes, Sec. 3 random
+ * bicliques with couplings from [-1, 1]). */
+typedef enum pb_dist { PB_DIST_PM1 = 0, PB_DIST_GAUSS = 1, PB_DIST_UNIF = 2 } pb_dist;
+
+typedef struct pb_instance_desc {
+    int32_t topo;          /* pb_topology */
+    int32_t L;             /* EA: side of the periodic cube (even, 2..64); N = L^3 */
+    int32_t n;             /* biclique: spins per side (1..16384); N = 2n */
+    int32_t jtype;         /* pb_jtype */
+    const void* J;         /* host.  EA: [3][N], bond (d, i) joins site i to its +x (d=0), +y (1), +z (2)
+                              neighbour.  Biclique: [n][n] row-major, J[i][j] joins left i to right j.
+                              int8 for PB_J_PM1_I8, float for PB_J_F32 */
+    const void* h;         /* host [N], int8 (PM1) or float (F32); NULL = no field */
+    const int32_t* colour; /* host [N]; NULL = canonical colouring.  A given colouring is
+                              checked: an internal edge gives PB_ECOLOUR; a proper colouring
+                              other than the canonical one gives PB_EUNSUPPORTED */
+} pb_instance_desc;
+
+typedef enum pb_sched_kind { PB_SCHED_LINEAR = 0, PB_SCHED_GEOMETRIC = 1, PB_SCHED_EXPLICIT = 2 } pb_sched_kind;
+
+/* Classical annealing schedule (Sec. 1.3.1; Algorithm 1's linear beta step).
+ * Level l = floor(s / d) of Lv = ceil(S / d) levels, end points included:
+ *   linear    beta0 + (beta1 - beta0) * l / (Lv - 1)
+ *   geometric beta0 * (beta1 / beta0)^(l / (Lv - 1))      (beta0, beta1 > 0)
+ *   explicit  betas[s], one per sweep (host array of n_sweeps values)
+ * A single level uses beta0.  All betas must be finite and >= 0. */
+typedef struct pb_schedule {
+    int32_t kind;          /* pb_sched_kind */
+    int32_t n_sweeps;      /* S >= 0 */
+    int32_t step_duration; /* d >= 1 */
+    int32_t reserved;      /* 0 */
+    double beta0;
+    double beta1;
+    const double* betas;   /* explicit only */
+} pb_schedule;
+
+/* How a run executes. */
+typedef enum pb_form {
+    PB_FORM_AUTO = 0,      /* resident form where it fits, else plain (EA); tensor form (biclique) */
+    PB_FORM_PLAIN = 1,     /* EA: spins in global memory, one launch per colour class and sweep */
+    PB_FORM_RESIDENT = 2,  /* EA: one persistent launch, each replica block's lattice kept in shared memory */
+    PB_FORM_CUDACORE = 3,  /* biclique: CUDA-core field (int8 dp4a for +-1, FP32 FMA for F32) */
+    PB_FORM_TENSOR = 4     /* biclique: tcgen05 tensor-core field */
+} pb_form;
+
+typedef struct pb_anneal_opts {
+    int32_t form;          /* pb_form */
+    int32_t flags;         /* 0 */
+    double target_energy;  /* record, per replica, the first sweep whose energy is <= target;
+                              NaN disables the record */
+} pb_anneal_opts;
+
+typedef struct pb_instance pb_instance;  /* opaque: device copy of one instance */
+typedef struct pb_run pb_run;            /* opaque: one anneal of R replicas of one instance */
+
+/* Library version string and the text of a status. */
+const char* pb_version(void);
+const char* pb_status_string(pb_status status);
+/* Message of the last failing call on this thread ("" if none). */
+const char* pb_last_error(void);
+
+/* Seeded instance generators (tag-2 Philox stream; Sec. 2 and Sec. 3).
+ * Coupling e (EA: e = d*N + i; biclique: e = i*n + j) is
+ *   PM1:   +1 iff word(e >> 2, 0, 0, 2 << 24)[e & 3] < 2^31, else -1   (int8 output)
+ *   GAUSS: Box-Muller on words 0, 1 of (e, 1, 0, 2 << 24), u = (w + 0.5) / 2^32,
+ *          z = sqrt(-2 ln u0) cos(2 pi u1) in FP64, rounded to float   (float output)
+ *   UNIF:  2u - 1 with u = (word(e >> 2, 2, 0, 2 << 24)[e & 3] + 0.5) / 2^32, rounded to float
+ * J_out is caller-owned host memory of out_bytes bytes (EA: 3 L^3 elements,
+ * biclique: n^2 elements).  Errors: PB_EINVAL on a bad size or law. */
+pb_status pb_generate_ea(int32_t L, int32_t dist, uint64_t seed, void* J_out, int64_t out_bytes);
+pb_status pb_generate_biclique(int32_t n, int32_t dist, uint64_t seed, void* J_out, int64_t out_bytes);
+
+/* Copy an instance to the device (Eq. 1 problem statement; the colouring of
+ * Sec. 1.2.2 is validated).  Host arrays are copied before the call returns;
+ * the work is ordered on `stream`.  Errors: PB_EINVAL (shape, type, +-1 check,
+ * |h| range), PB_ECOLOUR (odd L, improper colouring), PB_EUNSUPPORTED, PB_ENOMEM,
+ * PB_EDEVICE. */
+pb_status pb_create_instance(const pb_instance_desc* desc, void* stream, pb_instance** out);
+void pb_instance_destroy(pb_instance* inst);
+/* Number of spins N of an instance (EA L^3, biclique 2n), or -1. */
+int64_t pb_instance_spins(const pb_instance* inst);
+
+/* Start an anneal of `replicas` independent replicas (Sec. 1.3.1) on `stream`.
+ * Asynchronous: returns once the work is queued.  `opts` may be NULL (AUTO form,
+ * no target).  The instance must outlive the run.  Errors: PB_EINVAL (schedule,
+ * replicas < 1), PB_EUNSUPPORTED (form not available for the instance),
+ * PB_ENOMEM, PB_EDEVICE. */
+pb_status pb_anneal(pb_instance* inst, const pb_schedule* sched, int32_t replicas, uint64_t seed,
+                    void* stream, pb_run** out);
+pb_status pb_anneal_ex(pb_instance* inst, const pb_schedule* sched, int32_t replicas, uint64_t seed,
+                       const pb_anneal_opts* opts, void* stream, pb_run** out);
+
+/* Start `count` anneals that share ONE persistent launch on `stream` (EA
+ * resident form; every instance must be EA).  Replica blocks of all jobs are
+ * scheduled longest-first over all SMs.  Arrays have `count` entries; `opts`
+ * may be NULL; outs[k] receives the run of job k.  Results are identical to
+ * running each job alone.  Errors as pb_anneal; on error no run is returned. */
+pb_status pb_anneal_batch(int32_t count, pb_instance* const* insts, const pb_schedule* scheds,
+                          const int32_t* replicas, const uint64_t* seeds, const pb_anneal_opts* opts,
+                          void* stream, pb_run** outs);
+
+/* Wait for a run (host side): PB_OK when finished, PB_ETIMEOUT after timeout_ms
+ * (< 0 = no limit), PB_EDEVICE if a kernel of the run failed. */
+pb_status pb_wait(pb_run* run, int32_t timeout_ms);
+/* PB_OK if finished, PB_EBUSY if not, PB_EDEVICE on a device error. */
+pb_status pb_query(pb_run* run);
+
+/* Results (each waits for the run).  Energies are recomputed from the returned
+ * states on the device: exactly in int64 for PM1 instances, in FP64 for F32
+ * instances.  Arrays have `replicas` entries; any pointer may be NULL.
+ * best_sweep is -1 when the initial state was never beaten. */
+pb_status pb_energy(pb_run* run, double* final_E, double* best_E, int32_t* best_sweep);
+/* Best / final states, [replicas][N] int8 in {-1, +1}, out_bytes >= replicas * N. */
+pb_status pb_best_states(pb_run* run, int8_t* out, int64_t out_bytes);
+pb_status pb_final_states(pb_run* run, int8_t* out, int64_t out_bytes);
+/* First sweep whose energy reached opts->target_energy, per replica (-1 = never,
+ * or no target was set).  For F32 instances the comparison uses the kernel's
+ * FP32 running energy. */
+pb_status pb_target_sweeps(pb_run* run, int32_t* first_sweep);
+/* Device time of the run's kernels in milliseconds (CUDA events around the launches). */
+pb_status pb_run_device_ms(pb_run* run, float* ms);
+/* Device time of the run's annealing kernels alone (without set-up and readout), from
+ * CUDA events recorded on the run's stream around them; for a batch, the persistent
+ * launch shared by all jobs. */
+pb_status pb_run_kernel_ms(pb_run* run, float* ms);
+void pb_run_destroy(pb_run* run);
+
+/* Local fields F_i = sum_j J_ij m_j + h_i (Eq. 3) of given states, computed on the
+ * device with the same arithmetic the anneal kernels use for this instance
+ * (integer for PM1; FP32 for EA F32).  states: host [R][N] int8 in {-1, +1};
+ * fields_out: host [R][N] float, out_bytes >= 4 R N.  Synchronous. */
+pb_status pb_fields(pb_instance* inst, const int8_t* states, int32_t R, float* fields_out, int64_t out_bytes,
+                    void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PBIT_H */

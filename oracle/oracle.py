@@ -77,7 +77,7 @@ def _load():
             lib.orc_threshold.argtypes = [f64, f64]
             lib.orc_threshold.restype = u32
             lib.orc_fields.argtypes = [i32, i64, P, P, P, P, P, P]
-            lib.orc_anneal.argtypes = [i32, i64, P, P, P, P, P, i32, P, i32, i32, u64,
+            lib.orc_anneal.argtypes = [i32, i64, P, P, P, P, P, i32, P, i32, i32, i32, u64,
                                        P, P, P, P, P, P, P]
             lib.orc_anneal.restype = ctypes.c_int
             _lib = lib
@@ -208,8 +208,8 @@ def threshold(beta: float, F: float) -> int:
 
 # --------------------------------------------------------------- anneal
 def anneal(eu, ev, J, h, colour, betas, R: int, seed: int, n_colours: int | None = None,
-           trace: bool = False) -> dict:
-    """Classical annealing of R replicas (update groups in colour order); see the C file for the rules."""
+           trace: bool = False, r_first: int = 0) -> dict:
+    """Classical annealing of replicas r_first..r_first+R-1 (update groups in colour order); see the C file."""
     colour = np.ascontiguousarray(colour, np.int32)
     N = colour.size
     eu = np.ascontiguousarray(eu, np.int32)
@@ -227,8 +227,8 @@ def anneal(eu, ev, J, h, colour, betas, R: int, seed: int, n_colours: int | None
     )
     tr = np.empty((R, S), np.float64) if trace else None
     err = ctypes.c_double(0.0)
-    rc = _load().orc_anneal(N, eu.size, _p(eu), _p(ev), _p(J), _p(hh), _p(colour), n_colours, _p(betas), S, R,
-                            seed, _p(out["final_E"]), _p(out["best_E"]), _p(out["best_sweep"]),
+    rc = _load().orc_anneal(N, eu.size, _p(eu), _p(ev), _p(J), _p(hh), _p(colour), n_colours, _p(betas), S, r_first,
+                            R, seed, _p(out["final_E"]), _p(out["best_E"]), _p(out["best_sweep"]),
                             _p(out["final_state"]), _p(out["best_state"]), _p(tr), ctypes.byref(err))
     if rc == -2:
         raise ValueError("colouring has an edge inside a colour class")

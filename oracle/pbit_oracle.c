@@ -278,18 +278,19 @@ void orc_fields(int32_t N, int64_t n_edges, const int32_t* eu, const int32_t* ev
 }
 
 /* ------------------------------------------------------------------------ */
-/* Classical annealing of R independent replicas with update groups.         */
-/* Returns 0 on success, -1 on bad arguments, -2 if the colouring has an     */
+/* Classical annealing of replicas r_first .. r_first+R-1 (independent; a    */
+/* replica's trajectory depends only on its own index), with update groups.  */
+/* Outputs are indexed 0..R-1.  Returns 0 on success, -1 on bad arguments, -2 if the colouring has an     */
 /* internal edge, -3 on allocation failure.                                  */
 /*   trace_E   optional [R][S] energy after each sweep                       */
 /*   max_incr_err optional: largest |incremental E - recomputed E| seen      */
 /* ------------------------------------------------------------------------ */
 int orc_anneal(int32_t N, int64_t n_edges, const int32_t* eu, const int32_t* ev, const double* J,
                const double* h, const int32_t* colour, int32_t n_colours, const double* betas, int32_t S,
-               int32_t R, uint64_t seed, double* final_E, double* best_E, int32_t* best_sweep,
+               int32_t r_first, int32_t R, uint64_t seed, double* final_E, double* best_E, int32_t* best_sweep,
                int8_t* final_state, int8_t* best_state, double* trace_E, double* max_incr_err)
 {
-    if (N < 1 || R < 0 || S < 0 || n_colours < 1 || n_colours > 255) return -1;
+    if (N < 1 || R < 0 || r_first < 0 || S < 0 || n_colours < 1 || n_colours > 255) return -1;
     for (int32_t i = 0; i < N; ++i)
         if (colour[i] < 0 || colour[i] >= n_colours) return -1;
     if (orc_count_monochrome(n_edges, eu, ev, colour) != 0) return -2;
@@ -324,8 +325,9 @@ int orc_anneal(int32_t N, int64_t n_edges, const int32_t* eu, const int32_t* ev,
 
     double worst = 0.0;
     for (int32_t r = 0; r < R; ++r) {
-        const uint32_t rq = (uint32_t)(r >> 2);
-        const int rw = r & 3;
+        const int32_t rg = r_first + r; /* global replica index */
+        const uint32_t rq = (uint32_t)(rg >> 2);
+        const int rw = rg & 3;
         /* initial state: tag 1, sweep 0 */
         for (int32_t i = 0; i < N; ++i) {
             uint32_t w = orc_rand_word(seed, rank[i], 0u, rq, (ORC_TAG_INIT << 24) | (uint32_t)colour[i], rw);

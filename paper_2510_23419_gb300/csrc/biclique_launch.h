@@ -1,0 +1,67 @@
+// biclique_launch.h -- host/device interface of the complete-bipartite
+// (K_{n,n}) p-bit kernels (arXiv 2510.23419, Sec. 3).
+#pragma once
+
+#include "pb_common.h"
+
+namespace pb {
+
+// Spin encodings in global memory, one per coupling type, so that the spin
+// matrix is directly the B operand of the tensor-core field:
+//   PM1: FP8 e4m3, +1 = 0x38, -1 = 0xB8      (1 byte)
+//   F32: BF16,     +1 = 0x3F80, -1 = 0xBF80  (2 bytes)
+constexpr uint8_t kE4m3Plus = 0x38, kE4m3Minus = 0xB8;
+constexpr uint16_t kBf16Plus = 0x3F80, kBf16Minus = 0xBF80;
+
+struct BqDevice {
+    int32_t n, jtype, has_h, hmax;
+    const float* Jf;        // [n][n] couplings as float (PM1: +-1.0)
+    const float* Jft;       // [n][n] transpose
+    const int8_t* h8;       // PM1 [2n] or null
+    const float* hf;        // F32 [2n] (zeros when no field)
+    const void* Jraw;       // [n][n] int8 or float, for the exact energy
+    const void* hraw;       // [2n] int8 or float, or null
+    // tensor-core operands, [npad][npad] row-major, zero padded
+    int32_t npad;           // n rounded up to the tensor tile (0 if not built)
+    const uint8_t* Jq;      // e4m3 J
+    const uint8_t* Jqt;     // e4m3 J^T
+    const uint16_t* Jhi;    // bf16 high part of J
+    const uint16_t* Jlo;    // bf16 residual J - hi
+    const uint16_t* Jthi;
+    const uint16_t* Jtlo;
+};
+
+struct BqJob {
+    BqDevice inst;
+    uint32_t key0, key1;
+    int32_t S, step, nF, fmin;
+    const uint32_t* table;  // PM1 [levels][nF]
+    const float* betaf;     // F32 [levels]
+    int32_t R, Rpad;        // replicas, padded to the replica tile
+    int32_t ld;             // leading dimension of a spin row (>= n, padded for the tensor form)
+    void* spins[2];         // [Rpad][ld] live state of side A (colour 0) and side B (colour 1)
+    void* best[2];          // [Rpad][ld] best states
+    int32_t nblk;           // row blocks of the field kernels
+    void* part;             // [2][nblk][Rpad] energy partials (int32 PM1 / float F32): [0] -h.a, [1] -b.F_B
+    int32_t* E_best_i;
+    float* E_best_f;
+    int32_t* best_sweep;
+    int32_t* hit_sweep;
+    int32_t has_target, target_i;
+    float target_f;
+};
+
+constexpr int kBqTileRows = 64;   // CUDA-core field kernel: rows (spins of the updated side) per block
+constexpr int kBqTileReps = 64;   // replicas per block
+
+cudaError_t bq_launch_init(const BqJob& job, cudaStream_t st);
+// Field + decision of one side (side 0 = A uses J, side 1 = B uses J^T).
+// decide = 0: no update, only the energy partials of the current state.
+// fields_out != null: write F[r][side*n + i] (row stride 2n) and change nothing.
+cudaError_t bq_launch_cc_half(const BqJob& job, int side, int s, int decide, float* fields_out, cudaStream_t st);
+cudaError_t bq_launch_sweep_end(const BqJob& job, int s, int init, cudaStream_t st);
+cudaError_t bq_launch_readout(const BqJob& job, int which /*0 final, 1 best*/, int8_t* out_pm, double* out_E,
+                              cudaStream_t st);
+cudaError_t bq_launch_encode(const BqJob& job, const int8_t* d_states, cudaStream_t st);
+
+}  // namespace pb

@@ -1,0 +1,80 @@
+// ea_kernels.cuh -- device-side pieces of the EA (3D Edwards-Anderson,
+// periodic L^3 cube) p-bit update, shared by the plain and resident forms.
+//
+// Spin words: 4 replicas per uint32, one byte each, byte value 0 <=> m = +1,
+// 1 <=> m = -1.  Sites of colour c are addressed by their class rank
+// k = i >> 1; a class array is [half][WT] words (w fastest).
+//
+// Field of a +-1 site (Eq. 3): bit b of the 6-bit "pattern" of a replica is
+// (neighbour-b spin bit) XOR (bond-b sign bit); it is set exactly when the
+// term J_b m_b is negative, so F = 6 - 2 popcount(pattern) (+ h).  The
+// pattern of 4 replicas is built at once, shifted to bits 2..7 of each byte,
+// so a byte is directly the byte offset of the threshold in a 64-entry
+// table of uint32 (Eq. 2 decision).
+#pragma once
+
+#include "pb_common.h"
+
+namespace pb {
+
+// Pattern word of 4 replicas: bits (2+b) of every byte <- neighbour b's spin
+// byte (0/1), then xor with the site's bond-sign byte broadcast to 4 bytes.
+__device__ __forceinline__ uint32_t ea_pattern(uint32_t n0, uint32_t n1, uint32_t n2, uint32_t n3, uint32_t n4,
+                                               uint32_t n5, uint32_t jb)
+{
+    uint32_t p = (n0 << 2) | (n1 << 3) | (n2 << 4) | (n3 << 5) | (n4 << 6) | (n5 << 7);
+    return p ^ (jb * 0x01010101u);
+}
+
+// Per-byte count of set bits among bits 2..7 (6-bit fields), SWAR.
+__device__ __forceinline__ uint32_t ea_popc6_bytes(uint32_t y)
+{
+    uint32_t v = y >> 2;                       // bits 0..5 of each byte (bits 0,1 of y are zero)
+    v = v - ((v >> 1) & 0x15151515u);          // 2-bit counts in pairs (0,1), (2,3), (4,5)
+    v = (v & 0x33333333u) + ((v >> 2) & 0x33333333u);
+    v = (v + (v >> 4)) & 0x0F0F0F0Fu;
+    return v;
+}
+
+// Decision of one replica: new spin bit (1 <=> m = -1) is 1 unless r < T.
+__device__ __forceinline__ uint32_t decide_bit(uint32_t r, uint32_t T) { return r >= T ? 1u : 0u; }
+
+// FP32 threshold of the F32 path: floor(2^32 / (1 + e^{-2 beta F})), which is
+// 2^32 (1/2 + tanh(beta F)/2); the float->uint conversion saturates at 2^32-1.
+__device__ __forceinline__ uint32_t thr_f32(float F, float beta)
+{
+    const float e = __expf(-2.0f * beta * F);
+    const float P = __fdividef(1.0f, 1.0f + e);
+    return __float2uint_rz(P * 4294967296.0f);
+}
+
+// FP32 local field of replica b (byte b of the neighbour words), Eq. 3, in the
+// fixed order h + (+x) + (-x) + (+y) + (-y) + (+z) + (-z).
+__device__ __forceinline__ float ea_field_f32(const float (&jv)[6], float h, const uint32_t (&n)[6], int b)
+{
+    float F = h;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const bool neg = (n[k] >> (8 * b)) & 1u;
+        F += neg ? -jv[k] : jv[k];
+    }
+    return F;
+}
+
+// Neighbour rank offsets (in sites, inside the other colour's class array) of
+// the sites of one column: fixed x = 2q + px and y, z running.
+struct EaColumn {
+    int dxp, dxm, dyp, dym;  // +x, -x, +y, -y offsets relative to the site's own rank
+};
+
+__device__ __forceinline__ EaColumn ea_column(int L, int h2, int q, int y, int px)
+{
+    EaColumn o;
+    o.dxp = px ? ((q + 1 == h2) ? -(h2 - 1) : 1) : 0;
+    o.dxm = px ? 0 : ((q == 0) ? (h2 - 1) : -1);
+    o.dyp = (y + 1 == L) ? -(L - 1) * h2 : h2;
+    o.dym = (y == 0) ? (L - 1) * h2 : -h2;
+    return o;
+}
+
+}  // namespace pb

@@ -1,0 +1,78 @@
+// ea_launch.h -- host/device interface of the EA (periodic L^3 cube) kernels.
+#pragma once
+
+#include "pb_common.h"
+
+namespace pb {
+
+// One anneal job as the kernels see it (plain form: one tile with WT = R/4
+// rounded up; resident form: tiles of 4*WT replicas).  State buffers use the
+// tile layout: word ((tile*2 + c)*half + k)*WT + w holds replicas
+// tile*4*WT + 4w + (0..3) of the site of colour c and class rank k.
+struct EaJob {
+    EaDevice inst;
+    uint32_t key0, key1;      // Philox key = seed
+    int32_t S;                // sweeps
+    int32_t step;             // sweeps per beta level (1 for explicit schedules)
+    int32_t nF;               // PM1: threshold table width (F_max - F_min + 1)
+    int32_t fmin;             // PM1: F_min
+    const uint32_t* table;    // PM1: [levels][nF] thresholds
+    const float* betaf;       // F32: [levels] beta as float
+    int32_t R;                // replicas requested
+    int32_t WT;               // words (4 replicas each) per site in one tile
+    int32_t n_tiles;
+    int32_t has_target;
+    int32_t target_i;         // PM1 target energy (integer)
+    float target_f;           // F32 target energy
+    uint32_t* best_words;     // tile layout
+    uint32_t* final_words;    // tile layout (plain form: the live state)
+    int32_t* E_best_i;        // PM1 running-best energy  [n_tiles*4*WT]
+    float* E_best_f;          // F32 running-best energy
+    int32_t* best_sweep;      // [n_tiles*4*WT]
+    int32_t* hit_sweep;       // [n_tiles*4*WT]
+};
+
+struct EaWork {
+    int32_t job;
+    int32_t tile;
+};
+
+// Shared memory of one resident tile, in bytes.
+__host__ __device__ inline size_t ea_resident_smem(int L, int WT, int jtype, int has_h, int nF)
+{
+    const size_t N = (size_t)L * L * L;
+    size_t b = N * (size_t)WT * 4;                       // spins [2][half][WT]
+    if (jtype == PB_J_PM1_I8) {
+        b += (N + 15) / 16 * 16;                         // bond-sign bytes [2][half]
+        if (has_h) b += (N + 15) / 16 * 16;              // h bytes
+    }
+    const int tabw = (jtype == PB_J_PM1_I8) ? (has_h ? nF : 64) : 0;
+    b += (size_t)2 * ((tabw + 3) / 4 * 4) * 4;           // double-buffered threshold row
+    b += (size_t)32 * 4 * WT * 4;                        // per-warp energy partials
+    if (jtype == PB_J_PM1_I8 && has_h) b += (size_t)32 * 4 * WT * 4;  // per-warp h.m partials
+    b += (size_t)4 * WT;                                 // improved flags
+    return (b + 127) / 128 * 128;
+}
+
+constexpr int kResidentThreads = 1024;
+constexpr int kResidentMaxWT = 32;
+constexpr size_t kResidentSmemLimit = 227 * 1024;
+
+// Largest power-of-two WT <= min(32, cap) such that a class of the cube fits
+// the 1024 threads (h2*L*WT <= 1024) and the tile fits shared memory; 0 if none.
+int ea_resident_pick_wt(int L, int jtype, int has_h, int nF, int cap_words);
+
+// Opt the persistent kernel into `smem` bytes of dynamic shared memory (outside any capture).
+cudaError_t ea_resident_set_smem(size_t smem);
+cudaError_t ea_launch_resident(const EaJob* d_jobs, const EaWork* d_work, int n_work, int* d_counter, size_t smem,
+                               int grid, cudaStream_t st);
+cudaError_t ea_launch_plain_init(const EaJob& job, cudaStream_t st);
+cudaError_t ea_launch_plain_sweep(const EaJob& job, int s, cudaStream_t st);
+cudaError_t ea_launch_plain_energy(const EaJob& job, int s, bool init, cudaStream_t st);
+// Tile layout -> [R][N] int8 +-1, and energies recomputed from those states
+// (int64 for PM1, FP64 for F32).
+cudaError_t ea_launch_readout(const EaJob& job, const uint32_t* words, int8_t* out_pm, double* out_E,
+                              cudaStream_t st);
+cudaError_t ea_launch_fields(const EaDevice& inst, const int8_t* d_states, int R, float* d_out, cudaStream_t st);
+
+}  // namespace pb

@@ -1,0 +1,108 @@
+// pb_handles.h -- internal definitions of the opaque handles of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <memory>
+#include <vector>
+
+#include "biclique_launch.h"
+#include "ea_launch.h"
+#include "pb_common.h"
+
+namespace pb {
+
+// ---------------------------------------------------------------------------
+// Device buffer owned by a handle.
+// ---------------------------------------------------------------------------
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    ~DevBuf()
+    {
+        if (p) cudaFree(p);
+    }
+    cudaError_t alloc(size_t n)
+    {
+        bytes = n;
+        return cudaMalloc(&p, n ? n : 16);
+    }
+    template <typename T>
+    T* as() const
+    {
+        return static_cast<T*>(p);
+    }
+};
+
+#define PB_ALLOC(buf, n)                                                  \
+    do {                                                                  \
+        cudaError_t pb_e_ = (buf).alloc(n);                               \
+        if (pb_e_ != cudaSuccess) return ::pb::cuda_fail(pb_e_, "cudaMalloc"); \
+    } while (0)
+
+}  // namespace pb
+
+struct pb_instance {
+    int topo = 0, jtype = 0, L = 0, n = 0;
+    int64_t N = 0;
+    int has_h = 0, hmax = 0, maxdeg = 0;
+    // EA
+    pb::DevBuf jbits, h8, j6, hf, J3, hraw;
+    pb::EaDevice ea{};
+    // biclique
+    pb::BqDevice bq{};
+    pb::DevBuf bq_bufs[8];
+};
+
+namespace pb {
+struct BatchShared {
+    DevBuf jobs, work, counter;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t ev_k0 = nullptr, ev_k1 = nullptr;  // around the shared persistent launch
+    ~BatchShared()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (ev_k0) cudaEventDestroy(ev_k0);
+        if (ev_k1) cudaEventDestroy(ev_k1);
+    }
+};
+}  // namespace pb
+
+struct pb_run {
+    pb_instance* inst = nullptr;
+    int form = 0;
+    int R = 0, S = 0;
+    int64_t N = 0;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev_start = nullptr, ev_stop = nullptr;
+    cudaEvent_t ev_k0 = nullptr, ev_k1 = nullptr;  // around the annealing kernels
+    // EA
+    pb::EaJob job{};
+    // biclique
+    pb::BqJob bjob{};
+    pb::DevBuf table, betaf, best_words, final_words, E_best_i, E_best_f, best_sweep, hit_sweep;
+    pb::DevBuf best_pm, final_pm, E_out;  // readout: [R][N] x2, [2R] doubles
+    pb::DevBuf extra[8];
+    std::shared_ptr<pb::BatchShared> batch;
+    ~pb_run()
+    {
+        if (ev_start) cudaEventDestroy(ev_start);
+        if (ev_stop) cudaEventDestroy(ev_stop);
+        if (ev_k0) cudaEventDestroy(ev_k0);
+        if (ev_k1) cudaEventDestroy(ev_k1);
+    }
+};
+
+
+namespace pb {
+int sm_count();
+pb_status schedule_levels(const pb_schedule* sc, std::vector<double>& betas, int& step);
+uint32_t threshold_u32(double beta, double F);
+pb_status bq_build(pb_instance* I, const pb_instance_desc* d, cudaStream_t st);
+pb_status bq_anneal(pb_run* run, pb_instance* I, const pb_schedule* sc, int R, uint64_t seed,
+                    const pb_anneal_opts* opts, cudaStream_t st);
+pb_status bq_fields(pb_instance* I, const int8_t* d_states, int R, float* d_out, cudaStream_t st);
+}  // namespace pb

@@ -1,0 +1,294 @@
+"""Thin ctypes binding of the C ABI in ``include/pbit.h`` (libpbit.so).
+
+Argument marshalling only: every step of the annealing path runs in the CUDA
+library.  Function names follow the C ABI.  Arrays are numpy arrays on the
+host; CUDA streams come from PyTorch (``torch.cuda.current_stream()``) or as
+raw ``cudaStream_t`` integers.  There is no CPU fallback: if the library is
+missing, ``load()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+from . import _build
+
+PB_OK, PB_EINVAL, PB_ECOLOUR, PB_ENOMEM, PB_EDEVICE, PB_ETIMEOUT, PB_EBUSY, PB_EUNSUPPORTED = range(8)
+PB_TOPO_EA3D, PB_TOPO_BICLIQUE = 0, 1
+PB_J_PM1_I8, PB_J_F32 = 0, 1
+PB_DIST_PM1, PB_DIST_GAUSS, PB_DIST_UNIF = 0, 1, 2
+PB_SCHED_LINEAR, PB_SCHED_GEOMETRIC, PB_SCHED_EXPLICIT = 0, 1, 2
+PB_FORM_AUTO, PB_FORM_PLAIN, PB_FORM_RESIDENT, PB_FORM_CUDACORE, PB_FORM_TENSOR = range(5)
+
+_ERRNAMES = {0: "PB_OK", 1: "PB_EINVAL", 2: "PB_ECOLOUR", 3: "PB_ENOMEM", 4: "PB_EDEVICE", 5: "PB_ETIMEOUT",
+             6: "PB_EBUSY", 7: "PB_EUNSUPPORTED"}
+
+
+class PbError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_ERRNAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class pb_instance_desc(ctypes.Structure):
+    _fields_ = [("topo", ctypes.c_int32), ("L", ctypes.c_int32), ("n", ctypes.c_int32), ("jtype", ctypes.c_int32),
+                ("J", ctypes.c_void_p), ("h", ctypes.c_void_p), ("colour", ctypes.c_void_p)]
+
+
+class pb_schedule(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("n_sweeps", ctypes.c_int32), ("step_duration", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("beta0", ctypes.c_double), ("beta1", ctypes.c_double),
+                ("betas", ctypes.c_void_p)]
+
+
+class pb_anneal_opts(ctypes.Structure):
+    _fields_ = [("form", ctypes.c_int32), ("flags", ctypes.c_int32), ("target_energy", ctypes.c_double)]
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libpbit.so; raise if it has not been built (``__graft_entry__.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"CUDA library missing: {_build.LIB} (run __graft_entry__.build())")
+    lib = ctypes.CDLL(_build.LIB)
+    P, I32, I64, U64, D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+    st = ctypes.c_int
+    sig = {
+        "pb_version": ([], ctypes.c_char_p),
+        "pb_status_string": ([st], ctypes.c_char_p),
+        "pb_last_error": ([], ctypes.c_char_p),
+        "pb_generate_ea": ([I32, I32, U64, P, I64], st),
+        "pb_generate_biclique": ([I32, I32, U64, P, I64], st),
+        "pb_create_instance": ([P, P, P], st),
+        "pb_instance_destroy": ([P], None),
+        "pb_instance_spins": ([P], I64),
+        "pb_anneal": ([P, P, I32, U64, P, P], st),
+        "pb_anneal_ex": ([P, P, I32, U64, P, P, P], st),
+        "pb_anneal_batch": ([I32, P, P, P, P, P, P, P], st),
+        "pb_wait": ([P, I32], st),
+        "pb_query": ([P], st),
+        "pb_energy": ([P, P, P, P], st),
+        "pb_best_states": ([P, P, I64], st),
+        "pb_final_states": ([P, P, I64], st),
+        "pb_target_sweeps": ([P, P], st),
+        "pb_run_device_ms": ([P, P], st),
+        "pb_run_kernel_ms": ([P, P], st),
+        "pb_run_destroy": ([P], None),
+        "pb_fields": ([P, P, I32, P, I64, P], st),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != PB_OK:
+        raise PbError(status, load().pb_last_error().decode())
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+# ------------------------------------------------------------------ basics
+def pb_version() -> str:
+    return load().pb_version().decode()
+
+
+def pb_status_string(status: int) -> str:
+    return load().pb_status_string(status).decode()
+
+
+def pb_last_error() -> str:
+    return load().pb_last_error().decode()
+
+
+def pb_generate_ea(L: int, dist: int, seed: int) -> np.ndarray:
+    """Seeded EA couplings [3, L^3]: int8 for PB_DIST_PM1, float32 otherwise."""
+    J = np.empty((3, L ** 3), dtype=np.int8 if dist == PB_DIST_PM1 else np.float32)
+    _check(load().pb_generate_ea(L, dist, seed, _ptr(J), J.nbytes))
+    return J
+
+
+def pb_generate_biclique(n: int, dist: int, seed: int) -> np.ndarray:
+    J = np.empty((n, n), dtype=np.int8 if dist == PB_DIST_PM1 else np.float32)
+    _check(load().pb_generate_biclique(n, dist, seed, _ptr(J), J.nbytes))
+    return J
+
+
+# --------------------------------------------------------------- instances
+def pb_create_instance(topo: int, J: np.ndarray, h: np.ndarray | None = None, colour: np.ndarray | None = None,
+                       L: int = 0, n: int = 0, stream=None) -> ctypes.c_void_p:
+    pm1 = J.dtype == np.int8
+    J = np.ascontiguousarray(J)
+    hh = None if h is None else np.ascontiguousarray(h, dtype=np.int8 if pm1 else np.float32)
+    cc = None if colour is None else np.ascontiguousarray(colour, dtype=np.int32)
+    d = pb_instance_desc(topo=topo, L=L, n=n, jtype=PB_J_PM1_I8 if pm1 else PB_J_F32, J=_ptr(J), h=_ptr(hh),
+                         colour=_ptr(cc))
+    out = ctypes.c_void_p()
+    _check(load().pb_create_instance(ctypes.byref(d), _stream(stream), ctypes.byref(out)))
+    return out
+
+
+def pb_instance_destroy(inst):
+    if inst:
+        load().pb_instance_destroy(inst)
+
+
+def pb_instance_spins(inst) -> int:
+    return int(load().pb_instance_spins(inst))
+
+
+def make_schedule(kind: int, n_sweeps: int, beta0: float = 0.0, beta1: float = 0.0, step_duration: int = 1,
+                  betas: np.ndarray | None = None):
+    """pb_schedule (the explicit betas array is kept alive on the returned object)."""
+    b = None if betas is None else np.ascontiguousarray(betas, dtype=np.float64)
+    s = pb_schedule(kind=kind, n_sweeps=n_sweeps, step_duration=step_duration, reserved=0, beta0=beta0,
+                    beta1=beta1, betas=_ptr(b))
+    s._keep = b
+    return s
+
+
+def make_opts(form: int = PB_FORM_AUTO, target_energy: float = math.nan):
+    return pb_anneal_opts(form=form, flags=0, target_energy=target_energy)
+
+
+# ------------------------------------------------------------------- runs
+def pb_anneal(inst, sched: pb_schedule, replicas: int, seed: int, opts: pb_anneal_opts | None = None,
+              stream=None) -> ctypes.c_void_p:
+    out = ctypes.c_void_p()
+    lib = load()
+    if opts is None:
+        _check(lib.pb_anneal(inst, ctypes.byref(sched), replicas, seed, _stream(stream), ctypes.byref(out)))
+    else:
+        _check(lib.pb_anneal_ex(inst, ctypes.byref(sched), replicas, seed, ctypes.byref(opts), _stream(stream),
+                                ctypes.byref(out)))
+    return out
+
+
+def pb_anneal_ex(inst, sched: pb_schedule, replicas: int, seed: int, opts: pb_anneal_opts,
+                 stream=None) -> ctypes.c_void_p:
+    return pb_anneal(inst, sched, replicas, seed, opts, stream)
+
+
+def pb_anneal_batch(insts, scheds, replicas, seeds, opts=None, stream=None):
+    k = len(insts)
+    ia = (ctypes.c_void_p * k)(*[i.value for i in insts])
+    sa = (pb_schedule * k)(*scheds)
+    ra = (ctypes.c_int32 * k)(*replicas)
+    ea = (ctypes.c_uint64 * k)(*seeds)
+    oa = None if opts is None else (pb_anneal_opts * k)(*opts)
+    outs = (ctypes.c_void_p * k)()
+    _check(load().pb_anneal_batch(k, ia, sa, ra, ea, oa, _stream(stream), outs))
+    return [ctypes.c_void_p(o) for o in outs]
+
+
+def pb_wait(run, timeout_ms: int = -1) -> int:
+    return int(load().pb_wait(run, timeout_ms))
+
+
+def pb_query(run) -> int:
+    return int(load().pb_query(run))
+
+
+def pb_energy(run, replicas: int):
+    fe = np.empty(replicas, np.float64)
+    be = np.empty(replicas, np.float64)
+    bs = np.empty(replicas, np.int32)
+    _check(load().pb_energy(run, _ptr(fe), _ptr(be), _ptr(bs)))
+    return fe, be, bs
+
+
+def pb_best_states(run, replicas: int, N: int) -> np.ndarray:
+    out = np.empty((replicas, N), np.int8)
+    _check(load().pb_best_states(run, _ptr(out), out.nbytes))
+    return out
+
+
+def pb_final_states(run, replicas: int, N: int) -> np.ndarray:
+    out = np.empty((replicas, N), np.int8)
+    _check(load().pb_final_states(run, _ptr(out), out.nbytes))
+    return out
+
+
+def pb_target_sweeps(run, replicas: int) -> np.ndarray:
+    out = np.empty(replicas, np.int32)
+    _check(load().pb_target_sweeps(run, _ptr(out)))
+    return out
+
+
+def pb_run_device_ms(run) -> float:
+    ms = ctypes.c_float()
+    _check(load().pb_run_device_ms(run, ctypes.byref(ms)))
+    return float(ms.value)
+
+
+def pb_run_kernel_ms(run) -> float:
+    ms = ctypes.c_float()
+    _check(load().pb_run_kernel_ms(run, ctypes.byref(ms)))
+    return float(ms.value)
+
+
+def pb_run_destroy(run):
+    if run:
+        load().pb_run_destroy(run)
+
+
+def pb_fields(inst, states: np.ndarray, stream=None) -> np.ndarray:
+    states = np.ascontiguousarray(states, dtype=np.int8)
+    R, N = states.shape
+    out = np.empty((R, N), np.float32)
+    _check(load().pb_fields(inst, _ptr(states), R, _ptr(out), out.nbytes, _stream(stream)))
+    return out
+
+
+# ------------------------------------------------------- convenience layer
+def anneal(topo: int, J: np.ndarray, betas_or_sched, replicas: int, seed: int, h=None, L: int = 0, n: int = 0,
+           form: int = PB_FORM_AUTO, target_energy: float = math.nan, stream=None) -> dict:
+    """Create the instance, run one anneal, read every result back (synchronous)."""
+    inst = pb_create_instance(topo, J, h, None, L=L, n=n, stream=stream)
+    try:
+        sched = betas_or_sched
+        if not isinstance(sched, pb_schedule):
+            b = np.asarray(betas_or_sched, dtype=np.float64)
+            sched = make_schedule(PB_SCHED_EXPLICIT, b.size, betas=b)
+        run = pb_anneal(inst, sched, replicas, seed, make_opts(form, target_energy), stream=stream)
+        try:
+            N = pb_instance_spins(inst)
+            fe, be, bs = pb_energy(run, replicas)
+            return dict(final_E=fe, best_E=be, best_sweep=bs, final_state=pb_final_states(run, replicas, N),
+                        best_state=pb_best_states(run, replicas, N), target_sweep=pb_target_sweeps(run, replicas),
+                        device_ms=pb_run_device_ms(run))
+        finally:
+            pb_run_destroy(run)
+    finally:
+        pb_instance_destroy(inst)

@@ -1,0 +1,110 @@
+"""GPU parity of the biclique K_{n,n} path against the CPU oracle.
+
++-1 couplings: bit-exact trajectories (integer fields, FP64-built threshold
+table).  Real couplings: fields within 1e-5 of FP64 relative to
+sum_j |J_ij| + |h_i|, returned-state energies in FP64 within 1e-9 relative,
+ensemble mean energy per spin within 3 standard errors.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synth_inputs as syn
+
+pytestmark = pytest.mark.gpu
+
+FORMS = ["cudacore"]
+
+
+@pytest.fixture(scope="module")
+def pb():
+    from paper_2510_23419_gb300 import _build, native
+    _build.build()
+    native.load()
+    return native
+
+
+def _form(pb, name):
+    return {"cudacore": pb.PB_FORM_CUDACORE, "tensor": pb.PB_FORM_TENSOR}[name]
+
+
+def _gpu(pb, n, J, h, sc, R, seed, form):
+    return pb.anneal(pb.PB_TOPO_BICLIQUE, J, sc, R, seed, h=h, n=n, form=_form(pb, form))
+
+
+def _orc(orc, n, J, h, betas, R, seed):
+    return orc.anneal_biclique(n, np.asarray(J, np.float64), None if h is None else np.asarray(h, np.float64),
+                               betas, R, seed)
+
+
+CASES = [
+    # n, R, S, kind, b0, b1, hmax, seed
+    (32, 8, 60, 0, 0.05, 1.0, 0, 1),
+    (37, 5, 25, 0, 0.05, 0.8, 0, 2),
+    (64, 64, 20, 1, 0.01, 1.0, 0, 3),
+    (20, 3, 40, 0, 0.35, 3.5, 2, 4),
+    (130, 70, 6, 0, 0.02, 0.3, 0, 5),
+    (9, 1, 0, 0, 0.1, 0.1, 0, 6),
+]
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("case", CASES, ids=[f"n{c[0]}R{c[1]}S{c[2]}h{c[6]}" for c in CASES])
+def test_pm1_bit_exact(pb, orc, case, form):
+    n, R, S, kind, b0, b1, hmax, seed = case
+    J = syn.biclique_couplings(n, "pm1", seed)
+    h = syn.int_fields(2 * n, hmax, seed + 1) if hmax else None
+    sc = pb.make_schedule(kind, S, b0, b1)
+    ob = orc.schedule(kind, b0, b1, S)
+    g = _gpu(pb, n, J, h, sc, R, seed, form)
+    o = _orc(orc, n, J, h, ob, R, seed)
+    for k in ("final_state", "best_state", "final_E", "best_E", "best_sweep"):
+        assert np.array_equal(g[k], o[k]), k
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_ferromagnet_closed_form(pb, form):
+    n = 64
+    J = np.ones((n, n), np.int8)
+    sc = pb.make_schedule(pb.PB_SCHED_LINEAR, 100, 0.01, 0.5)
+    g = _gpu(pb, n, J, None, sc, 16, 3, form)
+    assert np.all(g["best_E"] == -n * n)
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_f32_fields(pb, orc, form):
+    n = 96
+    J = syn.biclique_couplings(n, "gauss", 11)
+    h = syn.real_fields(2 * n, 0.5, 12)
+    inst = pb.pb_create_instance(pb.PB_TOPO_BICLIQUE, J, h, n=n)
+    try:
+        m = syn.states(5, 2 * n, 13)
+        F = pb.pb_fields(inst, m)
+    finally:
+        pb.pb_instance_destroy(inst)
+    eu, ev, _ = orc.biclique_graph(n)
+    Jd = J.astype(np.float64).reshape(-1)
+    hd = h.astype(np.float64)
+    scale = orc.fields(eu, ev, np.abs(Jd), np.abs(hd), np.ones(2 * n, np.int8))
+    for r in range(5):
+        F64 = orc.fields(eu, ev, Jd, hd, m[r])
+        assert np.all(np.abs(F[r] - F64) <= 1e-5 * scale)
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_f32_energies_and_ensemble(pb, orc, form):
+    n, R, S = 48, 128, 80
+    J = syn.biclique_couplings(n, "unif", 21)
+    sc = pb.make_schedule(pb.PB_SCHED_LINEAR, S, 0.35, 3.5)
+    ob = orc.schedule(orc.SCHED_LINEAR, 0.35, 3.5, S)
+    g = _gpu(pb, n, J, None, sc, R, 5, form)
+    eu, ev, _ = orc.biclique_graph(n)
+    Jd = J.astype(np.float64).reshape(-1)
+    for r in range(R):
+        e = orc.energy(eu, ev, Jd, None, g["best_state"][r])
+        assert abs(g["best_E"][r] - e) <= 1e-9 * abs(e)
+    o = _orc(orc, n, J, None, ob, R, 5)
+    eg, eo = g["final_E"] / (2 * n), o["final_E"] / (2 * n)
+    se = math.sqrt(eg.var(ddof=1) / R + eo.var(ddof=1) / R)
+    assert abs(eg.mean() - eo.mean()) <= 3 * se + 1e-12
