@@ -8,6 +8,7 @@
 // Philox word of (i, s, r >> 2, side) and writes the new spins.  Fields of
 // +-1 instances are exact integers in FP32 (|F| <= n + |h| < 2^24).
 #include "biclique_launch.h"
+#include "ea_kernels.cuh"
 
 namespace pb {
 
@@ -30,12 +31,6 @@ struct SpinCode<2> {
     __device__ static bool minus(T v) { return (v & 0x8000u) != 0; }
 };
 
-__device__ __forceinline__ uint32_t thr_f32_bq(float F, float beta)
-{
-    const float e = __expf(-2.0f * beta * F);
-    const float P = __fdividef(1.0f, 1.0f + e);
-    return __float2uint_rz(P * 4294967296.0f);
-}
 
 __global__ void __launch_bounds__(256) bq_init_kernel(BqJob job)
 {
@@ -137,11 +132,11 @@ __global__ void __launch_bounds__(256) bq_cc_half_kernel(BqJob job, int side, in
     // ---- epilogue: decisions (Eq. 2), energy partials ----
     const bool pm1 = job.inst.jtype == PB_J_PM1_I8;
     const uint32_t* trow = nullptr;
-    float beta = 0.0f;
+    float cexp = 0.0f;
     if (pm1)
         trow = job.table + (size_t)(s / job.step) * job.nF;
     else
-        beta = job.betaf[s / job.step];
+        cexp = f32_cexp(job.betaf[s / job.step]);
     float e_field[4] = {0.f, 0.f, 0.f, 0.f};  // -m F  (side B)
     float e_h[4] = {0.f, 0.f, 0.f, 0.f};      // -h m  (side A)
     const int rq = r0 + tx * 4;
@@ -166,8 +161,7 @@ __global__ void __launch_bounds__(256) bq_cc_half_kernel(BqJob job, int side, in
             const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
-                const uint32_t T = pm1 ? trow[(int)F[b] - job.fmin] : thr_f32_bq(F[b], beta);
-                mn[b] = ws[b] >= T;
+                mn[b] = pm1 ? (ws[b] >= trow[(int)F[b] - job.fmin]) : (decide_f32(ws[b], F[b], cexp) != 0u);
                 own[(size_t)(rq + b) * job.ld + i] = SC::enc(mn[b]);
             }
         } else {

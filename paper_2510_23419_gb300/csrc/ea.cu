@@ -11,6 +11,7 @@
 //    neighbour word is read from shared memory.
 //  * plain: spins in global memory, one launch per colour class and sweep,
 //    plus one energy/best launch per sweep.
+#include "ea_fast.cuh"
 #include "ea_kernels.cuh"
 #include "ea_launch.h"
 
@@ -151,9 +152,9 @@ __device__ void ea_tile(const EaJob& job, int tile, unsigned char* smem)
     p += (size_t)2 * tabw4 * 4;
     int32_t* spart_i = reinterpret_cast<int32_t*>(p);
     float* spart_f = reinterpret_cast<float*>(p);
-    p += (size_t)32 * nrep * 4;
+    p += (size_t)kResidentWarps * nrep * 4;
     int32_t* spart_h = reinterpret_cast<int32_t*>(p);
-    if (JT == PB_J_PM1_I8 && HH) p += (size_t)32 * nrep * 4;
+    if (JT == PB_J_PM1_I8 && HH) p += (size_t)kResidentWarps * nrep * 4;
     uint8_t* sflag = p;
 
     const uint32_t key0 = job.key0, key1 = job.key1;
@@ -199,8 +200,8 @@ __device__ void ea_tile(const EaJob& job, int tile, unsigned char* smem)
         const uint32_t c3 = (kTagDecision << 24) | (uint32_t)c;
         const int buf = s & 1;
         const uint32_t* tab = stab + buf * tabw4;
-        float beta = 0.0f;
-        if (JT == PB_J_F32) beta = job.betaf[s / job.step];
+        float cexp = 0.0f;
+        if (JT == PB_J_F32) cexp = f32_cexp(job.betaf[s / job.step]);
         for (int zp = 0; zp < (g.zstep == 1 ? 2 : 1); ++zp) {
             const int z0 = (g.zstep == 1) ? zp : g.zfirst;
             const int px = (c + g.y + z0) & 1;
@@ -263,9 +264,8 @@ __device__ void ea_tile(const EaJob& job, int tile, unsigned char* smem)
                     for (int b = 0; b < 4; ++b) F[b] = ea_field_f32(jv, hv, nb, b);
                     if (decide) {
                         const U4 r = philox10((uint32_t)k, (uint32_t)s, g.tq, c3, key0, key1);
-                        snew = decide_bit(r.x, thr_f32(F[0], beta)) | (decide_bit(r.y, thr_f32(F[1], beta)) << 8) |
-                               (decide_bit(r.z, thr_f32(F[2], beta)) << 16) |
-                               (decide_bit(r.w, thr_f32(F[3], beta)) << 24);
+                        snew = decide_f32(r.x, F[0], cexp) | (decide_f32(r.y, F[1], cexp) << 8) |
+                               (decide_f32(r.z, F[2], cexp) << 16) | (decide_f32(r.w, F[3], cexp) << 24);
                         own[kw] = snew;
                     } else {
                         snew = own[kw];
@@ -296,7 +296,7 @@ __device__ void ea_tile(const EaJob& job, int tile, unsigned char* smem)
     auto energy_of = [&](int r, int32_t& Ei, float& Ef) {
         if (JT == PB_J_PM1_I8) {
             int32_t U = 0, H = 0;
-            for (int v = 0; v < 32; ++v) {
+            for (int v = 0; v < kResidentWarps; ++v) {
                 U += spart_i[v * nrep + r];
                 if (HH) H += spart_h[v * nrep + r];
             }
@@ -304,7 +304,7 @@ __device__ void ea_tile(const EaJob& job, int tile, unsigned char* smem)
             Ei = -(3 * N - 2 * U) - H;
         } else {
             float E = 0.0f;
-            for (int v = 0; v < 32; ++v) E += spart_f[v * nrep + r];
+            for (int v = 0; v < kResidentWarps; ++v) E += spart_f[v * nrep + r];
             Ef = E;
         }
     };
@@ -391,16 +391,20 @@ __global__ void __launch_bounds__(kResidentThreads, 1)
             if (job.inst.has_h)
                 ea_tile<0, 0, PB_J_PM1_I8, true>(job, wk.tile, smem);
             else if (L == 32 && WT == 1)
-                ea_tile<32, 1, PB_J_PM1_I8, false>(job, wk.tile, smem);
-            else if (L == 16 && WT == 8)
-                ea_tile<16, 8, PB_J_PM1_I8, false>(job, wk.tile, smem);
+                ea_tile_fast<32, 1, PB_J_PM1_I8>(job, wk.tile, smem);
+            else if (L == 16 && WT == 4)
+                ea_tile_fast<16, 4, PB_J_PM1_I8>(job, wk.tile, smem);
+            else if (L == 8 && WT == 16)
+                ea_tile_fast<8, 16, PB_J_PM1_I8>(job, wk.tile, smem);
             else
                 ea_tile<0, 0, PB_J_PM1_I8, false>(job, wk.tile, smem);
         } else {
             if (L == 32 && WT == 1)
-                ea_tile<32, 1, PB_J_F32, false>(job, wk.tile, smem);
-            else if (L == 16 && WT == 8)
-                ea_tile<16, 8, PB_J_F32, false>(job, wk.tile, smem);
+                ea_tile_fast<32, 1, PB_J_F32>(job, wk.tile, smem);
+            else if (L == 16 && WT == 4)
+                ea_tile_fast<16, 4, PB_J_F32>(job, wk.tile, smem);
+            else if (L == 8 && WT == 16)
+                ea_tile_fast<8, 16, PB_J_F32>(job, wk.tile, smem);
             else
                 ea_tile<0, 0, PB_J_F32, false>(job, wk.tile, smem);
         }
@@ -491,11 +495,10 @@ __global__ void __launch_bounds__(256) ea_plain_half_kernel(EaJob job, int c, in
         const float4 jb = __ldg(reinterpret_cast<const float4*>(job.inst.j6) + 2 * site + 1);
         const float jv[6] = {ja.x, ja.y, ja.z, ja.w, jb.x, jb.y};
         const float hv = __ldg(job.inst.hf + site);
-        const float beta = job.betaf[s / job.step];
-        snew = decide_bit(r.x, thr_f32(ea_field_f32(jv, hv, nb, 0), beta)) |
-               (decide_bit(r.y, thr_f32(ea_field_f32(jv, hv, nb, 1), beta)) << 8) |
-               (decide_bit(r.z, thr_f32(ea_field_f32(jv, hv, nb, 2), beta)) << 16) |
-               (decide_bit(r.w, thr_f32(ea_field_f32(jv, hv, nb, 3), beta)) << 24);
+        const float cexp = f32_cexp(job.betaf[s / job.step]);
+        snew = decide_f32(r.x, ea_field_f32(jv, hv, nb, 0), cexp) | (decide_f32(r.y, ea_field_f32(jv, hv, nb, 1), cexp) << 8) |
+               (decide_f32(r.z, ea_field_f32(jv, hv, nb, 2), cexp) << 16) |
+               (decide_f32(r.w, ea_field_f32(jv, hv, nb, 3), cexp) << 24);
     }
     job.final_words[(size_t)c * half * WT + j] = snew;
 }

@@ -39,14 +39,20 @@ __device__ __forceinline__ uint32_t ea_popc6_bytes(uint32_t y)
 // Decision of one replica: new spin bit (1 <=> m = -1) is 1 unless r < T.
 __device__ __forceinline__ uint32_t decide_bit(uint32_t r, uint32_t T) { return r >= T ? 1u : 0u; }
 
-// FP32 threshold of the F32 path: floor(2^32 / (1 + e^{-2 beta F})), which is
-// 2^32 (1/2 + tanh(beta F)/2); the float->uint conversion saturates at 2^32-1.
-__device__ __forceinline__ uint32_t thr_f32(float F, float beta)
+// FP32 decision of the F32 path (Eq. 2): m = +1 with probability
+// P = 1/2 + tanh(beta F)/2 = 1 / (1 + e^{-2 beta F}).  The word r gives
+// u = ((r >> 9) + 1/2) 2^-23, the comparison u < P is evaluated as
+// u (1 + e^{-2 beta F}) < 1, so it needs one exp2 and no reciprocal or
+// float->int conversion.  Returns the new spin bit (1 <=> m = -1).
+// cexp = -2 beta log2(e).
+__device__ __forceinline__ uint32_t decide_f32(uint32_t r, float F, float cexp)
 {
-    const float e = __expf(-2.0f * beta * F);
-    const float P = __fdividef(1.0f, 1.0f + e);
-    return __float2uint_rz(P * 4294967296.0f);
+    const float u = __uint_as_float(0x3F800000u | (r >> 9)) - 0.99999994f;
+    const float e = exp2f(cexp * F);
+    return fmaf(u, e, u) >= 1.0f ? 1u : 0u;
 }
+
+__device__ __forceinline__ float f32_cexp(float beta) { return -2.0f * beta * 1.4426950408889634f; }
 
 // FP32 local field of replica b (byte b of the neighbour words), Eq. 3, in the
 // fixed order h + (+x) + (-x) + (+y) + (-y) + (+z) + (-z).

@@ -386,10 +386,12 @@ static pb_status ea_enqueue_resident(std::vector<pb_run*>& runs, cudaStream_t st
     if (capture) PB_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     auto body = [&]() -> pb_status {
         PB_CUDA_TRY(cudaMemsetAsync(shared->counter.p, 0, 16, st));
-        PB_CUDA_TRY(cudaEventRecord(shared->ev_k0, st));
+        // inside a capture an event becomes a graph node only when recorded as external
+        const unsigned evf = capture ? cudaEventRecordExternal : cudaEventRecordDefault;
+        PB_CUDA_TRY(cudaEventRecordWithFlags(shared->ev_k0, st, evf));
         PB_CUDA_TRY(ea_launch_resident(shared->jobs.as<EaJob>(), shared->work.as<EaWork>(), (int)work.size(),
                                        shared->counter.as<int>(), smem, grid, st));
-        PB_CUDA_TRY(cudaEventRecord(shared->ev_k1, st));
+        PB_CUDA_TRY(cudaEventRecordWithFlags(shared->ev_k1, st, evf));
         for (pb_run* r : runs) {
             pb_status ps = ea_enqueue_readout(r, st);
             if (ps != PB_OK) return ps;
