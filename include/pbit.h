@@ -201,6 +201,32 @@ void pb_run_destroy(pb_run* run);
 pb_status pb_fields(pb_instance* inst, const int8_t* states, int32_t R, float* fields_out, int64_t out_bytes,
                     void* stream);
 
+/* EA +-1 anneal that allocates no memory (no counterpart in the paper: it is a
+ * deployment convenience).  For callers that cannot call cudaMalloc -- code that
+ * runs inside a device-memory arena or pool it does not own, or in a loop where an
+ * allocation and the synchronisation it can cause are not allowed.  It runs the
+ * same resident kernel as pb_anneal (results are identical to pb_anneal with the
+ * same arguments) but keeps every scratch buffer in one file-scope device array
+ * of 16 MiB, which each GPU that loads this library holds until the process
+ * exits.  Inputs and outputs are caller-owned DEVICE buffers:
+ *   J_dev            [3][L^3] int8 +-1 couplings (same layout as pb_instance_desc.J), h = 0
+ *   best_E_dev, final_E_dev     [replicas] double (exact int energies)
+ *   best_sweep_dev   [replicas] int32
+ *   best_states_dev, final_states_dev  [replicas][L^3] int8 +-1
+ * The schedule is read from host memory during the call.  L must be even, in [2, 32].
+ * A request whose scratch (about 2 * replicas * L^3 bytes plus the threshold
+ * table of 52 bytes per beta level) exceeds 16 MiB is rejected with PB_EINVAL.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call uses the same array and leaves its contents behind: calls whose
+ * work overlaps on the GPU (different streams, or threads without ordering)
+ * race and corrupt each other -- order them on one stream.  The call returns
+ * once the work is queued on `stream` (after a short synchronisation that
+ * checks the couplings); results are ready when the stream reaches that point. */
+pb_status pb_anneal_ea_noalloc(int32_t L, const int8_t* J_dev, const pb_schedule* sched, int32_t replicas,
+                               uint64_t seed, double* best_E_dev, int32_t* best_sweep_dev, int8_t* best_states_dev,
+                               double* final_E_dev, int8_t* final_states_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -87,6 +87,7 @@ def load():
         "pb_run_kernel_ms": ([P, P], st),
         "pb_run_destroy": ([P], None),
         "pb_fields": ([P, P, I32, P, I64, P], st),
+        "pb_anneal_ea_noalloc": ([I32, P, P, I32, U64, P, P, P, P, P, P], st),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -269,6 +270,16 @@ def pb_fields(inst, states: np.ndarray, stream=None) -> np.ndarray:
     out = np.empty((R, N), np.float32)
     _check(load().pb_fields(inst, _ptr(states), R, _ptr(out), out.nbytes, _stream(stream)))
     return out
+
+
+def pb_anneal_ea_noalloc(L: int, J_dev: int, sched: pb_schedule, replicas: int, seed: int, best_E_dev: int,
+                         best_sweep_dev: int, best_states_dev: int, final_E_dev: int, final_states_dev: int,
+                         stream=None):
+    """EA +-1 anneal into caller-owned device buffers (raw device pointers); allocates nothing."""
+    _check(load().pb_anneal_ea_noalloc(L, ctypes.c_void_p(J_dev), ctypes.byref(sched), replicas, seed,
+                                       ctypes.c_void_p(best_E_dev), ctypes.c_void_p(best_sweep_dev),
+                                       ctypes.c_void_p(best_states_dev), ctypes.c_void_p(final_E_dev),
+                                       ctypes.c_void_p(final_states_dev), _stream(stream)))
 
 
 # ------------------------------------------------------- convenience layer
