@@ -108,8 +108,8 @@ typedef enum pb_form {
     PB_FORM_AUTO = 0,      /* resident form where it fits, else plain (EA); tensor form (biclique) */
     PB_FORM_PLAIN = 1,     /* EA: spins in global memory, one launch per colour class and sweep */
     PB_FORM_RESIDENT = 2,  /* EA: one persistent launch, each replica block's lattice kept in shared memory */
-    PB_FORM_CUDACORE = 3,  /* biclique: CUDA-core field (int8 dp4a for +-1, FP32 FMA for F32) */
-    PB_FORM_TENSOR = 4     /* biclique: tcgen05 tensor-core field */
+    PB_FORM_CUDACORE = 3,  /* biclique: CUDA-core field (FP32 FMA; exact integers for +-1) */
+    PB_FORM_TENSOR = 4     /* biclique: tcgen05 tensor-core field (e4m3 for +-1, split BF16 for F32) */
 } pb_form;
 
 typedef struct pb_anneal_opts {
@@ -200,6 +200,12 @@ void pb_run_destroy(pb_run* run);
  * fields_out: host [R][N] float, out_bytes >= 4 R N.  Synchronous. */
 pb_status pb_fields(pb_instance* inst, const int8_t* states, int32_t R, float* fields_out, int64_t out_bytes,
                     void* stream);
+/* pb_fields with the arithmetic of a given form (pb_form; AUTO = the form pb_anneal picks).
+ * Biclique: PB_FORM_TENSOR (tensor-core e4m3, or split-BF16 products with FP32 accumulation)
+ * or PB_FORM_CUDACORE (FP32 FMA).  Errors as pb_fields, PB_EUNSUPPORTED for a form the
+ * instance has no kernel for. */
+pb_status pb_fields_ex(pb_instance* inst, const int8_t* states, int32_t R, int32_t form, float* fields_out,
+                       int64_t out_bytes, void* stream);
 
 /* EA +-1 anneal that allocates no memory (no counterpart in the paper: it is a
  * deployment convenience).  For callers that cannot call cudaMalloc -- code that

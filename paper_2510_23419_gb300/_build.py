@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpbit.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
-SOURCES = ["ea.cu", "biclique.cu", "noalloc.cu", "host_api.cpp", "biclique_host.cpp"]
+SOURCES = ["ea.cu", "biclique.cu", "biclique_tc.cu", "noalloc.cu", "host_api.cpp", "biclique_host.cpp"]
 
 
 def _nvcc() -> str:

@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <string>
 #include <vector>
 
@@ -12,6 +13,22 @@
 namespace pb {
 
 static int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+// float -> bf16 with round to nearest even (finite inputs), and back
+static uint16_t bf16_rne(float f)
+{
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+static float bf16_to_f(uint16_t h)
+{
+    const uint32_t u = (uint32_t)h << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
 
 pb_status bq_build(pb_instance* I, const pb_instance_desc* d, cudaStream_t st)
 {
@@ -88,9 +105,55 @@ pb_status bq_build(pb_instance* I, const pb_instance_desc* d, cudaStream_t st)
             PB_CUDA_TRY(cudaMemcpyAsync(B[2].p, d->h, 2 * (size_t)n, cudaMemcpyHostToDevice, st));
         }
     }
+    // tensor-core operands: e4m3 (+-1) or bf16 hi/lo (F32), row stride ldj (a multiple of 16 elements)
+    const int ldj = round_up(n, 16);
+    const size_t tn = (size_t)n * ldj;
+    if (pm1) {
+        std::vector<uint8_t> q8(tn, 0), q8t(tn, 0);
+        const int8_t* J = static_cast<const int8_t*>(d->J);
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) {
+                const uint8_t v = J[(size_t)i * n + j] > 0 ? kE4m3Plus : kE4m3Minus;
+                q8[(size_t)i * ldj + j] = v;
+                q8t[(size_t)j * ldj + i] = v;
+            }
+        PB_ALLOC(B[6], tn);
+        PB_ALLOC(B[7], tn);
+        PB_CUDA_TRY(cudaMemcpyAsync(B[6].p, q8.data(), tn, cudaMemcpyHostToDevice, st));
+        PB_CUDA_TRY(cudaMemcpyAsync(B[7].p, q8t.data(), tn, cudaMemcpyHostToDevice, st));
+        PB_CUDA_TRY(cudaStreamSynchronize(st));
+    } else {
+        std::vector<uint16_t> hi(tn, 0), lo(tn, 0), hit(tn, 0), lot(tn, 0);
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) {
+                const float v = Jf[(size_t)i * n + j];
+                const uint16_t h = bf16_rne(v);
+                const uint16_t l = bf16_rne(v - bf16_to_f(h));
+                hi[(size_t)i * ldj + j] = h;
+                lo[(size_t)i * ldj + j] = l;
+                hit[(size_t)j * ldj + i] = h;
+                lot[(size_t)j * ldj + i] = l;
+            }
+        for (int b = 0; b < 4; ++b) PB_ALLOC(B[6 + b], tn * 2);
+        PB_CUDA_TRY(cudaMemcpyAsync(B[6].p, hi.data(), tn * 2, cudaMemcpyHostToDevice, st));
+        PB_CUDA_TRY(cudaMemcpyAsync(B[7].p, lo.data(), tn * 2, cudaMemcpyHostToDevice, st));
+        PB_CUDA_TRY(cudaMemcpyAsync(B[8].p, hit.data(), tn * 2, cudaMemcpyHostToDevice, st));
+        PB_CUDA_TRY(cudaMemcpyAsync(B[9].p, lot.data(), tn * 2, cudaMemcpyHostToDevice, st));
+        PB_CUDA_TRY(cudaStreamSynchronize(st));
+    }
     PB_CUDA_TRY(cudaStreamSynchronize(st));
     BqDevice& q = I->bq;
     q = BqDevice{};
+    q.ldj = ldj;
+    if (pm1) {
+        q.Jq = B[6].as<uint8_t>();
+        q.Jqt = B[7].as<uint8_t>();
+    } else {
+        q.Jhi = B[6].as<uint16_t>();
+        q.Jlo = B[7].as<uint16_t>();
+        q.Jthi = B[8].as<uint16_t>();
+        q.Jtlo = B[9].as<uint16_t>();
+    }
     q.n = n;
     q.jtype = d->jtype;
     q.has_h = I->has_h;
@@ -105,7 +168,7 @@ pb_status bq_build(pb_instance* I, const pb_instance_desc* d, cudaStream_t st)
 }
 
 static pb_status bq_prepare(pb_run* run, pb_instance* I, const pb_schedule* sc, int R, uint64_t seed,
-                            const pb_anneal_opts* opts, cudaStream_t st)
+                            const pb_anneal_opts* opts, int form, cudaStream_t st)
 {
     std::vector<double> betas;
     int step = 1;
@@ -126,9 +189,11 @@ static pb_status bq_prepare(pb_run* run, pb_instance* I, const pb_schedule* sc, 
     j.S = sc->n_sweeps;
     j.step = step;
     j.R = R;
-    j.Rpad = round_up(R, kBqTileReps);
+    const bool tensor = form == PB_FORM_TENSOR;
+    run->form = form;
+    j.Rpad = round_up(R, tensor ? kBqTcReps : kBqTileReps);
     j.ld = round_up(n, 16);
-    j.nblk = (n + kBqTileRows - 1) / kBqTileRows;
+    j.nblk = (n + (tensor ? kBqTcRows : kBqTileRows) - 1) / (tensor ? kBqTcRows : kBqTileRows);
     const int nlev = std::max<int>(1, (int)betas.size());
     if (pm1) {
         const int fmax = n + I->hmax;
@@ -177,9 +242,32 @@ static pb_status bq_prepare(pb_run* run, pb_instance* I, const pb_schedule* sc, 
     PB_ALLOC(run->best_pm, (size_t)R * I->N);
     PB_ALLOC(run->final_pm, (size_t)R * I->N);
     PB_ALLOC(run->E_out, (size_t)2 * R * 8);
+    PB_ALLOC(run->extra[5], 16);
+    PB_CUDA_TRY(cudaMemsetAsync(run->extra[5].p, 0, 16, st));
+    run->dev_err = run->extra[5].as<int>();
+    if (tensor) {
+        const int esz = pm1 ? 1 : 2;
+        const BqDevice& q = I->bq;
+        const void* a[4] = {pm1 ? (const void*)q.Jq : (const void*)q.Jhi, pm1 ? (const void*)q.Jq : (const void*)q.Jlo,
+                            pm1 ? (const void*)q.Jqt : (const void*)q.Jthi, pm1 ? (const void*)q.Jqt : (const void*)q.Jtlo};
+        for (int k = 0; k < 4; ++k)
+            PB_CUDA_TRY(bq_tc_make_map(&run->maps.a[k], a[k], esz, (uint64_t)n, (uint64_t)n, (uint64_t)q.ldj * esz,
+                                       kBqTcRows));
+        for (int sd = 0; sd < 2; ++sd)
+            PB_CUDA_TRY(bq_tc_make_map(&run->maps.b[sd], j.spins[sd], esz, (uint64_t)n, (uint64_t)j.Rpad,
+                                       (uint64_t)j.ld * esz, kBqTcReps));
+        PB_CUDA_TRY(bq_tc_set_smem());
+    }
     PB_CUDA_TRY(cudaEventCreate(&run->ev_start));
     PB_CUDA_TRY(cudaEventCreate(&run->ev_stop));
     return PB_OK;
+}
+
+static cudaError_t bq_half(pb_run* run, int side, int s, int decide, float* fields_out, cudaStream_t st)
+{
+    if (run->form == PB_FORM_TENSOR)
+        return bq_launch_tc_half(run->maps, run->bjob, side, s, decide, fields_out, run->dev_err, st);
+    return bq_launch_cc_half(run->bjob, side, s, decide, fields_out, st);
 }
 
 static pb_status bq_enqueue_body(pb_run* run, cudaStream_t st)
@@ -187,12 +275,12 @@ static pb_status bq_enqueue_body(pb_run* run, cudaStream_t st)
     const BqJob& j = run->bjob;
     PB_CUDA_TRY(bq_launch_init(j, st));
     // energy of the initial state: side B fields of the initial A, no decisions
-    PB_CUDA_TRY(bq_launch_cc_half(j, 0, 0, 0, nullptr, st));
-    PB_CUDA_TRY(bq_launch_cc_half(j, 1, 0, 0, nullptr, st));
+    PB_CUDA_TRY(bq_half(run, 0, 0, 0, nullptr, st));
+    PB_CUDA_TRY(bq_half(run, 1, 0, 0, nullptr, st));
     PB_CUDA_TRY(bq_launch_sweep_end(j, -1, 1, st));
     for (int s = 0; s < j.S; ++s) {
-        PB_CUDA_TRY(bq_launch_cc_half(j, 0, s, 1, nullptr, st));
-        PB_CUDA_TRY(bq_launch_cc_half(j, 1, s, 1, nullptr, st));
+        PB_CUDA_TRY(bq_half(run, 0, s, 1, nullptr, st));
+        PB_CUDA_TRY(bq_half(run, 1, s, 1, nullptr, st));
         PB_CUDA_TRY(bq_launch_sweep_end(j, s, 0, st));
     }
     PB_CUDA_TRY(bq_launch_readout(j, 0, run->final_pm.as<int8_t>(), run->E_out.as<double>(), st));
@@ -203,12 +291,12 @@ static pb_status bq_enqueue_body(pb_run* run, cudaStream_t st)
 pb_status bq_anneal(pb_run* run, pb_instance* I, const pb_schedule* sc, int R, uint64_t seed,
                     const pb_anneal_opts* opts, cudaStream_t st)
 {
-    const int form = opts ? opts->form : PB_FORM_AUTO;
-    if (form != PB_FORM_AUTO && form != PB_FORM_CUDACORE)
+    int form = opts ? opts->form : PB_FORM_AUTO;
+    if (form == PB_FORM_AUTO) form = PB_FORM_TENSOR;
+    if (form != PB_FORM_TENSOR && form != PB_FORM_CUDACORE)
         return fail(PB_EUNSUPPORTED, "form not available for biclique instances");
-    pb_status ps = bq_prepare(run, I, sc, R, seed, opts, st);
+    pb_status ps = bq_prepare(run, I, sc, R, seed, opts, form, st);
     if (ps != PB_OK) return ps;
-    run->form = PB_FORM_CUDACORE;
     PB_CUDA_TRY(cudaEventRecord(run->ev_start, st));
     const bool capture = st != nullptr && st != cudaStreamLegacy && st != cudaStreamPerThread;
     if (capture) {
@@ -235,20 +323,26 @@ pb_status bq_anneal(pb_run* run, pb_instance* I, const pb_schedule* sc, int R, u
     return PB_OK;
 }
 
-pb_status bq_fields(pb_instance* I, const int8_t* d_states, int R, float* d_out, cudaStream_t st)
+pb_status bq_fields(pb_instance* I, const int8_t* d_states, int R, int form, float* d_out, cudaStream_t st)
 {
+    if (form == PB_FORM_AUTO) form = PB_FORM_TENSOR;
+    if (form != PB_FORM_TENSOR && form != PB_FORM_CUDACORE)
+        return fail(PB_EUNSUPPORTED, "form not available for biclique instances");
     pb_run run;
     pb_schedule sc{};
     sc.kind = PB_SCHED_LINEAR;
     sc.n_sweeps = 1;
     sc.step_duration = 1;
     sc.beta0 = sc.beta1 = 0.0;
-    pb_status ps = bq_prepare(&run, I, &sc, R, 0, nullptr, st);
+    pb_status ps = bq_prepare(&run, I, &sc, R, 0, nullptr, form, st);
     if (ps != PB_OK) return ps;
     PB_CUDA_TRY(bq_launch_encode(run.bjob, d_states, st));
-    PB_CUDA_TRY(bq_launch_cc_half(run.bjob, 0, 0, 0, d_out, st));
-    PB_CUDA_TRY(bq_launch_cc_half(run.bjob, 1, 0, 0, d_out, st));
+    PB_CUDA_TRY(bq_half(&run, 0, 0, 0, d_out, st));
+    PB_CUDA_TRY(bq_half(&run, 1, 0, 0, d_out, st));
     PB_CUDA_TRY(cudaStreamSynchronize(st));
+    int code = 0;
+    PB_CUDA_TRY(cudaMemcpy(&code, run.dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (code) return fail(PB_ETIMEOUT, "a device-side wait timed out (code " + std::to_string(code) + ")");
     return PB_OK;
 }
 

@@ -21,12 +21,12 @@ struct BqDevice {
     const float* hf;        // F32 [2n] (zeros when no field)
     const void* Jraw;       // [n][n] int8 or float, for the exact energy
     const void* hraw;       // [2n] int8 or float, or null
-    // tensor-core operands, [npad][npad] row-major, zero padded
-    int32_t npad;           // n rounded up to the tensor tile (0 if not built)
-    const uint8_t* Jq;      // e4m3 J
+    // tensor-core operands, [n][ldj] row-major (row stride ldj elements, a multiple of 16)
+    int32_t ldj;
+    const uint8_t* Jq;      // e4m3 J (PM1)
     const uint8_t* Jqt;     // e4m3 J^T
-    const uint16_t* Jhi;    // bf16 high part of J
-    const uint16_t* Jlo;    // bf16 residual J - hi
+    const uint16_t* Jhi;    // bf16 high part of J (F32): hi = bf16(J)
+    const uint16_t* Jlo;    // bf16 residual: lo = bf16(J - hi)
     const uint16_t* Jthi;
     const uint16_t* Jtlo;
 };

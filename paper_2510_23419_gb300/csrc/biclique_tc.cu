@@ -1,0 +1,424 @@
+// biclique_tc.cu -- tcgen05 tensor-core field of the biclique p-bit update
+// (arXiv 2510.23419, Sec. 3; update groups Sec. 1.2.2: each side is one colour
+// class, so the fields of a whole side are one dense product J M over
+// replicas).  One CTA computes a 128-row x 256-replica tile of
+//     F[i][r] = sum_j J[i][j] m[r][j] + h_i                      (Eq. 3)
+// with the FP32 accumulator in tensor memory, then applies the p-bit decision
+// (Eq. 2) to it and writes the new spins of the side (and the energy
+// partials of the sweep).
+//
+//  +-1 couplings: A = J in FP8 e4m3, B = spins in e4m3 (+-1 exact),
+//                 tcgen05.mma kind::f8f6f4, exact integer sums in FP32.
+//  real couplings: J = hi + lo with hi = bf16(J), lo = bf16(J - hi); spins
+//                 bf16 +-1; two kind::f16 MMAs per K step into one accumulator.
+//
+// Warp roles: warp 0 issues TMA loads (128-byte swizzle, K-major) into a
+// STAGES-deep ring, warp 1 allocates tensor memory and issues the MMAs,
+// warps 2..5 (one per tensor-memory lane quarter) run the epilogue.  Every
+// mbarrier wait is bounded; on timeout the CTA records an error and still
+// releases its tensor memory.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include "biclique_launch.h"
+#include "biclique_tc.h"
+#include "ea_kernels.cuh"
+
+namespace pb {
+
+namespace {
+
+constexpr int TBM = kBqTcRows;   // rows per tile (tensor-memory lanes)
+constexpr int TBN = kBqTcReps;   // replicas per tile (accumulator columns)
+constexpr int KBYTES = 128;     // K bytes per stage (one 128-byte swizzle row)
+constexpr int kThreads = 192;   // 6 warps
+constexpr uint32_t kWaitLimit = 1u << 26;
+
+template <int KIND>
+struct TcCfg;
+template <>
+struct TcCfg<0> {  // e4m3
+    static constexpr int STAGES = 4;
+    static constexpr int A_BYTES = TBM * KBYTES;
+    static constexpr int B_BYTES = TBN * KBYTES;
+    static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+    static constexpr int KELEM = 128;  // elements per stage
+    static constexpr int KSTEP_BYTES = 32;  // one MMA consumes K = 32 e4m3
+};
+template <>
+struct TcCfg<1> {  // bf16 hi + lo
+    static constexpr int STAGES = 3;
+    static constexpr int A_BYTES = TBM * KBYTES;
+    static constexpr int B_BYTES = TBN * KBYTES;
+    static constexpr int STAGE_BYTES = 2 * A_BYTES + B_BYTES;
+    static constexpr int KELEM = 64;
+    static constexpr int KSTEP_BYTES = 32;  // one MMA consumes K = 16 bf16
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// Bounded wait for the phase with the given parity; returns false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
+{
+    const uint32_t a = smem_u32(bar);
+    for (uint32_t it = 0; it < kWaitLimit; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (it > 64) __nanosleep(64);
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+            smem_u32(dst)),
+        "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
+// 128 bytes, 8-row groups 1024 bytes apart (stride byte offset), version 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFFu);            // start address
+    d |= (uint64_t)(16u >> 4) << 16;                    // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024u >> 4) << 32;                  // stride byte offset
+    d |= (uint64_t)1 << 46;                             // descriptor version
+    d |= (uint64_t)2 << 61;                             // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor: FP32 accumulator, A/B format, both K-major, N, M.
+__host__ __device__ constexpr uint32_t instr_desc(uint32_t ab_format, int M, int N)
+{
+    return (1u << 4)                      // D format: F32
+           | (ab_format << 7)              // A format
+           | (ab_format << 10)             // B format
+           | ((uint32_t)(N >> 3) << 17)    // N / 8
+           | ((uint32_t)(M >> 4) << 24);   // M / 16
+}
+
+template <int KIND>
+__device__ __forceinline__ void mma_issue(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc)
+{
+    if (KIND == 0) {
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
+    } else {
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
+    }
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+// Sum over the 32 lanes of a warp, per column: lane l holds e[0..31] (columns)
+// and ends with the sum of column l in e[0] (31 shuffles).
+__device__ __forceinline__ float warp_transpose_sum(float (&e)[32], int lane)
+{
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        const bool up = lane & o;
+#pragma unroll
+        for (int j = 0; j < o; ++j) {
+            const float send = up ? e[j] : e[j + o];
+            const float keep = up ? e[j + o] : e[j];
+            e[j] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, o);
+        }
+    }
+    return e[0];
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(kThreads, 1)
+    bq_tc_half_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmA2,
+                      const __grid_constant__ CUtensorMap tmB, BqJob job, int side, int s, int decide,
+                      float* fields_out, int* err)
+{
+    using Cfg = TcCfg<KIND>;
+    extern __shared__ unsigned char smem_raw[];
+    // 1024-byte alignment for the 128-byte swizzle
+    unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t full_bar[Cfg::STAGES];
+    __shared__ __align__(8) uint64_t empty_bar[Cfg::STAGES];
+    __shared__ __align__(8) uint64_t acc_bar;
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_fail;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n = job.inst.n;
+    const int i0 = blockIdx.x * TBM;
+    const int r0 = blockIdx.y * TBN;
+    const int nkb = (n + Cfg::KELEM - 1) / Cfg::KELEM;
+
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < Cfg::STAGES; ++q) {
+            mbar_init(&full_bar[q], 1);
+            mbar_init(&empty_bar[q], 1);
+        }
+        mbar_init(&acc_bar, 1);
+        s_fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(TBN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+
+    if (warp == 0) {
+        // ---------------- TMA producer ----------------
+        if (lane == 0) {
+            for (int kb = 0; kb < nkb; ++kb) {
+                const int st = kb % Cfg::STAGES;
+                const uint32_t ph = (uint32_t)(kb / Cfg::STAGES) & 1u;
+                if (!mbar_wait(&empty_bar[st], ph ^ 1u)) {
+                    atomicOr(err, 1);
+                    s_fail = 1;
+                    break;
+                }
+                unsigned char* sa = smem + st * Cfg::STAGE_BYTES;
+                mbar_expect_tx(&full_bar[st], (uint32_t)Cfg::STAGE_BYTES);
+                const int kc = kb * Cfg::KELEM;
+                tma_load_2d(sa, &tmA, &full_bar[st], kc, i0);
+                if (KIND == 1) tma_load_2d(sa + Cfg::A_BYTES, &tmA2, &full_bar[st], kc, i0);
+                tma_load_2d(sa + (KIND == 1 ? 2 : 1) * Cfg::A_BYTES, &tmB, &full_bar[st], kc, r0);
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            constexpr uint32_t idesc = instr_desc(KIND == 0 ? 0u : 1u, TBM, TBN);
+            bool ok = true;
+            for (int kb = 0; kb < nkb && ok; ++kb) {
+                const int st = kb % Cfg::STAGES;
+                const uint32_t ph = (uint32_t)(kb / Cfg::STAGES) & 1u;
+                if (!mbar_wait(&full_bar[st], ph)) {
+                    atomicOr(err, 2);
+                    s_fail = 1;
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t sa = smem_u32(smem + st * Cfg::STAGE_BYTES);
+                const uint32_t sb = sa + (KIND == 1 ? 2 : 1) * Cfg::A_BYTES;
+#pragma unroll
+                for (int k = 0; k < KBYTES / Cfg::KSTEP_BYTES; ++k) {
+                    const uint64_t bd = smem_desc(sb + k * Cfg::KSTEP_BYTES);
+                    mma_issue<KIND>(tmem, smem_desc(sa + k * Cfg::KSTEP_BYTES), bd, idesc, (kb | k) ? 1u : 0u);
+                    if (KIND == 1) mma_issue<KIND>(tmem, smem_desc(sa + Cfg::A_BYTES + k * Cfg::KSTEP_BYTES), bd, idesc, 1u);
+                }
+                mma_commit(&empty_bar[st]);
+            }
+            mma_commit(&acc_bar);
+        }
+    } else {
+        // ---------------- epilogue: 4 warps, one tensor-memory lane quarter each ----------------
+        const int quarter = warp & 3;
+        const int row = quarter * 32 + lane;
+        const int i = i0 + row;
+        const int et = threadIdx.x - 64;  // 0..127
+        const bool ok = mbar_wait(&acc_bar, 0);
+        if (!ok) {
+            atomicOr(err, 4);
+            s_fail = 1;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const bool pm1 = KIND == 0;
+        // stage memory is free once the accumulator is complete: threshold row + reduction buffers
+        uint32_t* stab = reinterpret_cast<uint32_t*>(smem);
+        const size_t tab_bytes = pm1 ? ((size_t)job.nF * 4 + 1023) / 1024 * 1024 : 0;
+        float* red = reinterpret_cast<float*>(smem + tab_bytes);  // [4][TBN], after the threshold row
+        float cexp = 0.0f;
+        if (pm1) {
+            const uint32_t* trow = job.table + (size_t)(s / job.step) * job.nF;
+            for (int f = et; f < job.nF; f += 128) stab[f] = trow[f];
+        } else {
+            cexp = f32_cexp(job.betaf[s / job.step]);
+        }
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+        const bool live = ok && i < n;
+        const float hv = (i < n) ? (pm1 ? (job.inst.h8 ? (float)job.inst.h8[side * n + i] : 0.0f)
+                                        : job.inst.hf[side * n + i])
+                                 : 0.0f;
+        const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16);
+        for (int c = 0; c < TBN / 32; ++c) {
+            float v[32];
+            tmem_ld32(taddr + (uint32_t)(c * 32), v);
+            float e[32];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int rq = r0 + c * 32 + 4 * q;
+                float F[4];
+#pragma unroll
+                for (int b = 0; b < 4; ++b) F[b] = v[4 * q + b] + hv;
+                bool mn[4] = {false, false, false, false};
+                if (live) {
+                    if (fields_out) {
+#pragma unroll
+                        for (int b = 0; b < 4; ++b)
+                            if (rq + b < job.R) fields_out[(size_t)(rq + b) * 2 * n + side * n + i] = F[b];
+                    } else if (decide) {
+                        const U4 w = philox10((uint32_t)i, (uint32_t)s, (uint32_t)(rq >> 2),
+                                              (kTagDecision << 24) | (uint32_t)side, job.key0, job.key1);
+                        const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) {
+                            mn[b] = pm1 ? (ws[b] >= stab[(int)F[b] - job.fmin]) : (decide_f32(ws[b], F[b], cexp) != 0u);
+                            const size_t off = (size_t)(rq + b) * job.ld + i;
+                            if (pm1)
+                                static_cast<uint8_t*>(job.spins[side])[off] = mn[b] ? kE4m3Minus : kE4m3Plus;
+                            else
+                                static_cast<uint16_t*>(job.spins[side])[off] = mn[b] ? kBf16Minus : kBf16Plus;
+                        }
+                    } else {
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) {
+                            const size_t off = (size_t)(rq + b) * job.ld + i;
+                            mn[b] = pm1 ? (static_cast<const uint8_t*>(job.spins[side])[off] & 0x80u) != 0
+                                        : (static_cast<const uint16_t*>(job.spins[side])[off] & 0x8000u) != 0;
+                        }
+                    }
+                }
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    // side 1: -m F (F includes h);  side 0: -h m
+                    const float x = (side == 1) ? F[b] : hv;
+                    e[4 * q + b] = live ? (mn[b] ? x : -x) : 0.0f;
+                }
+            }
+            if (!fields_out) red[quarter * TBN + c * 32 + lane] = warp_transpose_sum(e, lane);
+        }
+        if (!fields_out) {
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            for (int col = et; col < TBN; col += 128) {
+                const float sum = red[col] + red[TBN + col] + red[2 * TBN + col] + red[3 * TBN + col];
+                const size_t off = ((size_t)side * job.nblk + blockIdx.x) * job.Rpad + r0 + col;
+                if (pm1)
+                    static_cast<int32_t*>(job.part)[off] = (int32_t)sum;
+                else
+                    static_cast<float*>(job.part)[off] = sum;
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 1) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TBN));
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+}  // namespace
+
+size_t bq_tc_smem_bytes(int kind)
+{
+    const size_t st = kind == 0 ? (size_t)TcCfg<0>::STAGES * TcCfg<0>::STAGE_BYTES
+                                : (size_t)TcCfg<1>::STAGES * TcCfg<1>::STAGE_BYTES;
+    return st + 1024;  // alignment slack
+}
+
+// 2D row-major [rows][cols] matrix of elem_bytes elements (row stride ld_bytes),
+// loaded as boxes of [box_rows][128 bytes] with the 128-byte swizzle.
+cudaError_t bq_tc_make_map(CUtensorMap* map, const void* base, int elem_bytes, uint64_t cols, uint64_t rows,
+                           uint64_t ld_bytes, int box_rows)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = get_encoder();
+    if (!enc) return cudaErrorNotSupported;
+    const CUtensorMapDataType dt = elem_bytes == 1 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    const cuuint64_t dims[2] = {cols, rows};
+    const cuuint64_t strides[1] = {ld_bytes};
+    const cuuint32_t box[2] = {(cuuint32_t)(128 / elem_bytes), (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(map, dt, 2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t bq_tc_set_smem()
+{
+    cudaError_t e = cudaFuncSetAttribute(bq_tc_half_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)bq_tc_smem_bytes(0));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(bq_tc_half_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)bq_tc_smem_bytes(1));
+}
+
+cudaError_t bq_launch_tc_half(const BqTcMaps& maps, const BqJob& job, int side, int s, int decide, float* fields_out,
+                              int* err, cudaStream_t st)
+{
+    const int kind = job.inst.jtype == PB_J_PM1_I8 ? 0 : 1;
+    const size_t smem = bq_tc_smem_bytes(kind);
+    dim3 grid((unsigned)((job.inst.n + TBM - 1) / TBM), (unsigned)(job.Rpad / TBN));
+    const CUtensorMap& A = side == 0 ? maps.a[0] : maps.a[2];
+    const CUtensorMap& A2 = side == 0 ? maps.a[1] : maps.a[3];
+    const CUtensorMap& B = maps.b[1 - side];
+    if (kind == 0)
+        bq_tc_half_kernel<0><<<grid, kThreads, smem, st>>>(A, A2, B, job, side, s, decide, fields_out, err);
+    else
+        bq_tc_half_kernel<1><<<grid, kThreads, smem, st>>>(A, A2, B, job, side, s, decide, fields_out, err);
+    return cudaGetLastError();
+}
+
+}  // namespace pb

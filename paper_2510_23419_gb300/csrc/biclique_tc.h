@@ -1,0 +1,28 @@
+// biclique_tc.h -- host interface of the tcgen05 biclique field kernel.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "biclique_launch.h"
+
+namespace pb {
+
+// TMA descriptors of one run: a[0], a[1] = J (e4m3, or bf16 hi and lo),
+// a[2], a[3] = J^T; b[0], b[1] = spins of side A and side B.
+struct BqTcMaps {
+    CUtensorMap a[4];
+    CUtensorMap b[2];
+};
+
+constexpr int kBqTcRows = 128;   // rows of a tile (tensor-memory lanes)
+constexpr int kBqTcReps = 256;   // replicas of a tile (accumulator columns)
+
+size_t bq_tc_smem_bytes(int kind);
+cudaError_t bq_tc_set_smem();
+cudaError_t bq_tc_make_map(CUtensorMap* map, const void* base, int elem_bytes, uint64_t cols, uint64_t rows,
+                           uint64_t ld_bytes, int box_rows);
+cudaError_t bq_launch_tc_half(const BqTcMaps& maps, const BqJob& job, int side, int s, int decide, float* fields_out,
+                              int* err, cudaStream_t st);
+
+}  // namespace pb

@@ -432,7 +432,14 @@ static pb_status wait_run(pb_run* run, int32_t timeout_ms)
     const auto t0 = std::chrono::steady_clock::now();
     for (;;) {
         cudaError_t e = cudaEventQuery(run->ev_stop);
-        if (e == cudaSuccess) return PB_OK;
+        if (e == cudaSuccess) {
+            if (run->dev_err) {
+                int code = 0;
+                PB_CUDA_TRY(cudaMemcpy(&code, run->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+                if (code) return fail(PB_ETIMEOUT, "a device-side wait of the run timed out (code " + std::to_string(code) + ")");
+            }
+            return PB_OK;
+        }
         if (e != cudaErrorNotReady) return cuda_fail(e, "run failed");
         if (timeout_ms >= 0) {
             const auto el = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0);
@@ -703,6 +710,12 @@ void pb_run_destroy(pb_run* run)
 
 pb_status pb_fields(pb_instance* I, const int8_t* states, int32_t R, float* fields_out, int64_t out_bytes, void* stream)
 {
+    return pb_fields_ex(I, states, R, PB_FORM_AUTO, fields_out, out_bytes, stream);
+}
+
+pb_status pb_fields_ex(pb_instance* I, const int8_t* states, int32_t R, int32_t form, float* fields_out,
+                       int64_t out_bytes, void* stream)
+{
     if (!I || !states || !fields_out) return fail(PB_EINVAL, "null argument");
     if (R < 1) return fail(PB_EINVAL, "R must be >= 1");
     const int64_t n = (int64_t)R * I->N;
@@ -717,7 +730,7 @@ pb_status pb_fields(pb_instance* I, const int8_t* states, int32_t R, float* fiel
     if (I->topo == PB_TOPO_EA3D)
         PB_CUDA_TRY(ea_launch_fields(I->ea, dm.as<int8_t>(), R, df.as<float>(), st));
     else {
-        pb_status ps = bq_fields(I, dm.as<int8_t>(), R, df.as<float>(), st);
+        pb_status ps = bq_fields(I, dm.as<int8_t>(), R, form, df.as<float>(), st);
         if (ps != PB_OK) return ps;
     }
     PB_CUDA_TRY(cudaMemcpyAsync(fields_out, df.p, (size_t)n * 4, cudaMemcpyDeviceToHost, st));

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "biclique_launch.h"
+#include "biclique_tc.h"
 #include "ea_launch.h"
 #include "pb_common.h"
 
@@ -54,7 +55,7 @@ struct pb_instance {
     pb::EaDevice ea{};
     // biclique
     pb::BqDevice bq{};
-    pb::DevBuf bq_bufs[8];
+    pb::DevBuf bq_bufs[12];
 };
 
 namespace pb {
@@ -83,6 +84,8 @@ struct pb_run {
     pb::EaJob job{};
     // biclique
     pb::BqJob bjob{};
+    pb::BqTcMaps maps{};
+    int* dev_err = nullptr;  // device error word of bounded waits (null if the form has none)
     pb::DevBuf table, betaf, best_words, final_words, E_best_i, E_best_f, best_sweep, hit_sweep;
     pb::DevBuf best_pm, final_pm, E_out;  // readout: [R][N] x2, [2R] doubles
     pb::DevBuf extra[8];
@@ -104,5 +107,5 @@ uint32_t threshold_u32(double beta, double F);
 pb_status bq_build(pb_instance* I, const pb_instance_desc* d, cudaStream_t st);
 pb_status bq_anneal(pb_run* run, pb_instance* I, const pb_schedule* sc, int R, uint64_t seed,
                     const pb_anneal_opts* opts, cudaStream_t st);
-pb_status bq_fields(pb_instance* I, const int8_t* d_states, int R, float* d_out, cudaStream_t st);
+pb_status bq_fields(pb_instance* I, const int8_t* d_states, int R, int form, float* d_out, cudaStream_t st);
 }  // namespace pb

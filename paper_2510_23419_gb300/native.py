@@ -87,6 +87,7 @@ def load():
         "pb_run_kernel_ms": ([P, P], st),
         "pb_run_destroy": ([P], None),
         "pb_fields": ([P, P, I32, P, I64, P], st),
+        "pb_fields_ex": ([P, P, I32, I32, P, I64, P], st),
         "pb_anneal_ea_noalloc": ([I32, P, P, I32, U64, P, P, P, P, P, P], st),
     }
     for name, (args, res) in sig.items():
@@ -265,10 +266,14 @@ def pb_run_destroy(run):
 
 
 def pb_fields(inst, states: np.ndarray, stream=None) -> np.ndarray:
+    return pb_fields_ex(inst, states, PB_FORM_AUTO, stream)
+
+
+def pb_fields_ex(inst, states: np.ndarray, form: int, stream=None) -> np.ndarray:
     states = np.ascontiguousarray(states, dtype=np.int8)
     R, N = states.shape
     out = np.empty((R, N), np.float32)
-    _check(load().pb_fields(inst, _ptr(states), R, _ptr(out), out.nbytes, _stream(stream)))
+    _check(load().pb_fields_ex(inst, _ptr(states), R, form, _ptr(out), out.nbytes, _stream(stream)))
     return out
 
 

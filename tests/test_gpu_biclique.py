@@ -14,7 +14,7 @@ import synth_inputs as syn
 
 pytestmark = pytest.mark.gpu
 
-FORMS = ["cudacore"]
+FORMS = ["cudacore", "tensor"]
 
 
 @pytest.fixture(scope="module")
@@ -46,6 +46,8 @@ CASES = [
     (20, 3, 40, 0, 0.35, 3.5, 2, 4),
     (130, 70, 6, 0, 0.02, 0.3, 0, 5),
     (9, 1, 0, 0, 0.1, 0.1, 0, 6),
+    (256, 300, 8, 1, 0.01, 0.2, 0, 7),
+    (200, 20, 10, 0, 0.005, 0.1, 3, 8),
 ]
 
 
@@ -73,14 +75,14 @@ def test_ferromagnet_closed_form(pb, form):
 
 
 @pytest.mark.parametrize("form", FORMS)
-def test_f32_fields(pb, orc, form):
-    n = 96
+@pytest.mark.parametrize("n", [96, 300])
+def test_f32_fields(pb, orc, form, n):
     J = syn.biclique_couplings(n, "gauss", 11)
     h = syn.real_fields(2 * n, 0.5, 12)
     inst = pb.pb_create_instance(pb.PB_TOPO_BICLIQUE, J, h, n=n)
     try:
         m = syn.states(5, 2 * n, 13)
-        F = pb.pb_fields(inst, m)
+        F = pb.pb_fields_ex(inst, m, _form(pb, form))
     finally:
         pb.pb_instance_destroy(inst)
     eu, ev, _ = orc.biclique_graph(n)
@@ -108,3 +110,35 @@ def test_f32_energies_and_ensemble(pb, orc, form):
     eg, eo = g["final_E"] / (2 * n), o["final_E"] / (2 * n)
     se = math.sqrt(eg.var(ddof=1) / R + eo.var(ddof=1) / R)
     assert abs(eg.mean() - eo.mean()) <= 3 * se + 1e-12
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_pm1_fields_exact(pb, orc, form):
+    n = 160
+    J = syn.biclique_couplings(n, "pm1", 31)
+    h = syn.int_fields(2 * n, 4, 32)
+    inst = pb.pb_create_instance(pb.PB_TOPO_BICLIQUE, J, h, n=n)
+    try:
+        m = syn.states(3, 2 * n, 33)
+        F = pb.pb_fields_ex(inst, m, _form(pb, form))
+    finally:
+        pb.pb_instance_destroy(inst)
+    eu, ev, _ = orc.biclique_graph(n)
+    for r in range(3):
+        assert np.array_equal(F[r].astype(np.float64), orc.fields(eu, ev, J.astype(float).reshape(-1), h.astype(float), m[r]))
+
+
+def test_tensor_sampled_large(pb, orc):
+    """n = 2048, 512 replicas (two replica tiles), 30 sweeps on tensor cores; three
+    replicas replayed one by one on the oracle, bit-exact."""
+    n, R, S = 2048, 512, 30
+    J = pb.pb_generate_biclique(n, pb.PB_DIST_PM1, 5)
+    sc = pb.make_schedule(pb.PB_SCHED_LINEAR, S, 0.35, 3.5)
+    g = _gpu(pb, n, J, None, sc, R, 9, "tensor")
+    ob = orc.schedule(orc.SCHED_LINEAR, 0.35, 3.5, S)
+    eu, ev, col = orc.biclique_graph(n)
+    Jd = J.astype(np.float64).reshape(-1)
+    for r in (0, 257, 511):
+        o = orc.anneal(eu, ev, Jd, None, col, ob, 1, 9, r_first=r)
+        assert np.array_equal(o["final_state"][0], g["final_state"][r])
+        assert o["best_E"][0] == g["best_E"][r] and o["best_sweep"][0] == g["best_sweep"][r]
