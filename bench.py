@@ -45,6 +45,30 @@ CONFIG = {
 }
 
 
+def profiled_traffic():
+    """DRAM bytes of one bench launch of the resident kernel, from the committed ncu
+    summary, if the kernel sources are unchanged since that capture (else None)."""
+    import glob
+    import hashlib
+    import re
+    csrc = os.path.join(ROOT, "paper_2510_23419_gb300", "csrc")
+    files = [os.path.join(csrc, f) for f in ("ea.cu", "ea_fast.cuh", "ea_kernels.cuh", "ea_launch.h", "pb_common.h")]
+    try:
+        h = hashlib.sha256()
+        for f in files:
+            with open(f, "rb") as fh:
+                h.update(fh.read())
+        with open(os.path.join(ROOT, "profiles", "ea_resident_batch_dram.md")) as fh:
+            txt = fh.read()
+    except OSError:
+        return None
+    stamp = re.search(r"first 16 hex digits\): `([0-9a-f]{16})`", txt)
+    val = re.search(r"traffic_bytes_per_launch: (\d+)", txt)
+    if not stamp or not val or stamp.group(1) != h.hexdigest()[:16]:
+        return None
+    return int(val.group(1))
+
+
 def updates_per_step():
     return sum((L ** 3) * S_SWEEPS * R_REPLICAS for L, _, _ in JOBS)
 
@@ -70,6 +94,10 @@ class ClockSampler:
             self.thread.start()
         except (FileNotFoundError, OSError):
             self.proc = None
+            return
+        t0 = time.time()  # let the sampler start up before the timed region
+        while not self.lines and time.time() - t0 < 5.0:
+            time.sleep(0.05)
 
     def _read(self):
         for line in self.proc.stdout:
@@ -141,6 +169,40 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------- small profiling cases
+CASES = {
+    # name: (topology, L or n, law, replicas, sweeps, form)
+    "ea-L32-pm1-small": ("ea", 32, "pm1", 608, 50, "resident"),
+    "ea-L32-gauss-small": ("ea", 32, "gauss", 608, 50, "resident"),
+    "ea-L16-pm1-small": ("ea", 16, "pm1", 2432, 50, "resident"),
+}
+
+
+def run_case(name):
+    """One launch of the hot-path kernel on a small case (152 tiles: one wave), for ncu."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2510_23419_gb300 import native as pb
+    topo, size, law, R, S, form = CASES[name]
+    dist = {"pm1": pb.PB_DIST_PM1, "gauss": pb.PB_DIST_GAUSS, "unif": pb.PB_DIST_UNIF}[law]
+    forms = {"resident": pb.PB_FORM_RESIDENT, "plain": pb.PB_FORM_PLAIN, "cudacore": pb.PB_FORM_CUDACORE,
+             "tensor": pb.PB_FORM_TENSOR}
+    if topo == "ea":
+        J = pb.pb_generate_ea(size, dist, 3)
+        inst = pb.pb_create_instance(pb.PB_TOPO_EA3D, J, None, L=size)
+    else:
+        J = pb.pb_generate_biclique(size, dist, 3)
+        inst = pb.pb_create_instance(pb.PB_TOPO_BICLIQUE, J, None, n=size)
+    sc = pb.make_schedule(pb.PB_SCHED_GEOMETRIC, S, 0.1, 5.0)
+    run = pb.pb_anneal(inst, sc, R, 7, pb.make_opts(forms[form]))
+    ms = pb.pb_run_kernel_ms(run)
+    torch.cuda.synchronize()
+    print(json.dumps({"case": name, "kernel_ms": ms}))
+    pb.pb_run_destroy(run)
+    pb.pb_instance_destroy(inst)
+
+
 # --------------------------------------------------------------- ours
 def main():
     ap = argparse.ArgumentParser()
@@ -150,7 +212,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-form comparison run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--case", default=None, choices=sorted(CASES),
+                    help="run one small launch of a hot-path kernel (for ncu) and exit")
     args = ap.parse_args()
+    if args.case:
+        run_case(args.case)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
@@ -271,8 +338,10 @@ def main():
     # the high and low halves as two IMAD issues at 64 IMAD/clk/SM: 6.4 updates/clk/SM
     alu_peak = 152 * 64.0 / 10.0 * sm_max * 1e6 / 1e9          # Gupdate/s
     hbm = float(peaks.get("hbm_gbs", 6800.0))
+    traffic = profiled_traffic()
     roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Gupdate/s",
-                "frac": achieved / alu_peak, "traffic": None,
+                "frac": achieved / alu_peak, "traffic": traffic,
+                "traffic_source": "profiles/ea_resident_batch_dram.md (ncu dram__bytes_read+write, one full launch)",
                 "peak_source": "derived: 152 SMs x 64 IMAD/clk x max SM clock / 10 IMAD per update (Philox)",
                 "kernel": "ea_resident_kernel", "kernel_ms": k_ms,
                 "hbm_equiv": {"bytes_per_update": 2, "achieved_gbs": achieved * 2, "peak_gbs": hbm,

@@ -172,7 +172,8 @@ __device__ void ea_tile(const EaJob& job, int tile, unsigned char* smem)
         const int c = ck >= half ? 1 : 0;
         const int k = ck - c * half;
         const U4 r = philox10((uint32_t)k, 0u, (uint32_t)(tile * WT + w2), (kTagInit << 24) | (uint32_t)c, key0, key1);
-        sp[j] = (r.x >> 31) | ((r.y >> 31) << 8) | ((r.z >> 31) << 16) | ((r.w >> 31) << 24);
+        sp[j] = (JT == PB_J_PM1_I8) ? ((r.x >> 31) | ((r.y >> 31) << 8) | ((r.z >> 31) << 16) | ((r.w >> 31) << 24))
+                                    : f32_word(r.x >> 31, r.y >> 31, r.z >> 31, r.w >> 31);
     }
 
     auto build_table = [&](int s, int buf) {
@@ -264,15 +265,15 @@ __device__ void ea_tile(const EaJob& job, int tile, unsigned char* smem)
                     for (int b = 0; b < 4; ++b) F[b] = ea_field_f32(jv, hv, nb, b);
                     if (decide) {
                         const U4 r = philox10((uint32_t)k, (uint32_t)s, g.tq, c3, key0, key1);
-                        snew = decide_f32(r.x, F[0], cexp) | (decide_f32(r.y, F[1], cexp) << 8) |
-                               (decide_f32(r.z, F[2], cexp) << 16) | (decide_f32(r.w, F[3], cexp) << 24);
+                        snew = f32_word(decide_f32(r.x, F[0], cexp), decide_f32(r.y, F[1], cexp),
+                                        decide_f32(r.z, F[2], cexp), decide_f32(r.w, F[3], cexp));
                         own[kw] = snew;
                     } else {
                         snew = own[kw];
                     }
 #pragma unroll
                     for (int b = 0; b < 4; ++b) {
-                        const bool dn = (snew >> (8 * b)) & 1u;  // m = -1
+                        const bool dn = f32_minus(snew, b);  // m = -1
                         if (c == 1)
                             ef[b] += dn ? F[b] : -F[b];           // -m F
                         else if (job.inst.has_h)
@@ -496,9 +497,8 @@ __global__ void __launch_bounds__(256) ea_plain_half_kernel(EaJob job, int c, in
         const float jv[6] = {ja.x, ja.y, ja.z, ja.w, jb.x, jb.y};
         const float hv = __ldg(job.inst.hf + site);
         const float cexp = f32_cexp(job.betaf[s / job.step]);
-        snew = decide_f32(r.x, ea_field_f32(jv, hv, nb, 0), cexp) | (decide_f32(r.y, ea_field_f32(jv, hv, nb, 1), cexp) << 8) |
-               (decide_f32(r.z, ea_field_f32(jv, hv, nb, 2), cexp) << 16) |
-               (decide_f32(r.w, ea_field_f32(jv, hv, nb, 3), cexp) << 24);
+        snew = f32_word(decide_f32(r.x, ea_field_f32(jv, hv, nb, 0), cexp), decide_f32(r.y, ea_field_f32(jv, hv, nb, 1), cexp),
+                        decide_f32(r.z, ea_field_f32(jv, hv, nb, 2), cexp), decide_f32(r.w, ea_field_f32(jv, hv, nb, 3), cexp));
     }
     job.final_words[(size_t)c * half * WT + j] = snew;
 }
@@ -514,7 +514,9 @@ __global__ void __launch_bounds__(256) ea_plain_init_kernel(EaJob job)
     const int c = ck >= half ? 1 : 0;
     const int k = (int)(ck - (long long)c * half);
     const U4 r = philox10((uint32_t)k, 0u, (uint32_t)w, (kTagInit << 24) | (uint32_t)c, job.key0, job.key1);
-    job.final_words[j] = (r.x >> 31) | ((r.y >> 31) << 8) | ((r.z >> 31) << 16) | ((r.w >> 31) << 24);
+    job.final_words[j] = (job.inst.jtype == PB_J_PM1_I8)
+                             ? ((r.x >> 31) | ((r.y >> 31) << 8) | ((r.z >> 31) << 16) | ((r.w >> 31) << 24))
+                             : f32_word(r.x >> 31, r.y >> 31, r.z >> 31, r.w >> 31);
 }
 
 // One block per word column w (4 replicas): energy of the current state, best
@@ -573,11 +575,11 @@ __global__ void __launch_bounds__(256) ea_plain_energy_kernel(EaJob job, int s, 
 #pragma unroll
                     for (int b = 0; b < 4; ++b) {
                         const float F = ea_field_f32(jv, hv, nb, b);
-                        ef[b] += ((sv >> (8 * b)) & 1u) ? F : -F;
+                        ef[b] += f32_minus(sv, b) ? F : -F;
                     }
                 } else if (job.inst.has_h) {
 #pragma unroll
-                    for (int b = 0; b < 4; ++b) ef[b] += ((sv >> (8 * b)) & 1u) ? hv : -hv;
+                    for (int b = 0; b < 4; ++b) ef[b] += f32_minus(sv, b) ? hv : -hv;
                 }
             }
         }
@@ -656,7 +658,8 @@ __global__ void __launch_bounds__(256) ea_readout_kernel(EaJob job, const uint32
     const int w = (r / 4) % WT;
     const int b = r & 3;
     const uint32_t v = words[(((size_t)tile * 2 + c) * half + k) * WT + w];
-    out[j] = ((v >> (8 * b)) & 1u) ? (int8_t)-1 : (int8_t)1;
+    const uint32_t minus = (job.inst.jtype == PB_J_PM1_I8) ? ((v >> (8 * b)) & 1u) : f32_minus(v, b);
+    out[j] = minus ? (int8_t)-1 : (int8_t)1;
 }
 
 // E = -sum_{d,i} J[d][i] m_i m_{i+d} - sum_i h_i m_i, one block per replica;
@@ -730,7 +733,8 @@ __global__ void __launch_bounds__(256) ea_fields_kernel(EaDevice inst, const int
         const int row = kk / (L >> 1), qq = kk - row * (L >> 1);
         const int yy = row % L, zz = row / L;
         const int xx = 2 * qq + ((1 - c + yy + zz) & 1);
-        nb[b] = (mr[xx + L * (yy + L * zz)] < 0) ? 1u : 0u;
+        const bool minus = mr[xx + L * (yy + L * zz)] < 0;
+        nb[b] = (inst.jtype == PB_J_PM1_I8) ? (minus ? 1u : 0u) : (minus ? 0xBFu : 0x3Fu);
     }
     if (inst.jtype == PB_J_PM1_I8) {
         const uint32_t X = ea_pattern(nb[0], nb[1], nb[2], nb[3], nb[4], nb[5], inst.jbits[c * half + k]);
@@ -755,7 +759,7 @@ int ea_resident_pick_wt(int L, int jtype, int has_h, int nF, int cap_words)
     const int h2 = L / 2;
     int best = 0;
     for (int wt = 1; wt <= kResidentMaxWT; wt *= 2) {
-        if ((long long)h2 * L * wt > kResidentThreads) break;
+        if ((long long)h2 * L * wt > kResidentThreads / 2) break;
         if (ea_resident_smem(L, wt, jtype, has_h, nF) > kResidentSmemLimit) break;
         best = wt;
         if (wt >= cap_words) break;

@@ -1,14 +1,14 @@
 // ea_fast.cuh -- compile-time-shaped resident tile of the EA p-bit update
 // (arXiv 2510.23419: Eqs. 2-3, update groups of Sec. 1.2.2, classical
 // annealing of Sec. 1.3.1) for cubes whose colour-class columns exactly fill
-// the CTA: one thread owns the column (q, y, w) of both colours, i.e. the
-// sites x = 2q + parity, fixed y, all z, for 4 replicas.
+// half the CTA: thread (cw, zp) owns the column (q, y, w) for z = zp mod 2 of
+// both colours, i.e. the sites x = 2q + parity, fixed y, every other z, for 4
+// replicas.
 //
 // Same arithmetic, random words and outputs as the generic tile; what changes
 // is only the instruction budget:
-//  * z is unrolled, so every neighbour word is a shared-memory load at
-//    [per-thread base + immediate]; periodic wrap in z is resolved at compile
-//    time, in x and y it lives in the per-thread bases;
+//  * x and y neighbours (and their periodic wrap) are per-thread bases, the
+//    two z-wrapping sites are peeled out of the z loop;
 //  * the Philox round keys live in registers, and the first round's products
 //    of counter words 1..3 (sweep, replica quad, colour) are hoisted;
 //  * the thread's bond-sign bytes live in registers (one PRMT broadcasts a
@@ -76,10 +76,11 @@ constexpr int kResidentWarps = kResidentThreads / 32;
 template <int L, int WT, int JT>
 struct EaFastTile {
     static constexpr int T = kResidentThreads;
+    static constexpr int CWN = kResidentThreads / 2;  // column-words: two threads (z parities) per column
     static constexpr int h2 = L / 2;
     static constexpr int half = h2 * L * L;
     static constexpr int N = 2 * half;
-    static_assert(h2 * L * WT == T, "fast tile: one column-word per thread");
+    static_assert(h2 * L * WT == CWN, "fast tile: one column-word per thread pair");
     static constexpr int SZ = L * h2 * WT;  // words between z planes of a class array
     static constexpr int CLS = half * WT;   // words of one class array
     static constexpr int NREP = 4 * WT;
@@ -87,7 +88,7 @@ struct EaFastTile {
     static constexpr bool PM1 = JT == PB_J_PM1_I8;
 
     const EaJob& job;
-    int tile, t, lane, warp, w, q, y, base0, oyp, oym;
+    int tile, t, lane, warp, w, q, y, zp, base0, oyp, oym;
     uint32_t tq;
     uint32_t* sp;
     int32_t* spart_i;
@@ -95,7 +96,7 @@ struct EaFastTile {
     uint8_t* sflag;
     uint32_t* s_tab;
     RoundKeys rk;
-    const uint32_t* sjb4;  // bond-sign bytes, word [(c*L/4 + z/4)*T + t] byte z%4
+    const uint32_t* sjb4;  // bond-sign bytes of the thread's sites: word [(c*L/8 + zz/4)*T + t] byte zz%4, z = zp + 2 zz
 
     __device__ __forceinline__ EaFastTile(const EaJob& j, int tile_, unsigned char* smem, uint32_t* tab)
         : job(j), tile(tile_), s_tab(tab)
@@ -103,9 +104,11 @@ struct EaFastTile {
         t = threadIdx.x;
         lane = t & 31;
         warp = t >> 5;
-        w = t % WT;
-        q = (t / WT) % h2;
-        y = t / (WT * h2);
+        const int cw = t % CWN;
+        zp = t / CWN;
+        w = cw % WT;
+        q = (cw / WT) % h2;
+        y = cw / (WT * h2);
         sp = reinterpret_cast<uint32_t*>(smem);
         spart_i = reinterpret_cast<int32_t*>(sp + N * WT);
         spart_f = reinterpret_cast<float*>(spart_i);
@@ -121,14 +124,14 @@ struct EaFastTile {
 #pragma unroll 1
             for (int c = 0; c < 2; ++c)
 #pragma unroll 1
-                for (int z4 = 0; z4 < L / 4; ++z4) {
+                for (int z4 = 0; z4 < L / 8; ++z4) {
                     uint32_t v = 0;
 #pragma unroll
                     for (int b = 0; b < 4; ++b) {
-                        const int z = 4 * z4 + b;
+                        const int z = zp + 2 * (4 * z4 + b);
                         v |= (uint32_t)job.inst.jbits[c * half + q + h2 * (y + L * z)] << (8 * b);
                     }
-                    jw[(c * (L / 4) + z4) * T + t] = v;
+                    jw[(c * (L / 8) + z4) * T + t] = v;
                 }
         }
     }
@@ -138,11 +141,12 @@ struct EaFastTile {
 #pragma unroll
         for (int c = 0; c < 2; ++c)
 #pragma unroll 4
-            for (int z = 0; z < L; ++z) {
+            for (int z = zp; z < L; z += 2) {
                 const int k = q + h2 * (y + L * z);
                 const U4 r = philox10((uint32_t)k, 0u, tq, (kTagInit << 24) | (uint32_t)c, job.key0, job.key1);
                 sp[c * CLS + base0 + z * SZ] =
-                    (r.x >> 31) | ((r.y >> 31) << 8) | ((r.z >> 31) << 16) | ((r.w >> 31) << 24);
+                    PM1 ? ((r.x >> 31) | ((r.y >> 31) << 8) | ((r.z >> 31) << 16) | ((r.w >> 31) << 24))
+                        : f32_word(r.x >> 31, r.y >> 31, r.z >> 31, r.w >> 31);
             }
     }
 
@@ -162,11 +166,11 @@ struct EaFastTile {
     {
         const uint32_t* o = sp + (1 - C) * CLS;
         uint32_t* own = sp + C * CLS;
+        const int zp = this->zp;
         const PhiloxPre pre = philox_pre((uint32_t)s, tq, (kTagDecision << 24) | (uint32_t)C, rk);
         float cexp = 0.0f;
         if constexpr (!PM1) cexp = f32_cexp(job.betaf[s / job.step]);
-#pragma unroll
-        for (int zp = 0; zp < 2; ++zp) {
+        {
             const int px = (C + y + zp) & 1;
             const int oxp = (px ? ((q + 1 == h2) ? -(h2 - 1) : 1) : 0) * WT;
             const int oxm = (px ? 0 : ((q == 0) ? (h2 - 1) : -1)) * WT;
@@ -195,7 +199,8 @@ struct EaFastTile {
         const uint32_t n4 = bz[zup * SZ], n5 = bz[zdn * SZ];
         uint32_t snew;
         if constexpr (PM1) {
-            const uint32_t jb = __byte_perm(jword<C>(z >> 2), 0u, (uint32_t)(z & 3) * 0x1111u);
+            const int zz = z >> 1;
+            const uint32_t jb = __byte_perm(jword<C>(zz >> 2), 0u, (uint32_t)(zz & 3) * 0x1111u);
             const uint32_t X = ((n0 << 2) | (n1 << 3) | (n2 << 4) | (n3 << 5) | (n4 << 6) | (n5 << 7)) ^ jb;
             if constexpr (DECIDE) {
                 const U4 r = philox_c0((uint32_t)k, pre, rk);
@@ -223,19 +228,19 @@ struct EaFastTile {
             for (int b = 0; b < 4; ++b) F[b] = ea_field_f32(jv, hv, nb, b);
             if constexpr (DECIDE) {
                 const U4 r = philox_c0((uint32_t)k, pre, rk);
-                snew = decide_f32(r.x, F[0], cexp) + decide_f32(r.y, F[1], cexp) * 0x100u +
-                       decide_f32(r.z, F[2], cexp) * 0x10000u + decide_f32(r.w, F[3], cexp) * 0x1000000u;
+                snew = f32_word(decide_f32(r.x, F[0], cexp), decide_f32(r.y, F[1], cexp), decide_f32(r.z, F[2], cexp),
+                                decide_f32(r.w, F[3], cexp));
                 own[base0 + z * SZ] = snew;
             } else {
                 snew = own[base0 + z * SZ];
             }
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
-                const bool dn = (snew >> (8 * b)) & 1u;
+                const float m = f32_sign(snew, b);  // -m F (class 1), -h m (class 0)
                 if (C == 1)
-                    ef[b] += dn ? F[b] : -F[b];
+                    ef[b] = fmaf(-m, F[b], ef[b]);
                 else if (job.inst.has_h)
-                    ef[b] += dn ? hv : -hv;
+                    ef[b] = fmaf(-m, hv, ef[b]);
             }
         }
     }
@@ -244,7 +249,7 @@ struct EaFastTile {
     template <int C>
     __device__ __forceinline__ uint32_t jword(int z4) const
     {
-        return sjb4[(C * (L / 4) + z4) * T + t];
+        return sjb4[(C * (L / 8) + z4) * T + t];
     }
 
     __device__ __forceinline__ void partials(uint32_t uacc, const float (&ef)[4])
@@ -306,7 +311,7 @@ struct EaFastTile {
             uint32_t* dst = gdst + ((size_t)tile * 2 + c) * CLS + base0;
             const uint32_t* src = sp + c * CLS + base0;
 #pragma unroll 4
-            for (int z = 0; z < L; ++z) {
+            for (int z = zp; z < L; z += 2) {
                 const uint32_t v = src[z * SZ];
                 if (mask == 0xFFFFFFFFu)
                     dst[z * SZ] = v;
@@ -387,7 +392,7 @@ __device__ __forceinline__ void ea_tile_fast(const EaJob& job, int tile, unsigne
     tl.run();
 }
 
-// Fast-tile shapes: (L, WT) with (L/2) L WT == kResidentThreads.
+// Fast-tile shapes: (L, WT) with (L/2) L WT == kResidentThreads / 2.
 __host__ __device__ constexpr bool ea_fast_shape(int L, int WT)
 {
     return (L == 32 && WT == 1) || (L == 16 && WT == 4) || (L == 8 && WT == 16);

@@ -54,16 +54,28 @@ __device__ __forceinline__ uint32_t decide_f32(uint32_t r, float F, float cexp)
 
 __device__ __forceinline__ float f32_cexp(float beta) { return -2.0f * beta * 1.4426950408889634f; }
 
+// F32 spin words: byte b is the top byte of the float +-1.0 of replica b
+// (0x3F <=> m = +1, 0xBF <=> m = -1), so one byte permute yields the spin as
+// a float.  (+-1 instances use bytes 0 / 1, see above.)
+__device__ __forceinline__ float f32_sign(uint32_t n, int b)
+{
+    return __uint_as_float(__byte_perm(n, 0x3F800000u, 0x0654u | ((uint32_t)b << 12)));
+}
+// spin word from four "minus" bits (1 <=> m = -1)
+__device__ __forceinline__ uint32_t f32_word(uint32_t s0, uint32_t s1, uint32_t s2, uint32_t s3)
+{
+    return 0x3F3F3F3Fu | (s0 << 7) | (s1 << 15) | (s2 << 23) | (s3 << 31);
+}
+__device__ __forceinline__ uint32_t f32_minus(uint32_t n, int b) { return (n >> (8 * b + 7)) & 1u; }
+
 // FP32 local field of replica b (byte b of the neighbour words), Eq. 3, in the
-// fixed order h + (+x) + (-x) + (+y) + (-y) + (+z) + (-z).
+// fixed order h + (+x) + (-x) + (+y) + (-y) + (+z) + (-z); each term is one
+// fused multiply-add by the exact +-1.0, i.e. the rounded sum F + (+-J).
 __device__ __forceinline__ float ea_field_f32(const float (&jv)[6], float h, const uint32_t (&n)[6], int b)
 {
     float F = h;
 #pragma unroll
-    for (int k = 0; k < 6; ++k) {
-        const bool neg = (n[k] >> (8 * b)) & 1u;
-        F += neg ? -jv[k] : jv[k];
-    }
+    for (int k = 0; k < 6; ++k) F = fmaf(jv[k], f32_sign(n[k], b), F);
     return F;
 }
 

@@ -48,26 +48,26 @@ __host__ __device__ inline size_t ea_resident_smem(int L, int WT, int jtype, int
     }
     const int tabw = (jtype == PB_J_PM1_I8) ? (has_h ? nF : 64) : 0;
     b += (size_t)2 * ((tabw + 3) / 4 * 4) * 4;           // double-buffered threshold row
-    b += (size_t)(512 / 32) * 4 * WT * 4;                // per-warp energy partials
-    if (jtype == PB_J_PM1_I8 && has_h) b += (size_t)(512 / 32) * 4 * WT * 4;  // per-warp h.m partials
+    b += (size_t)(1024 / 32) * 4 * WT * 4;               // per-warp energy partials
+    if (jtype == PB_J_PM1_I8 && has_h) b += (size_t)(1024 / 32) * 4 * WT * 4;  // per-warp h.m partials
     b += (size_t)4 * WT;                                 // improved flags
-    // compile-time-shaped tiles keep their bond bytes as [2][L/4][threads] words
+    // compile-time-shaped tiles keep their bond bytes as [2][L/8][threads] words
     const bool fast = !has_h && ((L == 32 && WT == 1) || (L == 16 && WT == 4) || (L == 8 && WT == 16));
     if (fast && jtype == PB_J_PM1_I8) {
-        const size_t f = N * (size_t)WT * 4 + (size_t)(512 / 32) * 4 * WT * 4 + 128 + (size_t)2 * (L / 4) * 512 * 4;
+        const size_t f = N * (size_t)WT * 4 + (size_t)(1024 / 32) * 4 * WT * 4 + 128 + (size_t)2 * (L / 8) * 1024 * 4;
         if (f > b) b = f;
     }
     return (b + 127) / 128 * 128;
 }
 
-constexpr int kResidentThreads = 512;
+constexpr int kResidentThreads = 1024;
 constexpr int kResidentWarpsH = kResidentThreads / 32;
 constexpr int kResidentMaxWT = 32;
 constexpr size_t kResidentSmemLimit = 227 * 1024;
 
-// Largest power-of-two WT <= min(32, cap) such that a class of the cube fits
-// the CTA's threads (h2*L*WT <= kResidentThreads) and the tile fits shared
-// memory; 0 if none.
+// Largest power-of-two WT <= min(32, cap) such that the column-words of a
+// class fit half the CTA (h2*L*WT <= kResidentThreads/2: two threads, one per
+// z parity, per column) and the tile fits shared memory; 0 if none.
 int ea_resident_pick_wt(int L, int jtype, int has_h, int nF, int cap_words);
 
 // Opt the persistent kernel into `smem` bytes of dynamic shared memory (outside any capture).
