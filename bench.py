@@ -169,12 +169,47 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------ biclique
+def biclique_block(pb, stream, peaks):
+    """Biclique K_{n,n}, n = 4096, 4096 replicas, linear beta 0.35 -> 3.5: sweep-loop kernels of the
+    tensor-core form (+-1 in FP8 e4m3, N(0,1) in split BF16) and of the FP32 CUDA-core form, timed with
+    the library's events around the sweep loop.  Tensor roofline: 2n FLOP per update (e4m3) or 4n
+    (two BF16 products) against the measured BF16 peak (x2 for FP8, the nominal dense ratio)."""
+    n, R = 4096, 4096
+    bf16 = float(peaks.get("bf16_tflops", 1964.9))
+    out = {"workload": "biclique n=4096 (8192 spins), 4096 replicas, linear beta 0.35->3.5, h=0"}
+    for law, form, S in (("pm1", "tensor", 200), ("gauss", "tensor", 100), ("pm1", "cudacore", 4)):
+        J = pb.pb_generate_biclique(n, pb.PB_DIST_PM1 if law == "pm1" else pb.PB_DIST_GAUSS, 11)
+        inst = pb.pb_create_instance(pb.PB_TOPO_BICLIQUE, J, None, n=n, stream=stream)
+        sc = pb.make_schedule(pb.PB_SCHED_LINEAR, S, 0.35, 3.5)
+        f = pb.PB_FORM_TENSOR if form == "tensor" else pb.PB_FORM_CUDACORE
+        run = pb.pb_anneal(inst, sc, R, 5, pb.make_opts(f), stream=stream)
+        ms = pb.pb_run_kernel_ms(run)
+        pb.pb_run_destroy(run)
+        pb.pb_instance_destroy(inst)
+        upd = 2 * n * R * S
+        flop_per_upd = (2 * n) if (law == "pm1" or form == "cudacore") else (4 * n)
+        tf = upd * flop_per_upd / (ms / 1e3) / 1e12
+        key = f"{law}_{form}"
+        ent = {"sweeps": S, "ms": ms, "updates_per_s": upd / (ms / 1e3), "tflops": tf}
+        if form == "tensor":
+            peak = 2 * bf16 if law == "pm1" else bf16
+            ent.update({"peak_tflops": peak, "frac": tf / peak,
+                        "peak_source": "measured bf16 burst" + (" x 2 (nominal fp8/bf16 ratio)" if law == "pm1" else "")})
+        out[key] = ent
+    return out
+
+
 # ------------------------------------------------- small profiling cases
 CASES = {
     # name: (topology, L or n, law, replicas, sweeps, form)
     "ea-L32-pm1-small": ("ea", 32, "pm1", 608, 50, "resident"),
     "ea-L32-gauss-small": ("ea", 32, "gauss", 608, 50, "resident"),
     "ea-L16-pm1-small": ("ea", 16, "pm1", 2432, 50, "resident"),
+    "bq-n4096-R4096-pm1-tensor": ("bq", 4096, "pm1", 4096, 2, "tensor"),
+    "bq-n4096-R4096-gauss-tensor": ("bq", 4096, "gauss", 4096, 2, "tensor"),
+    "bq-n4096-R1024-pm1-cudacore": ("bq", 4096, "pm1", 1024, 1, "cudacore"),
+    "bq-n1024-R1024-pm1-tensor": ("bq", 1024, "pm1", 1024, 4, "tensor"),
 }
 
 
@@ -212,6 +247,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-form comparison run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--no-biclique", action="store_true", help="skip the biclique tensor-core measurement")
     ap.add_argument("--case", default=None, choices=sorted(CASES),
                     help="run one small launch of a hot-path kernel (for ncu) and exit")
     args = ap.parse_args()
@@ -381,6 +417,9 @@ def main():
             pb.pb_run_destroy(r)
         pv = updates_per_step() / (pms / 1e3)
         line["plain_form"] = {"value": pv, "unit": UNIT, "ms_per_step": pms, "speedup_of_batched": value / world / pv}
+
+    if rank == 0 and not args.no_biclique:
+        line["biclique"] = biclique_block(pb, stream, peaks)
 
     if rank == 0 and not args.no_cpu and world == 1:
         from oracle import oracle as orc

@@ -271,9 +271,9 @@ __global__ void __launch_bounds__(256) bq_energy_kernel(BqJob job, const int8_t*
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         if (JT == PB_J_PM1_I8) {
             const int8_t* Jr = static_cast<const int8_t*>(job.inst.Jraw) + (size_t)i * n;
-            long long u = 0;
-            for (int j = 0; j < n; ++j) u += (long long)Jr[j] * b[j];
-            ai -= u * a[i];
+            int u = 0;  // |u| <= n: exact in int32
+            for (int j = 0; j < n; ++j) u += Jr[j] * b[j];
+            ai -= (long long)u * a[i];
         } else {
             const float* Jr = static_cast<const float*>(job.inst.Jraw) + (size_t)i * n;
             double u = 0.0;

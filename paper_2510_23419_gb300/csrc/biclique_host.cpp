@@ -260,6 +260,8 @@ static pb_status bq_prepare(pb_run* run, pb_instance* I, const pb_schedule* sc, 
     }
     PB_CUDA_TRY(cudaEventCreate(&run->ev_start));
     PB_CUDA_TRY(cudaEventCreate(&run->ev_stop));
+    PB_CUDA_TRY(cudaEventCreate(&run->ev_k0));
+    PB_CUDA_TRY(cudaEventCreate(&run->ev_k1));
     return PB_OK;
 }
 
@@ -278,11 +280,17 @@ static pb_status bq_enqueue_body(pb_run* run, cudaStream_t st)
     PB_CUDA_TRY(bq_half(run, 0, 0, 0, nullptr, st));
     PB_CUDA_TRY(bq_half(run, 1, 0, 0, nullptr, st));
     PB_CUDA_TRY(bq_launch_sweep_end(j, -1, 1, st));
+    // events around the sweep loop (inside a capture they must be recorded as external nodes)
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    PB_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
+    const unsigned evf = cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
+    PB_CUDA_TRY(cudaEventRecordWithFlags(run->ev_k0, st, evf));
     for (int s = 0; s < j.S; ++s) {
         PB_CUDA_TRY(bq_half(run, 0, s, 1, nullptr, st));
         PB_CUDA_TRY(bq_half(run, 1, s, 1, nullptr, st));
         PB_CUDA_TRY(bq_launch_sweep_end(j, s, 0, st));
     }
+    PB_CUDA_TRY(cudaEventRecordWithFlags(run->ev_k1, st, evf));
     PB_CUDA_TRY(bq_launch_readout(j, 0, run->final_pm.as<int8_t>(), run->E_out.as<double>(), st));
     PB_CUDA_TRY(bq_launch_readout(j, 1, run->best_pm.as<int8_t>(), run->E_out.as<double>() + run->R, st));
     return PB_OK;

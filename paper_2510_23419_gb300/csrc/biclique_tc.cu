@@ -40,6 +40,7 @@ struct TcCfg;
 template <>
 struct TcCfg<0> {  // e4m3
     static constexpr int STAGES = 4;
+    static constexpr int TAB_BYTES = 33 * 1024;  // threshold row of up to 8448 entries (n + |h| <= 4223)
     static constexpr int A_BYTES = TBM * KBYTES;
     static constexpr int B_BYTES = TBN * KBYTES;
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
@@ -49,6 +50,7 @@ struct TcCfg<0> {  // e4m3
 template <>
 struct TcCfg<1> {  // bf16 hi + lo
     static constexpr int STAGES = 3;
+    static constexpr int TAB_BYTES = 0;
     static constexpr int A_BYTES = TBM * KBYTES;
     static constexpr int B_BYTES = TBN * KBYTES;
     static constexpr int STAGE_BYTES = 2 * A_BYTES + B_BYTES;
@@ -266,21 +268,41 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int row = quarter * 32 + lane;
         const int i = i0 + row;
         const int et = threadIdx.x - 64;  // 0..127
+        const bool pm1 = KIND == 0;
+        const uint32_t* trow = pm1 ? job.table + (size_t)(s / job.step) * job.nF : nullptr;
+        // The threshold row goes to its own shared region while the MMAs run (these
+        // warps are idle until the accumulator is complete); a row too large for that
+        // region is staged in the stage ring once the MMAs no longer need it.
+        const bool tab_early = pm1 && (size_t)job.nF * 4 <= (size_t)Cfg::TAB_BYTES;
+        uint32_t* stab = reinterpret_cast<uint32_t*>(tab_early ? smem + Cfg::STAGES * Cfg::STAGE_BYTES : smem);
+        if (tab_early) {
+            for (int f0 = et; f0 < job.nF; f0 += 128 * 8) {
+                uint32_t v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int f = f0 + u * 128;
+                    v[u] = f < job.nF ? __ldg(trow + f) : 0u;
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int f = f0 + u * 128;
+                    if (f < job.nF) stab[f] = v[u];
+                }
+            }
+        }
         const bool ok = mbar_wait(&acc_bar, 0);
         if (!ok) {
             atomicOr(err, 4);
             s_fail = 1;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const bool pm1 = KIND == 0;
-        // stage memory is free once the accumulator is complete: threshold row + reduction buffers
-        uint32_t* stab = reinterpret_cast<uint32_t*>(smem);
-        const size_t tab_bytes = pm1 ? ((size_t)job.nF * 4 + 1023) / 1024 * 1024 : 0;
-        float* red = reinterpret_cast<float*>(smem + tab_bytes);  // [4][TBN], after the threshold row
+        // the stage ring is free once the accumulator is complete: reduction buffers (and a large row)
+        const size_t tab_bytes = (pm1 && !tab_early) ? ((size_t)job.nF * 4 + 1023) / 1024 * 1024 : 0;
+        float* red = reinterpret_cast<float*>(smem + tab_bytes);  // [4][TBN]
         float cexp = 0.0f;
         if (pm1) {
-            const uint32_t* trow = job.table + (size_t)(s / job.step) * job.nF;
-            for (int f = et; f < job.nF; f += 128) stab[f] = trow[f];
+            if (!tab_early)
+                for (int f = et; f < job.nF; f += 128) stab[f] = trow[f];
         } else {
             cexp = f32_cexp(job.betaf[s / job.step]);
         }
@@ -374,8 +396,8 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encoder()
 
 size_t bq_tc_smem_bytes(int kind)
 {
-    const size_t st = kind == 0 ? (size_t)TcCfg<0>::STAGES * TcCfg<0>::STAGE_BYTES
-                                : (size_t)TcCfg<1>::STAGES * TcCfg<1>::STAGE_BYTES;
+    const size_t st = kind == 0 ? (size_t)TcCfg<0>::STAGES * TcCfg<0>::STAGE_BYTES + TcCfg<0>::TAB_BYTES
+                                : (size_t)TcCfg<1>::STAGES * TcCfg<1>::STAGE_BYTES + TcCfg<1>::TAB_BYTES;
     return st + 1024;  // alignment slack
 }
 
