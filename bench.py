@@ -69,6 +69,24 @@ def profiled_traffic():
     return int(val.group(1))
 
 
+def rank_seeds(rank: int):
+    """Replicas only: every rank anneals its own copy of the batch with its own seeds."""
+    return [1000 * rank + 100 + q for q in range(len(JOBS))]
+
+
+def aggregate_ranks(local_ms: float, local_updates: int, dist=None, device="cpu"):
+    """Whole-job result over ranks: the slowest rank's time and the sum of all ranks' updates.
+    With no process group this is the local result."""
+    if dist is None:
+        return local_ms, local_updates
+    import torch
+    t = torch.tensor([local_ms], dtype=torch.float64, device=device)
+    u = torch.tensor([float(local_updates)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(u.item())
+
+
 def updates_per_step():
     return sum((L ** 3) * S_SWEEPS * R_REPLICAS for L, _, _ in JOBS)
 
@@ -281,7 +299,7 @@ def main():
     Js = [pb.pb_generate_ea(L, pb.PB_DIST_PM1 if law == "pm1" else pb.PB_DIST_GAUSS, seed) for L, law, seed in JOBS]
     insts = [pb.pb_create_instance(pb.PB_TOPO_EA3D, J, None, L=L, stream=stream) for J, (L, _, _) in zip(Js, JOBS)]
     scheds = [pb.make_schedule(pb.PB_SCHED_GEOMETRIC, S_SWEEPS, BETA0, BETA1) for _ in JOBS]
-    seeds = [1000 * rank + 100 + q for q in range(len(JOBS))]
+    seeds = rank_seeds(rank)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def one_step(opts=None):
@@ -323,12 +341,7 @@ def main():
     barrier()
     torch.cuda.synchronize()
     clocks = sampler.stop()
-    t_local = sum(step_ms)
-    t = torch.tensor([t_local], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    t_max_ms = float(t.item())
-    upd = updates_per_step() * args.steps * world
+    t_max_ms, upd = aggregate_ranks(sum(step_ms), updates_per_step() * args.steps, dist, device="cuda")
     value = upd / (t_max_ms / 1e3)
     ms_per_step = t_max_ms / args.steps
 

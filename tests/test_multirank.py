@@ -1,0 +1,67 @@
+"""Multi-GPU path of the benchmark (replicas only, weak scaling) on CPU ranks.
+
+Two gloo ranks check the whole-job aggregation the benchmark uses: the time is
+the slowest rank's, the updates are the sum over ranks; ranks draw distinct
+seeds (independent replicas, no data-path collective); the reference arm runs
+on rank 0 only."""
+import os
+import socket
+import sys
+
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, q):
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    import torch.distributed as dist
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        local_ms = 100.0 + 50.0 * rank
+        t, u = bench.aggregate_ranks(local_ms, 1000 * (rank + 1), dist, device="cpu")
+        q.put((rank, t, u, bench.rank_seeds(rank)))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_rank_aggregation():
+    world, port = 2, _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+    assert all(p.exitcode == 0 for p in procs)
+    res = sorted(q.get(timeout=5) for _ in range(world))
+    for rank, t, u, seeds in res:
+        assert t == 150.0            # max over ranks
+        assert u == 1000 + 2000      # sum over ranks
+    assert set(res[0][3]).isdisjoint(res[1][3])   # independent replicas per rank
+
+
+def test_single_process_aggregation_is_local():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.aggregate_ranks(12.5, 77, None) == (12.5, 77)
+
+
+def test_reference_arm_other_ranks_exit_quietly(capsys):
+    sys.path.insert(0, ROOT)
+    import bench
+
+    class A:
+        steps, warmup, gpus = 1, 0, 2
+    bench.run_reference(A(), rank=1)
+    assert capsys.readouterr().out == ""
