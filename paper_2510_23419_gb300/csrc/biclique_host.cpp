@@ -194,6 +194,7 @@ static pb_status bq_prepare(pb_run* run, pb_instance* I, const pb_schedule* sc, 
     j.Rpad = round_up(R, tensor ? kBqTcReps : kBqTileReps);
     j.ld = round_up(n, 16);
     j.nblk = (n + (tensor ? kBqTcRows : kBqTileRows) - 1) / (tensor ? kBqTcRows : kBqTileRows);
+    if (tensor) j.nblk = (j.nblk + 1) & ~1;  // row tiles come in clusters of two
     const int nlev = std::max<int>(1, (int)betas.size());
     if (pm1) {
         const int fmax = n + I->hmax;
@@ -255,7 +256,7 @@ static pb_status bq_prepare(pb_run* run, pb_instance* I, const pb_schedule* sc, 
                                        kBqTcRows));
         for (int sd = 0; sd < 2; ++sd)
             PB_CUDA_TRY(bq_tc_make_map(&run->maps.b[sd], j.spins[sd], esz, (uint64_t)n, (uint64_t)j.Rpad,
-                                       (uint64_t)j.ld * esz, kBqTcReps));
+                                       (uint64_t)j.ld * esz, kBqTcReps / 2));  // half a tile per cluster CTA
         PB_CUDA_TRY(bq_tc_set_smem());
     }
     PB_CUDA_TRY(cudaEventCreate(&run->ev_start));

@@ -5,7 +5,9 @@
 //     F[i][r] = sum_j J[i][j] m[r][j] + h_i                      (Eq. 3)
 // with the FP32 accumulator in tensor memory, then applies the p-bit decision
 // (Eq. 2) to it and writes the new spins of the side (and the energy
-// partials of the sweep).
+// partials of the sweep).  The kernel is persistent: clusters of two CTAs
+// loop over the tiles, with two accumulators in tensor memory so that the
+// epilogue of one tile overlaps the MMAs of the next.
 //
 //  +-1 couplings: A = J in FP8 e4m3, B = spins in e4m3 (+-1 exact),
 //                 tcgen05.mma kind::f8f6f4, exact integer sums in FP32.
@@ -14,12 +16,15 @@
 //
 // Warp roles: warp 0 issues TMA loads (128-byte swizzle, K-major) into a
 // STAGES-deep ring, warp 1 allocates tensor memory and issues the MMAs,
-// warps 2..5 (one per tensor-memory lane quarter) run the epilogue.  Every
+// warps 2..17 run the epilogue (warp w reads tensor-memory lanes
+// 32 (w % 4) .. +31, i.e. 32 rows, and a quarter of the 256 columns).  Every
 // mbarrier wait is bounded; on timeout the CTA records an error and still
 // releases its tensor memory.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
+
+#include <algorithm>
 
 #include "biclique_launch.h"
 #include "biclique_tc.h"
@@ -32,14 +37,16 @@ namespace {
 constexpr int TBM = kBqTcRows;   // rows per tile (tensor-memory lanes)
 constexpr int TBN = kBqTcReps;   // replicas per tile (accumulator columns)
 constexpr int KBYTES = 128;     // K bytes per stage (one 128-byte swizzle row)
-constexpr int kThreads = 192;   // 6 warps
+constexpr int kEpiWarps = 16;   // epilogue warps: four per tensor-memory lane quarter
+constexpr int kThreads = 64 + 32 * kEpiWarps;
+constexpr int kEpiCols = TBN / (kEpiWarps / 4);  // accumulator columns per epilogue warp
 constexpr uint32_t kWaitLimit = 1u << 26;
 
 template <int KIND>
 struct TcCfg;
 template <>
 struct TcCfg<0> {  // e4m3
-    static constexpr int STAGES = 4;
+    static constexpr int STAGES = 3;
     static constexpr int TAB_BYTES = 33 * 1024;  // threshold row of up to 8448 entries (n + |h| <= 4223)
     static constexpr int A_BYTES = TBM * KBYTES;
     static constexpr int B_BYTES = TBN * KBYTES;
@@ -96,6 +103,29 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
         : "memory");
 }
 
+// TMA load multicast to the CTAs of `mask` (same shared offset and barrier offset in each).
+__device__ __forceinline__ void tma_load_2d_mc(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1,
+                                               uint16_t mask)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
+        " [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "h"(mask)
+        : "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ void cluster_sync()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 // Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
 // 128 bytes, 8-row groups 1024 bytes apart (stride byte offset), version 1.
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr)
@@ -141,6 +171,15 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar)
                  : "memory");
 }
 
+// Arrive on the barrier at this shared offset in every CTA of `mask` once the MMAs complete.
+__device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t mask)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+                     smem_u32(bar)),
+                 "h"(mask)
+                 : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
 {
     uint32_t r[32];
@@ -174,208 +213,254 @@ __device__ __forceinline__ float warp_transpose_sum(float (&e)[32], int lane)
     return e[0];
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Persistent kernel.  A cluster is two CTAs; cluster c processes the
+// cluster-tiles ct = c, c + nclusters, ... ; cluster-tile ct is (row pair
+// p = ct % nrp, replica block b = ct / nrp) and the CTA of rank k in the
+// cluster owns row tile 2p + k.  Both CTAs load their own J rows and one
+// half of the shared spin tile, the latter multicast into both; a stage is
+// refilled only after the MMAs of both CTAs have released it.  The FP32
+// accumulator is double-buffered in tensor memory (2 x 256 columns), so the
+// epilogue of one tile runs while the MMAs of the next fill the other buffer.
 template <int KIND>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     bq_tc_half_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmA2,
                       const __grid_constant__ CUtensorMap tmB, BqJob job, int side, int s, int decide,
                       float* fields_out, int* err)
 {
     using Cfg = TcCfg<KIND>;
+    constexpr int S = Cfg::STAGES;
     extern __shared__ unsigned char smem_raw[];
-    // 1024-byte alignment for the 128-byte swizzle
     unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    __shared__ __align__(8) uint64_t full_bar[Cfg::STAGES];
-    __shared__ __align__(8) uint64_t empty_bar[Cfg::STAGES];
-    __shared__ __align__(8) uint64_t acc_bar;
+    uint32_t* stab = reinterpret_cast<uint32_t*>(smem + S * Cfg::STAGE_BYTES);
+    float* red = reinterpret_cast<float*>(smem + S * Cfg::STAGE_BYTES + Cfg::TAB_BYTES);  // [4][TBN]
+    __shared__ __align__(8) uint64_t full_bar[S];
+    __shared__ __align__(8) uint64_t empty_bar[S];
+    __shared__ __align__(8) uint64_t accf_bar[2];
+    __shared__ __align__(8) uint64_t acce_bar[2];
     __shared__ uint32_t tmem_base;
-    __shared__ int s_fail;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n = job.inst.n;
-    const int i0 = blockIdx.x * TBM;
-    const int r0 = blockIdx.y * TBN;
     const int nkb = (n + Cfg::KELEM - 1) / Cfg::KELEM;
+    const int nrp = (((n + TBM - 1) / TBM) + 1) / 2;
+    const int nct = nrp * (job.Rpad / TBN);
+    const int clus = blockIdx.x >> 1, nclus = gridDim.x >> 1;
+    const uint32_t crank = cluster_rank();
 
     if (threadIdx.x == 0) {
-        for (int q = 0; q < Cfg::STAGES; ++q) {
+        for (int q = 0; q < S; ++q) {
             mbar_init(&full_bar[q], 1);
-            mbar_init(&empty_bar[q], 1);
+            mbar_init(&empty_bar[q], 2);  // released by the MMAs of both CTAs of the cluster
         }
-        mbar_init(&acc_bar, 1);
-        s_fail = 0;
+        for (int q = 0; q < 2; ++q) {
+            mbar_init(&accf_bar[q], 1);
+            mbar_init(&acce_bar[q], kEpiWarps);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
-                     "r"(TBN));
+                     "r"(2 * TBN));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     }
     __syncthreads();
+    cluster_sync();  // both CTAs' barriers exist before any multicast reaches them
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base;
 
     if (warp == 0) {
         // ---------------- TMA producer ----------------
         if (lane == 0) {
-            for (int kb = 0; kb < nkb; ++kb) {
-                const int st = kb % Cfg::STAGES;
-                const uint32_t ph = (uint32_t)(kb / Cfg::STAGES) & 1u;
-                if (!mbar_wait(&empty_bar[st], ph ^ 1u)) {
-                    atomicOr(err, 1);
-                    s_fail = 1;
-                    break;
+            uint32_t g = 0;
+            bool ok = true;
+            for (int ct = clus; ct < nct && ok; ct += nclus) {
+                const int i0 = (2 * (ct % nrp) + (int)crank) * TBM;
+                const int r0 = (ct / nrp) * TBN;
+                for (int kb = 0; kb < nkb; ++kb, ++g) {
+                    const int st = (int)(g % S);
+                    const uint32_t ph = (g / S) & 1u;
+                    if (!mbar_wait(&empty_bar[st], ph ^ 1u)) {
+                        atomicOr(err, 1);
+                        ok = false;
+                        break;
+                    }
+                    unsigned char* sa = smem + st * Cfg::STAGE_BYTES;
+                    mbar_expect_tx(&full_bar[st], (uint32_t)Cfg::STAGE_BYTES);
+                    const int kc = kb * Cfg::KELEM;
+                    tma_load_2d(sa, &tmA, &full_bar[st], kc, i0);
+                    if (KIND == 1) tma_load_2d(sa + Cfg::A_BYTES, &tmA2, &full_bar[st], kc, i0);
+                    // this CTA's half of the shared spin tile, into both CTAs
+                    tma_load_2d_mc(sa + (KIND == 1 ? 2 : 1) * Cfg::A_BYTES + crank * (Cfg::B_BYTES / 2), &tmB,
+                                   &full_bar[st], kc, r0 + (int)crank * (TBN / 2), (uint16_t)0x3);
                 }
-                unsigned char* sa = smem + st * Cfg::STAGE_BYTES;
-                mbar_expect_tx(&full_bar[st], (uint32_t)Cfg::STAGE_BYTES);
-                const int kc = kb * Cfg::KELEM;
-                tma_load_2d(sa, &tmA, &full_bar[st], kc, i0);
-                if (KIND == 1) tma_load_2d(sa + Cfg::A_BYTES, &tmA2, &full_bar[st], kc, i0);
-                tma_load_2d(sa + (KIND == 1 ? 2 : 1) * Cfg::A_BYTES, &tmB, &full_bar[st], kc, r0);
             }
         }
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
             constexpr uint32_t idesc = instr_desc(KIND == 0 ? 0u : 1u, TBM, TBN);
+            uint32_t g = 0, j = 0;
             bool ok = true;
-            for (int kb = 0; kb < nkb && ok; ++kb) {
-                const int st = kb % Cfg::STAGES;
-                const uint32_t ph = (uint32_t)(kb / Cfg::STAGES) & 1u;
-                if (!mbar_wait(&full_bar[st], ph)) {
-                    atomicOr(err, 2);
-                    s_fail = 1;
+            for (int ct = clus; ct < nct && ok; ct += nclus, ++j) {
+                const uint32_t buf = j & 1u, aph = (j >> 1) & 1u;
+                if (!mbar_wait(&acce_bar[buf], aph ^ 1u)) {
+                    atomicOr(err, 8);
                     ok = false;
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t sa = smem_u32(smem + st * Cfg::STAGE_BYTES);
-                const uint32_t sb = sa + (KIND == 1 ? 2 : 1) * Cfg::A_BYTES;
+                const uint32_t d = tmem + buf * TBN;
+                for (int kb = 0; kb < nkb; ++kb, ++g) {
+                    const int st = (int)(g % S);
+                    const uint32_t ph = (g / S) & 1u;
+                    if (!mbar_wait(&full_bar[st], ph)) {
+                        atomicOr(err, 2);
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t sa = smem_u32(smem + st * Cfg::STAGE_BYTES);
+                    const uint32_t sb = sa + (KIND == 1 ? 2 : 1) * Cfg::A_BYTES;
 #pragma unroll
-                for (int k = 0; k < KBYTES / Cfg::KSTEP_BYTES; ++k) {
-                    const uint64_t bd = smem_desc(sb + k * Cfg::KSTEP_BYTES);
-                    mma_issue<KIND>(tmem, smem_desc(sa + k * Cfg::KSTEP_BYTES), bd, idesc, (kb | k) ? 1u : 0u);
-                    if (KIND == 1) mma_issue<KIND>(tmem, smem_desc(sa + Cfg::A_BYTES + k * Cfg::KSTEP_BYTES), bd, idesc, 1u);
+                    for (int k = 0; k < KBYTES / Cfg::KSTEP_BYTES; ++k) {
+                        const uint64_t bd = smem_desc(sb + k * Cfg::KSTEP_BYTES);
+                        mma_issue<KIND>(d, smem_desc(sa + k * Cfg::KSTEP_BYTES), bd, idesc, (kb | k) ? 1u : 0u);
+                        if (KIND == 1)
+                            mma_issue<KIND>(d, smem_desc(sa + Cfg::A_BYTES + k * Cfg::KSTEP_BYTES), bd, idesc, 1u);
+                    }
+                    mma_commit_mc(&empty_bar[st], (uint16_t)0x3);
                 }
-                mma_commit(&empty_bar[st]);
+                mma_commit(&accf_bar[buf]);
             }
-            mma_commit(&acc_bar);
         }
     } else {
-        // ---------------- epilogue: 4 warps, one tensor-memory lane quarter each ----------------
+        // ---------------- epilogue: 16 warps, four per tensor-memory lane quarter ----------------
         const int quarter = warp & 3;
+        const int slot = (warp - 2) >> 2;  // which quarter of the columns
         const int row = quarter * 32 + lane;
-        const int i = i0 + row;
-        const int et = threadIdx.x - 64;  // 0..127
+        const int et = threadIdx.x - 64;
+        constexpr int ET = 32 * kEpiWarps;
         const bool pm1 = KIND == 0;
+        float cexp = 0.0f;
+        // threshold row of this sweep's beta level, staged once per launch when it fits
         const uint32_t* trow = pm1 ? job.table + (size_t)(s / job.step) * job.nF : nullptr;
-        // The threshold row goes to its own shared region while the MMAs run (these
-        // warps are idle until the accumulator is complete); a row too large for that
-        // region is staged in the stage ring once the MMAs no longer need it.
-        const bool tab_early = pm1 && (size_t)job.nF * 4 <= (size_t)Cfg::TAB_BYTES;
-        uint32_t* stab = reinterpret_cast<uint32_t*>(tab_early ? smem + Cfg::STAGES * Cfg::STAGE_BYTES : smem);
-        if (tab_early) {
-            for (int f0 = et; f0 < job.nF; f0 += 128 * 8) {
-                uint32_t v[8];
+        const bool staged = pm1 && job.nF * 4 <= Cfg::TAB_BYTES;
+        const uint32_t* tab = staged ? stab : trow;
+        if (staged) {
+            for (int f0 = et; f0 < job.nF; f0 += ET * 4) {
+                uint32_t v[4];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int f = f0 + u * 128;
+                for (int u = 0; u < 4; ++u) {
+                    const int f = f0 + u * ET;
                     v[u] = f < job.nF ? __ldg(trow + f) : 0u;
                 }
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int f = f0 + u * 128;
+                for (int u = 0; u < 4; ++u) {
+                    const int f = f0 + u * ET;
                     if (f < job.nF) stab[f] = v[u];
                 }
             }
         }
-        const bool ok = mbar_wait(&acc_bar, 0);
-        if (!ok) {
-            atomicOr(err, 4);
-            s_fail = 1;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // the stage ring is free once the accumulator is complete: reduction buffers (and a large row)
-        const size_t tab_bytes = (pm1 && !tab_early) ? ((size_t)job.nF * 4 + 1023) / 1024 * 1024 : 0;
-        float* red = reinterpret_cast<float*>(smem + tab_bytes);  // [4][TBN]
-        float cexp = 0.0f;
-        if (pm1) {
-            if (!tab_early)
-                for (int f = et; f < job.nF; f += 128) stab[f] = trow[f];
-        } else {
-            cexp = f32_cexp(job.betaf[s / job.step]);
-        }
-        asm volatile("bar.sync 1, 128;" ::: "memory");
-        const bool live = ok && i < n;
-        const float hv = (i < n) ? (pm1 ? (job.inst.h8 ? (float)job.inst.h8[side * n + i] : 0.0f)
-                                        : job.inst.hf[side * n + i])
-                                 : 0.0f;
-        const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16);
-        for (int c = 0; c < TBN / 32; ++c) {
-            float v[32];
-            tmem_ld32(taddr + (uint32_t)(c * 32), v);
-            float e[32];
+        if (!pm1) cexp = f32_cexp(job.betaf[s / job.step]);
+        asm volatile("bar.sync 1, %0;" ::"r"(ET) : "memory");
+        uint32_t j = 0;
+        bool ok = true;
+        for (int ct = clus; ct < nct; ct += nclus, ++j) {
+            const uint32_t buf = j & 1u, aph = (j >> 1) & 1u;
+            const int rt = 2 * (ct % nrp) + (int)crank;
+            const int i = rt * TBM + row;
+            const int r0 = (ct / nrp) * TBN;
+            if (ok && !mbar_wait(&accf_bar[buf], aph)) {
+                atomicOr(err, 4);
+                ok = false;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const bool live = ok && i < n;
+            const float hv = (i < n) ? (pm1 ? (job.inst.h8 ? (float)job.inst.h8[side * n + i] : 0.0f)
+                                            : job.inst.hf[side * n + i])
+                                     : 0.0f;
+            const uint32_t taddr = tmem + buf * TBN + ((uint32_t)(quarter * 32) << 16);
+            for (int cc = 0; cc < kEpiCols / 32; ++cc) {
+                const int c = slot * (kEpiCols / 32) + cc;
+                float v[32];
+                tmem_ld32(taddr + (uint32_t)(c * 32), v);
+                if (cc == kEpiCols / 32 - 1) {
+                    // this warp has read its part of the accumulator: release the buffer
+                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&acce_bar[buf]);
+                }
+                float e[32];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int rq = r0 + c * 32 + 4 * q;
-                float F[4];
+                for (int q = 0; q < 8; ++q) {
+                    const int rq = r0 + c * 32 + 4 * q;
+                    float F[4];
 #pragma unroll
-                for (int b = 0; b < 4; ++b) F[b] = v[4 * q + b] + hv;
-                bool mn[4] = {false, false, false, false};
-                if (live) {
-                    if (fields_out) {
+                    for (int b = 0; b < 4; ++b) F[b] = v[4 * q + b] + hv;
+                    bool mn[4] = {false, false, false, false};
+                    if (live) {
+                        if (fields_out) {
 #pragma unroll
-                        for (int b = 0; b < 4; ++b)
-                            if (rq + b < job.R) fields_out[(size_t)(rq + b) * 2 * n + side * n + i] = F[b];
-                    } else if (decide) {
-                        const U4 w = philox10((uint32_t)i, (uint32_t)s, (uint32_t)(rq >> 2),
-                                              (kTagDecision << 24) | (uint32_t)side, job.key0, job.key1);
-                        const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+                            for (int b = 0; b < 4; ++b)
+                                if (rq + b < job.R) fields_out[(size_t)(rq + b) * 2 * n + side * n + i] = F[b];
+                        } else if (decide) {
+                            const U4 w = philox10((uint32_t)i, (uint32_t)s, (uint32_t)(rq >> 2),
+                                                  (kTagDecision << 24) | (uint32_t)side, job.key0, job.key1);
+                            const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
-                        for (int b = 0; b < 4; ++b) {
-                            mn[b] = pm1 ? (ws[b] >= stab[(int)F[b] - job.fmin]) : (decide_f32(ws[b], F[b], cexp) != 0u);
-                            const size_t off = (size_t)(rq + b) * job.ld + i;
-                            if (pm1)
-                                static_cast<uint8_t*>(job.spins[side])[off] = mn[b] ? kE4m3Minus : kE4m3Plus;
-                            else
-                                static_cast<uint16_t*>(job.spins[side])[off] = mn[b] ? kBf16Minus : kBf16Plus;
-                        }
-                    } else {
+                            for (int b = 0; b < 4; ++b) {
+                                mn[b] = pm1 ? (ws[b] >= tab[(int)F[b] - job.fmin]) : (decide_f32(ws[b], F[b], cexp) != 0u);
+                                const size_t off = (size_t)(rq + b) * job.ld + i;
+                                if (pm1)
+                                    static_cast<uint8_t*>(job.spins[side])[off] = mn[b] ? kE4m3Minus : kE4m3Plus;
+                                else
+                                    static_cast<uint16_t*>(job.spins[side])[off] = mn[b] ? kBf16Minus : kBf16Plus;
+                            }
+                        } else {
 #pragma unroll
-                        for (int b = 0; b < 4; ++b) {
-                            const size_t off = (size_t)(rq + b) * job.ld + i;
-                            mn[b] = pm1 ? (static_cast<const uint8_t*>(job.spins[side])[off] & 0x80u) != 0
-                                        : (static_cast<const uint16_t*>(job.spins[side])[off] & 0x8000u) != 0;
+                            for (int b = 0; b < 4; ++b) {
+                                const size_t off = (size_t)(rq + b) * job.ld + i;
+                                mn[b] = pm1 ? (static_cast<const uint8_t*>(job.spins[side])[off] & 0x80u) != 0
+                                            : (static_cast<const uint16_t*>(job.spins[side])[off] & 0x8000u) != 0;
+                            }
                         }
                     }
-                }
 #pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    // side 1: -m F (F includes h);  side 0: -h m
-                    const float x = (side == 1) ? F[b] : hv;
-                    e[4 * q + b] = live ? (mn[b] ? x : -x) : 0.0f;
+                    for (int b = 0; b < 4; ++b) {
+                        // side 1: -m F (F includes h);  side 0: -h m
+                        const float x = (side == 1) ? F[b] : hv;
+                        e[4 * q + b] = live ? (mn[b] ? x : -x) : 0.0f;
+                    }
                 }
+                if (!fields_out) red[quarter * TBN + c * 32 + lane] = warp_transpose_sum(e, lane);
             }
-            if (!fields_out) red[quarter * TBN + c * 32 + lane] = warp_transpose_sum(e, lane);
-        }
-        if (!fields_out) {
-            asm volatile("bar.sync 1, 128;" ::: "memory");
-            for (int col = et; col < TBN; col += 128) {
-                const float sum = red[col] + red[TBN + col] + red[2 * TBN + col] + red[3 * TBN + col];
-                const size_t off = ((size_t)side * job.nblk + blockIdx.x) * job.Rpad + r0 + col;
-                if (pm1)
-                    static_cast<int32_t*>(job.part)[off] = (int32_t)sum;
-                else
-                    static_cast<float*>(job.part)[off] = sum;
+            if (!fields_out) {
+                asm volatile("bar.sync 1, %0;" ::"r"(ET) : "memory");
+                for (int col = et; col < TBN; col += ET) {
+                    const float sum = red[col] + red[TBN + col] + red[2 * TBN + col] + red[3 * TBN + col];
+                    const size_t off = ((size_t)side * job.nblk + rt) * job.Rpad + r0 + col;
+                    if (pm1)
+                        static_cast<int32_t*>(job.part)[off] = (int32_t)sum;
+                    else
+                        static_cast<float*>(job.part)[off] = sum;
+                }
+                asm volatile("bar.sync 1, %0;" ::"r"(ET) : "memory");  // red is reused by the next tile
             }
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
+    cluster_sync();  // no CTA leaves while its peer may still signal its barriers
     if (warp == 1) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TBN));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TBN));
     }
 }
 
@@ -394,11 +479,50 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encoder()
 
 }  // namespace
 
+size_t bq_tc_smem_bytes(int kind);
+
+namespace {
+
+// How many two-CTA clusters of the kernel can be resident at once on this
+// device (a GPC with an odd number of free SMs leaves one SM unused); cached
+// per device and kind.
+int tc_active_clusters(int kind)
+{
+    static int cache[64][2] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && cache[dev][kind] > 0) return cache[dev][kind];
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int n = 0;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * std::max(1, sms / 2));
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = bq_tc_smem_bytes(kind);
+    cudaLaunchAttribute at;
+    at.id = cudaLaunchAttributeClusterDimension;
+    at.val.clusterDim.x = 2;
+    at.val.clusterDim.y = 1;
+    at.val.clusterDim.z = 1;
+    cfg.attrs = &at;
+    cfg.numAttrs = 1;
+    const cudaError_t e = kind == 0 ? cudaOccupancyMaxActiveClusters(&n, bq_tc_half_kernel<0>, &cfg)
+                                    : cudaOccupancyMaxActiveClusters(&n, bq_tc_half_kernel<1>, &cfg);
+    if (e != cudaSuccess || n < 1) {
+        (void)cudaGetLastError();
+        n = std::max(1, sms / 2);
+    }
+    if (dev >= 0 && dev < 64) cache[dev][kind] = n;
+    return n;
+}
+
+}  // namespace
+
 size_t bq_tc_smem_bytes(int kind)
 {
     const size_t st = kind == 0 ? (size_t)TcCfg<0>::STAGES * TcCfg<0>::STAGE_BYTES + TcCfg<0>::TAB_BYTES
                                 : (size_t)TcCfg<1>::STAGES * TcCfg<1>::STAGE_BYTES + TcCfg<1>::TAB_BYTES;
-    return st + 1024;  // alignment slack
+    return st + (size_t)4 * TBN * 4 + 1024;  // + reduction buffer + alignment slack
 }
 
 // 2D row-major [rows][cols] matrix of elem_bytes elements (row stride ld_bytes),
@@ -423,8 +547,12 @@ cudaError_t bq_tc_set_smem()
     cudaError_t e = cudaFuncSetAttribute(bq_tc_half_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)bq_tc_smem_bytes(0));
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(bq_tc_half_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)bq_tc_smem_bytes(1));
+    e = cudaFuncSetAttribute(bq_tc_half_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)bq_tc_smem_bytes(1));
+    if (e != cudaSuccess) return e;
+    tc_active_clusters(0);  // occupancy queries outside any stream capture
+    tc_active_clusters(1);
+    return cudaSuccess;
 }
 
 cudaError_t bq_launch_tc_half(const BqTcMaps& maps, const BqJob& job, int side, int s, int decide, float* fields_out,
@@ -432,7 +560,10 @@ cudaError_t bq_launch_tc_half(const BqTcMaps& maps, const BqJob& job, int side, 
 {
     const int kind = job.inst.jtype == PB_J_PM1_I8 ? 0 : 1;
     const size_t smem = bq_tc_smem_bytes(kind);
-    dim3 grid((unsigned)((job.inst.n + TBM - 1) / TBM), (unsigned)(job.Rpad / TBN));
+    const int nrp = (((job.inst.n + TBM - 1) / TBM) + 1) / 2;
+    const int nct = nrp * (job.Rpad / TBN);
+    const int nclus = std::max(1, std::min(nct, tc_active_clusters(kind)));
+    dim3 grid((unsigned)(2 * nclus));  // persistent clusters of two CTAs
     const CUtensorMap& A = side == 0 ? maps.a[0] : maps.a[2];
     const CUtensorMap& A2 = side == 0 ? maps.a[1] : maps.a[3];
     const CUtensorMap& B = maps.b[1 - side];
