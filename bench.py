@@ -228,6 +228,8 @@ CASES = {
     "bq-n4096-R4096-gauss-tensor": ("bq", 4096, "gauss", 4096, 2, "tensor"),
     "bq-n4096-R1024-pm1-cudacore": ("bq", 4096, "pm1", 1024, 1, "cudacore"),
     "bq-n1024-R1024-pm1-tensor": ("bq", 1024, "pm1", 1024, 4, "tensor"),
+    "bq-n4096-R4096-pm1-tensor-s200": ("bq", 4096, "pm1", 4096, 200, "tensor"),
+    "bq-n4096-R4096-gauss-tensor-s100": ("bq", 4096, "gauss", 4096, 100, "tensor"),
 }
 
 
@@ -250,8 +252,9 @@ def run_case(name):
     sc = pb.make_schedule(pb.PB_SCHED_GEOMETRIC, S, 0.1, 5.0)
     run = pb.pb_anneal(inst, sc, R, 7, pb.make_opts(forms[form]))
     ms = pb.pb_run_kernel_ms(run)
+    dev_ms = pb.pb_run_device_ms(run)
     torch.cuda.synchronize()
-    print(json.dumps({"case": name, "kernel_ms": ms}))
+    print(json.dumps({"case": name, "kernel_ms": ms, "device_ms": dev_ms}))
     pb.pb_run_destroy(run)
     pb.pb_instance_destroy(inst)
 

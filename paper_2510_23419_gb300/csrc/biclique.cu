@@ -197,14 +197,20 @@ __global__ void __launch_bounds__(256) bq_cc_half_kernel(BqJob job, int side, in
     }
 }
 
-// One block per replica: energy of the state after the sweep, running best,
-// snapshot of improved replicas.
-__global__ void __launch_bounds__(128) bq_sweep_end_kernel(BqJob job, int s, int init)
+// Energy of the state after the sweep (the row-tile partials of both sides,
+// summed in a fixed order), running best, snapshot of improved replicas.
+// 32 replicas per block: one thread per replica reads the partials (coalesced
+// across replicas), then the block copies the improved replicas' rows with
+// 16-byte loads and stores.
+constexpr int kEndReps = 32;
+
+__global__ void __launch_bounds__(256) bq_sweep_end_kernel(BqJob job, int s, int init)
 {
-    __shared__ int s_imp;
-    const int r = blockIdx.x;
+    __shared__ int s_imp[kEndReps];
+    const int r0 = blockIdx.x * kEndReps;
     const bool pm1 = job.inst.jtype == PB_J_PM1_I8;
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < kEndReps) {
+        const int r = r0 + threadIdx.x;
         bool imp;
         if (pm1) {
             const int32_t* p = static_cast<const int32_t*>(job.part);
@@ -225,16 +231,28 @@ __global__ void __launch_bounds__(128) bq_sweep_end_kernel(BqJob job, int s, int
         }
         if (init) job.hit_sweep[r] = -1;
         if (imp) job.best_sweep[r] = init ? -1 : s;
-        s_imp = imp ? 1 : 0;
+        s_imp[threadIdx.x] = imp ? 1 : 0;
     }
     __syncthreads();
-    if (!s_imp) return;
-    const int bytes = job.ld * (pm1 ? 1 : 2);
-    for (int side = 0; side < 2; ++side) {
-        const uint8_t* src = static_cast<const uint8_t*>(job.spins[side]) + (size_t)r * bytes;
-        uint8_t* dst = static_cast<uint8_t*>(job.best[side]) + (size_t)r * bytes;
-        for (int q = threadIdx.x * 4; q < bytes; q += blockDim.x * 4)
-            *reinterpret_cast<uint32_t*>(dst + q) = *reinterpret_cast<const uint32_t*>(src + q);
+    // one warp per improved replica row, eight independent 16-byte loads in flight per lane
+    const int nvec = job.ld * (pm1 ? 1 : 2) / 16;  // the row is a multiple of 16 bytes
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int q = warp; q < kEndReps; q += (int)(blockDim.x >> 5)) {
+        if (!s_imp[q]) continue;
+        const size_t row = (size_t)(r0 + q) * nvec;
+        for (int side = 0; side < 2; ++side) {
+            const uint4* __restrict__ src = static_cast<const uint4*>(job.spins[side]) + row;
+            uint4* __restrict__ dst = static_cast<uint4*>(job.best[side]) + row;
+            for (int k0 = lane; k0 < nvec; k0 += 32 * 8) {
+                uint4 t[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (k0 + 32 * u < nvec) t[u] = src[k0 + 32 * u];
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (k0 + 32 * u < nvec) dst[k0 + 32 * u] = t[u];
+            }
+        }
     }
 }
 
@@ -256,57 +274,146 @@ __global__ void __launch_bounds__(256) bq_readout_kernel(BqJob job, int which, i
     out[j] = minus ? (int8_t)-1 : (int8_t)1;
 }
 
-// E = -sum_ij J_ij a_i b_j - sum h m, one block per replica: int64 (PM1) or FP64 (F32).
-template <int JT>
-__global__ void __launch_bounds__(256) bq_energy_kernel(BqJob job, const int8_t* __restrict__ m, double* __restrict__ E)
+// Exact energy of returned states (Eq. 1 with the sign reading E = -sum J a b - sum h m).
+// Tiled over 64 rows i x 64 replicas r: U[i][r] = sum_j J[i][j] b[r][j], then
+// the tile's part -sum_i a[r][i] U[i][r] goes to epart[row tile][r].
+//   +-1: int8 products four at a time (__dp4a), exact int32 (|U| <= n).
+//   real: U as an unevaluated FP32 pair hi + lo, every term added by the
+//         error-free two-sum (Knuth), so U is accurate to about 2^-48
+//         relative to sum_j |J_ij|; the row sum is taken in FP64.
+constexpr int kEt = 64;
+
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x)
 {
-    __shared__ long long red_i[8];
-    __shared__ double red_f[8];
-    const int n = job.inst.n;
-    const int r = blockIdx.x;
-    const int8_t* a = m + (size_t)r * 2 * n;
-    const int8_t* b = a + n;
-    long long ai = 0;
-    double af = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const float s = hi + x;
+    const float bb = s - hi;
+    const float err = (hi - (s - bb)) + (x - bb);
+    hi = s;
+    lo += err;
+}
+
+template <int JT>
+__global__ void __launch_bounds__(256) bq_energy_tile_kernel(BqJob job, const int8_t* __restrict__ m)
+{
+    const int n = job.inst.n, R = job.R;
+    const int i0 = blockIdx.x * kEt, r0 = blockIdx.y * kEt;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // replica quad, row quad
+    __shared__ __align__(16) uint32_t Js[kEt][kEt + 4];  // PM1: [j/4][i] packed bytes; F32: [j][i] floats
+    __shared__ __align__(16) uint32_t Bs[kEt][kEt + 4];  // PM1: [j/4][r] packed bytes; F32: [j][r] sign masks
+    __shared__ double red[16][kEt + 1];
+
+    int acc_i[4][4];
+    float hi[4][4], lo[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            acc_i[a][b] = 0;
+            hi[a][b] = 0.0f;
+            lo[a][b] = 0.0f;
+        }
+
+    for (int j0 = 0; j0 < n; j0 += kEt) {
         if (JT == PB_J_PM1_I8) {
-            const int8_t* Jr = static_cast<const int8_t*>(job.inst.Jraw) + (size_t)i * n;
-            int u = 0;  // |u| <= n: exact in int32
-            for (int j = 0; j < n; ++j) u += Jr[j] * b[j];
-            ai -= (long long)u * a[i];
+            const int8_t* J = static_cast<const int8_t*>(job.inst.Jraw);
+            for (int e = threadIdx.x; e < kEt * (kEt / 4); e += 256) {
+                const int w = e & 15, q = e >> 4;  // word (4 columns), row (of J or of the spins)
+                uint32_t jw = 0, bw = 0;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int j = j0 + 4 * w + c;
+                    const int i = i0 + q, r = r0 + q;
+                    const uint32_t jv = (i < n && j < n) ? (uint8_t)J[(size_t)i * n + j] : 0u;
+                    const uint32_t bv = (r < R && j < n) ? (uint8_t)m[(size_t)r * 2 * n + n + j] : 0u;
+                    jw |= jv << (8 * c);
+                    bw |= bv << (8 * c);
+                }
+                Js[w][q] = jw;
+                Bs[w][q] = bw;
+            }
         } else {
-            const float* Jr = static_cast<const float*>(job.inst.Jraw) + (size_t)i * n;
-            double u = 0.0;
-            for (int j = 0; j < n; ++j) u += (double)Jr[j] * (double)b[j];
-            af -= u * (double)a[i];
+            const float* J = static_cast<const float*>(job.inst.Jraw);
+            for (int e = threadIdx.x; e < kEt * kEt; e += 256) {
+                const int j = e & (kEt - 1), q = e >> 6;
+                const int i = i0 + q, r = r0 + q;
+                const float jv = (i < n && j0 + j < n) ? J[(size_t)i * n + j0 + j] : 0.0f;
+                const int8_t bv = (r < R && j0 + j < n) ? m[(size_t)r * 2 * n + n + j0 + j] : (int8_t)1;
+                Js[j][q] = __float_as_uint(jv);
+                Bs[j][q] = bv < 0 ? 0x80000000u : 0u;
+            }
         }
-    }
-    if (job.inst.hraw) {
-        for (int c = threadIdx.x; c < 2 * n; c += blockDim.x) {
-            if (JT == PB_J_PM1_I8)
-                ai -= (long long)static_cast<const int8_t*>(job.inst.hraw)[c] * a[c];
-            else
-                af -= (double)static_cast<const float*>(job.inst.hraw)[c] * (double)a[c];
+        __syncthreads();
+        if (JT == PB_J_PM1_I8) {
+#pragma unroll 4
+            for (int w = 0; w < kEt / 4; ++w) {
+                const uint4 jv = *reinterpret_cast<const uint4*>(&Js[w][ty * 4]);
+                const uint4 bv = *reinterpret_cast<const uint4*>(&Bs[w][tx * 4]);
+                const int ja[4] = {(int)jv.x, (int)jv.y, (int)jv.z, (int)jv.w};
+                const int ba[4] = {(int)bv.x, (int)bv.y, (int)bv.z, (int)bv.w};
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) acc_i[a][b] = __dp4a(ja[a], ba[b], acc_i[a][b]);
+            }
+        } else {
+#pragma unroll 2
+            for (int j = 0; j < kEt; ++j) {
+                const uint4 jv = *reinterpret_cast<const uint4*>(&Js[j][ty * 4]);
+                const uint4 sv = *reinterpret_cast<const uint4*>(&Bs[j][tx * 4]);
+                const uint32_t ja[4] = {jv.x, jv.y, jv.z, jv.w};
+                const uint32_t sa[4] = {sv.x, sv.y, sv.z, sv.w};
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) two_sum_acc(hi[a][b], lo[a][b], __uint_as_float(ja[a] ^ sa[b]));
+            }
         }
+        __syncthreads();
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        ai += __shfl_xor_sync(0xFFFFFFFFu, ai, o);
-        af += __shfl_xor_sync(0xFFFFFFFFu, af, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        red_i[threadIdx.x >> 5] = ai;
-        red_f[threadIdx.x >> 5] = af;
+    // -sum over this thread's 4 rows of a[r][i] U[i][r], per replica, then over the 16 row quads
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        const int r = r0 + tx * 4 + b;
+        double t = 0.0;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const int i = i0 + ty * 4 + a;
+            if (i < n && r < R) {
+                const double av = (double)m[(size_t)r * 2 * n + i];
+                const double u = JT == PB_J_PM1_I8 ? (double)acc_i[a][b] : (double)hi[a][b] + (double)lo[a][b];
+                t -= av * u;
+            }
+        }
+        red[ty][tx * 4 + b] = t;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        long long si = 0;
-        double sf = 0.0;
-        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
-            si += red_i[q];
-            sf += red_f[q];
-        }
-        E[r] = (JT == PB_J_PM1_I8) ? (double)si : sf;
+    if (threadIdx.x < kEt) {
+        const int r = r0 + threadIdx.x;
+        double t = 0.0;
+        for (int q = 0; q < 16; ++q) t += red[q][threadIdx.x];
+        if (r < R) job.epart[(size_t)blockIdx.x * R + r] = t;
     }
+}
+
+// E[r] = sum over row tiles of epart (fixed order) - sum_c h_c m_c; one warp per replica.
+template <int JT>
+__global__ void __launch_bounds__(256) bq_energy_sum_kernel(BqJob job, const int8_t* __restrict__ m, double* __restrict__ E)
+{
+    const int n = job.inst.n, R = job.R;
+    const int r = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (r >= R) return;
+    const int nt = (n + kEt - 1) / kEt;
+    double t = 0.0;
+    for (int q = lane; q < nt; q += 32) t += job.epart[(size_t)q * R + r];
+    if (job.inst.hraw) {
+        for (int c = lane; c < 2 * n; c += 32) {
+            const double hv = JT == PB_J_PM1_I8 ? (double)static_cast<const int8_t*>(job.inst.hraw)[c]
+                                                : (double)static_cast<const float*>(job.inst.hraw)[c];
+            t -= hv * (double)m[(size_t)r * 2 * n + c];
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xFFFFFFFFu, t, o);
+    if (lane == 0) E[r] = t;
 }
 
 unsigned nblocks(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
@@ -338,17 +445,21 @@ cudaError_t bq_launch_cc_half(const BqJob& job, int side, int s, int decide, flo
 
 cudaError_t bq_launch_sweep_end(const BqJob& job, int s, int init, cudaStream_t st)
 {
-    bq_sweep_end_kernel<<<job.Rpad, 128, 0, st>>>(job, s, init);
+    bq_sweep_end_kernel<<<job.Rpad / kEndReps, 256, 0, st>>>(job, s, init);
     return cudaGetLastError();
 }
 
 cudaError_t bq_launch_readout(const BqJob& job, int which, int8_t* out_pm, double* out_E, cudaStream_t st)
 {
     bq_readout_kernel<<<nblocks((long long)job.R * 2 * job.inst.n, 256), 256, 0, st>>>(job, which, out_pm);
-    if (job.inst.jtype == PB_J_PM1_I8)
-        bq_energy_kernel<PB_J_PM1_I8><<<job.R, 256, 0, st>>>(job, out_pm, out_E);
-    else
-        bq_energy_kernel<PB_J_F32><<<job.R, 256, 0, st>>>(job, out_pm, out_E);
+    const dim3 grid((unsigned)((job.inst.n + kEt - 1) / kEt), (unsigned)((job.R + kEt - 1) / kEt));
+    if (job.inst.jtype == PB_J_PM1_I8) {
+        bq_energy_tile_kernel<PB_J_PM1_I8><<<grid, 256, 0, st>>>(job, out_pm);
+        bq_energy_sum_kernel<PB_J_PM1_I8><<<nblocks(job.R, 8), 256, 0, st>>>(job, out_pm, out_E);
+    } else {
+        bq_energy_tile_kernel<PB_J_F32><<<grid, 256, 0, st>>>(job, out_pm);
+        bq_energy_sum_kernel<PB_J_F32><<<nblocks(job.R, 8), 256, 0, st>>>(job, out_pm, out_E);
+    }
     return cudaGetLastError();
 }
 

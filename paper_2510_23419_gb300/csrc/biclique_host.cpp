@@ -203,6 +203,19 @@ static pb_status bq_prepare(pb_run* run, pb_instance* I, const pb_schedule* sc, 
         std::vector<uint32_t> tab((size_t)nlev * j.nF, 0x80000000u);
         for (size_t l = 0; l < betas.size(); ++l)
             for (int f = 0; f < j.nF; ++f) tab[l * j.nF + f] = threshold_u32(betas[l], (double)(f + j.fmin));
+        // Per level, the window of the row outside which T is saturated: every entry
+        // below it is 0 and every entry above it 2^32 - 1 (T is nondecreasing in F),
+        // with one saturated entry kept on each side.
+        run->bq_win.assign((size_t)nlev * 2, 0);
+        for (size_t l = 0; l < betas.size(); ++l) {
+            const uint32_t* row = tab.data() + l * j.nF;
+            int lo = 0, hi = j.nF - 1;
+            while (lo + 1 < j.nF && row[lo + 1] == 0u) ++lo;
+            while (hi - 1 >= 0 && row[hi - 1] == 0xFFFFFFFFu) --hi;
+            if (hi < lo) hi = lo;
+            run->bq_win[2 * l] = lo;
+            run->bq_win[2 * l + 1] = hi - lo + 1;
+        }
         PB_ALLOC(run->table, tab.size() * 4);
         PB_CUDA_TRY(cudaMemcpyAsync(run->table.p, tab.data(), tab.size() * 4, cudaMemcpyHostToDevice, st));
         PB_CUDA_TRY(cudaStreamSynchronize(st));
@@ -246,6 +259,8 @@ static pb_status bq_prepare(pb_run* run, pb_instance* I, const pb_schedule* sc, 
     PB_ALLOC(run->extra[5], 16);
     PB_CUDA_TRY(cudaMemsetAsync(run->extra[5].p, 0, 16, st));
     run->dev_err = run->extra[5].as<int>();
+    PB_ALLOC(run->extra[6], (size_t)((n + 63) / 64) * R * 8);
+    j.epart = run->extra[6].as<double>();
     if (tensor) {
         const int esz = pm1 ? 1 : 2;
         const BqDevice& q = I->bq;
@@ -269,7 +284,12 @@ static pb_status bq_prepare(pb_run* run, pb_instance* I, const pb_schedule* sc, 
 static cudaError_t bq_half(pb_run* run, int side, int s, int decide, float* fields_out, cudaStream_t st)
 {
     if (run->form == PB_FORM_TENSOR)
-        return bq_launch_tc_half(run->maps, run->bjob, side, s, decide, fields_out, run->dev_err, st);
+    {
+        const size_t l = (size_t)(s / std::max(1, run->bjob.step));
+        const bool w = 2 * l + 1 < run->bq_win.size();
+        return bq_launch_tc_half(run->maps, run->bjob, side, s, decide, fields_out, run->dev_err,
+                                 w ? run->bq_win[2 * l] : 0, w ? run->bq_win[2 * l + 1] : 0, st);
+    }
     return bq_launch_cc_half(run->bjob, side, s, decide, fields_out, st);
 }
 

@@ -49,6 +49,7 @@ struct BqJob {
     int32_t* hit_sweep;
     int32_t has_target, target_i;
     float target_f;
+    double* epart;          // [ceil(n/64)][R] row-tile parts of the exact readout energy
 };
 
 constexpr int kBqTileRows = 64;   // CUDA-core field kernel: rows (spins of the updated side) per block

@@ -1,7 +1,7 @@
 // biclique_tc.cu -- tcgen05 tensor-core field of the biclique p-bit update
 // (arXiv 2510.23419, Sec. 3; update groups Sec. 1.2.2: each side is one colour
 // class, so the fields of a whole side are one dense product J M over
-// replicas).  One CTA computes a 128-row x 256-replica tile of
+// replicas).  A pair of CTAs computes a 256-row x 256-replica tile of
 //     F[i][r] = sum_j J[i][j] m[r][j] + h_i                      (Eq. 3)
 // with the FP32 accumulator in tensor memory, then applies the p-bit decision
 // (Eq. 2) to it and writes the new spins of the side (and the energy
@@ -14,12 +14,15 @@
 //  real couplings: J = hi + lo with hi = bf16(J), lo = bf16(J - hi); spins
 //                 bf16 +-1; two kind::f16 MMAs per K step into one accumulator.
 //
-// Warp roles: warp 0 issues TMA loads (128-byte swizzle, K-major) into a
-// STAGES-deep ring, warp 1 allocates tensor memory and issues the MMAs,
-// warps 2..17 run the epilogue (warp w reads tensor-memory lanes
-// 32 (w % 4) .. +31, i.e. 32 rows, and a quarter of the 256 columns).  Every
-// mbarrier wait is bounded; on timeout the CTA records an error and still
-// releases its tensor memory.
+// Two CTAs (a cluster) form a pair that computes a 256-row x 256-replica tile
+// with tcgen05.mma.cta_group::2 (M = 256): each CTA stages its own 128 rows of
+// J and half of the spin tile, and keeps its 128 rows of the accumulator.
+// Warp roles per CTA: warp 0 issues TMA loads (128-byte swizzle, K-major) into
+// a STAGES-deep ring, warp 1 allocates tensor memory (and, in the even CTA,
+// issues the MMAs), warps 2..17 run the epilogue (warp w reads tensor-memory
+// lanes 32 (w % 4) .. +31, i.e. 32 rows, and a quarter of the 256 columns).
+// Every mbarrier wait is bounded; on timeout the CTA records an error and
+// still releases its tensor memory.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
@@ -44,22 +47,25 @@ constexpr uint32_t kWaitLimit = 1u << 26;
 
 template <int KIND>
 struct TcCfg;
+// Per-CTA stage: this CTA's 128 rows of J (one or two operands) and its half
+// (128 replicas) of the spin tile, 128 bytes of K each.
 template <>
 struct TcCfg<0> {  // e4m3
-    static constexpr int STAGES = 3;
+    static_assert(kBqTcWindowMax * 32 * 4 <= 33 * 1024, "replicated threshold window must fit the table region");
+    static constexpr int STAGES = 5;
     static constexpr int TAB_BYTES = 33 * 1024;  // threshold row of up to 8448 entries (n + |h| <= 4223)
     static constexpr int A_BYTES = TBM * KBYTES;
-    static constexpr int B_BYTES = TBN * KBYTES;
+    static constexpr int B_BYTES = (TBN / 2) * KBYTES;
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
     static constexpr int KELEM = 128;  // elements per stage
     static constexpr int KSTEP_BYTES = 32;  // one MMA consumes K = 32 e4m3
 };
 template <>
 struct TcCfg<1> {  // bf16 hi + lo
-    static constexpr int STAGES = 3;
+    static constexpr int STAGES = 4;
     static constexpr int TAB_BYTES = 0;
     static constexpr int A_BYTES = TBM * KBYTES;
-    static constexpr int B_BYTES = TBN * KBYTES;
+    static constexpr int B_BYTES = (TBN / 2) * KBYTES;
     static constexpr int STAGE_BYTES = 2 * A_BYTES + B_BYTES;
     static constexpr int KELEM = 64;
     static constexpr int KSTEP_BYTES = 32;  // one MMA consumes K = 16 bf16
@@ -94,24 +100,66 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
     return false;
 }
 
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1)
+// TMA load into this CTA's shared memory that signals the barrier at shared::cluster
+// address `bar`, which may live in the peer CTA of the pair.
+__device__ __forceinline__ void tma_load_2d_pair(void* dst, const CUtensorMap* map, uint32_t bar, int c0, int c1)
 {
     asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
-            smem_u32(dst)),
-        "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
+        "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(bar), "r"(c0), "r"(c1)
         : "memory");
 }
 
-// TMA load multicast to the CTAs of `mask` (same shared offset and barrier offset in each).
-__device__ __forceinline__ void tma_load_2d_mc(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1,
-                                               uint16_t mask)
+// shared::cluster address of `p` (same offset) in the CTA of rank `rank`.
+__device__ __forceinline__ uint32_t map_rank(const void* p, uint32_t rank)
 {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
-        " [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(smem_u32(dst)),
-        "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "h"(mask)
-        : "memory");
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
+    return r;
+}
+
+// Philox4x32-10 of the counter (c0, c1, c2, c3) for a thread whose c0, c1, c3
+// are fixed over a tile and c2 varies: the first round's c0 product and the
+// key/counter words it is combined with are computed once per tile.
+struct PhiloxFixed {
+    uint32_t n0x;  // c1 ^ k0
+    uint32_t n2;   // hi(MulA * c0) ^ c3 ^ k1
+    uint32_t x3;   // lo(MulA * c0)
+};
+
+__device__ __forceinline__ PhiloxFixed philox_fixed(uint32_t c0, uint32_t c1, uint32_t c3, uint32_t k0, uint32_t k1)
+{
+    uint32_t hA, lA;
+    mulhilo32(kPhiloxMulA, c0, hA, lA);
+    return PhiloxFixed{c1 ^ k0, hA ^ c3 ^ k1, lA};
+}
+
+__device__ __forceinline__ U4 philox_c2(uint32_t c2, const PhiloxFixed& f, uint32_t k0, uint32_t k1)
+{
+    uint32_t hB, lB;
+    mulhilo32(kPhiloxMulB, c2, hB, lB);
+    uint32_t x0 = hB ^ f.n0x, x1 = lB, x2 = f.n2, x3 = f.x3;
+#pragma unroll
+    for (int r = 1; r < 10; ++r) {
+        k0 += kPhiloxWeylA;
+        k1 += kPhiloxWeylB;
+        uint32_t hA2, lA2, hB2, lB2;
+        mulhilo32(kPhiloxMulA, x0, hA2, lA2);
+        mulhilo32(kPhiloxMulB, x2, hB2, lB2);
+        const uint32_t y0 = hB2 ^ x1 ^ k0;
+        const uint32_t y2 = hA2 ^ x3 ^ k1;
+        x0 = y0;
+        x1 = lB2;
+        x2 = y2;
+        x3 = lA2;
+    }
+    return U4{x0, x1, x2, x3};
+}
+
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
 __device__ __forceinline__ uint32_t cluster_rank()
@@ -149,34 +197,31 @@ __host__ __device__ constexpr uint32_t instr_desc(uint32_t ab_format, int M, int
            | ((uint32_t)(M >> 4) << 24);   // M / 16
 }
 
+// One M=256 MMA over the CTA pair: A rows 0..127 and B columns 0..127 from the
+// issuing (even) CTA, A rows 128..255 and B columns 128..255 from its peer, at
+// the same shared-memory offsets; each CTA's tensor memory holds its 128 rows.
 template <int KIND>
 __device__ __forceinline__ void mma_issue(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc)
 {
     if (KIND == 0) {
         asm volatile(
             "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-            " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+            " tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
             "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
     } else {
         asm volatile(
             "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+            " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
             "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
     }
 }
 
-__device__ __forceinline__ void mma_commit(uint64_t* bar)
+// Arrive on the barrier at this shared offset in both CTAs of the pair once the MMAs complete.
+__device__ __forceinline__ void mma_commit_pair(uint64_t* bar)
 {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
-}
-
-// Arrive on the barrier at this shared offset in every CTA of `mask` once the MMAs complete.
-__device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t mask)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
                      smem_u32(bar)),
-                 "h"(mask)
+                 "h"((uint16_t)0x3)
                  : "memory");
 }
 
@@ -213,27 +258,35 @@ __device__ __forceinline__ float warp_transpose_sum(float (&e)[32], int lane)
     return e[0];
 }
 
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-// Persistent kernel.  A cluster is two CTAs; cluster c processes the
-// cluster-tiles ct = c, c + nclusters, ... ; cluster-tile ct is (row pair
-// p = ct % nrp, replica block b = ct / nrp) and the CTA of rank k in the
-// cluster owns row tile 2p + k.  Both CTAs load their own J rows and one
-// half of the shared spin tile, the latter multicast into both; a stage is
-// refilled only after the MMAs of both CTAs have released it.  The FP32
-// accumulator is double-buffered in tensor memory (2 x 256 columns), so the
-// epilogue of one tile runs while the MMAs of the next fill the other buffer.
-template <int KIND>
+// Persistent kernel over CTA pairs (clusters of two).  Cluster c processes
+// the cluster-tiles ct = c, c + nclusters, ...; cluster-tile ct is (row pair
+// p = ct % nrp, replica block b = ct / nrp), a 256-row x 256-replica tile
+// computed by one M=256, N=256 MMA chain over the pair: the CTA of rank k
+// loads row tile 2p + k of J and replicas 128k..128k+127 of the block's spins
+// into its own ring, both signalling the even CTA's "full" barrier; the even
+// CTA issues the MMAs and its commits release the stage in both CTAs.  The
+// FP32 accumulator is double-buffered in tensor memory (2 x 256 columns), so
+// the epilogue of one tile (each CTA its 128 rows) overlaps the MMAs of the
+// next; a buffer is reused once the epilogue warps of both CTAs released it.
+//
+// TABMODE (+-1 couplings) says where the decisions read the threshold row
+// T[F - F_min] of the sweep's beta level:
+//   0  global memory (row too large for shared memory);
+//   1  the dense row, copied into shared memory once per launch;
+//   2  only the window [wlo, wlo + ww) of fields where T is neither 0 nor
+//      2^32 - 1 (plus one saturated entry on each side), copied 32 times so
+//      that lane l reads copy l: a conflict-free shared-memory load.  A field
+//      outside the window is clamped to its edge, which holds the saturated
+//      value, so every decision compares against the same table value.
+template <int KIND, int TABMODE>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     bq_tc_half_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmA2,
                       const __grid_constant__ CUtensorMap tmB, BqJob job, int side, int s, int decide,
-                      float* fields_out, int* err)
+                      float* fields_out, int* err, int wlo, int ww)
 {
     using Cfg = TcCfg<KIND>;
     constexpr int S = Cfg::STAGES;
+    constexpr int NA = KIND == 1 ? 2 : 1;  // J operands per stage
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint32_t* stab = reinterpret_cast<uint32_t*>(smem + S * Cfg::STAGE_BYTES);
@@ -254,35 +307,35 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
 
     if (threadIdx.x == 0) {
         for (int q = 0; q < S; ++q) {
-            mbar_init(&full_bar[q], 1);
-            mbar_init(&empty_bar[q], 2);  // released by the MMAs of both CTAs of the cluster
+            mbar_init(&full_bar[q], 1);   // even CTA: its producer's arrive + both CTAs' bytes
+            mbar_init(&empty_bar[q], 1);  // the pair's MMA commit
         }
         for (int q = 0; q < 2; ++q) {
             mbar_init(&accf_bar[q], 1);
-            mbar_init(&acce_bar[q], kEpiWarps);
+            mbar_init(&acce_bar[q], 2 * kEpiWarps);  // even CTA: epilogue warps of both CTAs
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
                      "r"(2 * TBN));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     }
     __syncthreads();
-    cluster_sync();  // both CTAs' barriers exist before any multicast reaches them
+    cluster_sync();  // both CTAs' barriers exist before any remote signal reaches them
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base;
 
     if (warp == 0) {
-        // ---------------- TMA producer ----------------
+        // ---------------- TMA producer (both CTAs) ----------------
         if (lane == 0) {
             uint32_t g = 0;
             bool ok = true;
             for (int ct = clus; ct < nct && ok; ct += nclus) {
                 const int i0 = (2 * (ct % nrp) + (int)crank) * TBM;
-                const int r0 = (ct / nrp) * TBN;
+                const int r0 = (ct / nrp) * TBN + (int)crank * (TBN / 2);
                 for (int kb = 0; kb < nkb; ++kb, ++g) {
                     const int st = (int)(g % S);
                     const uint32_t ph = (g / S) & 1u;
@@ -292,20 +345,19 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                         break;
                     }
                     unsigned char* sa = smem + st * Cfg::STAGE_BYTES;
-                    mbar_expect_tx(&full_bar[st], (uint32_t)Cfg::STAGE_BYTES);
+                    const uint32_t fb = map_rank(&full_bar[st], 0);
+                    if (crank == 0) mbar_expect_tx(&full_bar[st], (uint32_t)(2 * Cfg::STAGE_BYTES));
                     const int kc = kb * Cfg::KELEM;
-                    tma_load_2d(sa, &tmA, &full_bar[st], kc, i0);
-                    if (KIND == 1) tma_load_2d(sa + Cfg::A_BYTES, &tmA2, &full_bar[st], kc, i0);
-                    // this CTA's half of the shared spin tile, into both CTAs
-                    tma_load_2d_mc(sa + (KIND == 1 ? 2 : 1) * Cfg::A_BYTES + crank * (Cfg::B_BYTES / 2), &tmB,
-                                   &full_bar[st], kc, r0 + (int)crank * (TBN / 2), (uint16_t)0x3);
+                    tma_load_2d_pair(sa, &tmA, fb, kc, i0);
+                    if (KIND == 1) tma_load_2d_pair(sa + Cfg::A_BYTES, &tmA2, fb, kc, i0);
+                    tma_load_2d_pair(sa + NA * Cfg::A_BYTES, &tmB, fb, kc, r0);
                 }
             }
         }
     } else if (warp == 1) {
-        // ---------------- MMA issuer ----------------
-        if (lane == 0) {
-            constexpr uint32_t idesc = instr_desc(KIND == 0 ? 0u : 1u, TBM, TBN);
+        // ---------------- MMA issuer (even CTA only) ----------------
+        if (lane == 0 && crank == 0) {
+            constexpr uint32_t idesc = instr_desc(KIND == 0 ? 0u : 1u, 2 * TBM, TBN);
             uint32_t g = 0, j = 0;
             bool ok = true;
             for (int ct = clus; ct < nct && ok; ct += nclus, ++j) {
@@ -327,7 +379,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const uint32_t sa = smem_u32(smem + st * Cfg::STAGE_BYTES);
-                    const uint32_t sb = sa + (KIND == 1 ? 2 : 1) * Cfg::A_BYTES;
+                    const uint32_t sb = sa + NA * Cfg::A_BYTES;
 #pragma unroll
                     for (int k = 0; k < KBYTES / Cfg::KSTEP_BYTES; ++k) {
                         const uint64_t bd = smem_desc(sb + k * Cfg::KSTEP_BYTES);
@@ -335,9 +387,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                         if (KIND == 1)
                             mma_issue<KIND>(d, smem_desc(sa + Cfg::A_BYTES + k * Cfg::KSTEP_BYTES), bd, idesc, 1u);
                     }
-                    mma_commit_mc(&empty_bar[st], (uint16_t)0x3);
+                    mma_commit_pair(&empty_bar[st]);
                 }
-                mma_commit(&accf_bar[buf]);
+                if (ok) mma_commit_pair(&accf_bar[buf]);
             }
         }
     } else {
@@ -348,12 +400,17 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
         const int et = threadIdx.x - 64;
         constexpr int ET = 32 * kEpiWarps;
         const bool pm1 = KIND == 0;
+        const uint32_t acce_r0 = map_rank(&acce_bar[0], 0), acce_r1 = map_rank(&acce_bar[1], 0);
         float cexp = 0.0f;
-        // threshold row of this sweep's beta level, staged once per launch when it fits
         const uint32_t* trow = pm1 ? job.table + (size_t)(s / job.step) * job.nF : nullptr;
-        const bool staged = pm1 && job.nF * 4 <= Cfg::TAB_BYTES;
-        const uint32_t* tab = staged ? stab : trow;
-        if (staged) {
+        if (TABMODE == 2) {
+            for (int f = et; f < ww; f += ET) {
+                const uint32_t v = __ldg(trow + wlo + f);
+#pragma unroll 8
+                for (int c = 0; c < 32; ++c) stab[f * 32 + ((c + f) & 31)] = v;
+            }
+        }
+        if (TABMODE == 1) {
             for (int f0 = et; f0 < job.nF; f0 += ET * 4) {
                 uint32_t v[4];
 #pragma unroll
@@ -369,6 +426,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
             }
         }
         if (!pm1) cexp = f32_cexp(job.betaf[s / job.step]);
+        // Energy partials of this side: side 1 contributes -b.F_B (F_B includes h_B),
+        // side 0 only -h_A.a, which is zero without a field (its partials stay zero).
+        const bool energy = !fields_out && (side == 1 || job.inst.has_h);
         asm volatile("bar.sync 1, %0;" ::"r"(ET) : "memory");
         uint32_t j = 0;
         bool ok = true;
@@ -387,6 +447,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                                             : job.inst.hf[side * n + i])
                                      : 0.0f;
             const uint32_t taddr = tmem + buf * TBN + ((uint32_t)(quarter * 32) << 16);
+            const PhiloxFixed pf = philox_fixed((uint32_t)i, (uint32_t)s, (kTagDecision << 24) | (uint32_t)side, job.key0,
+                                                job.key1);
             for (int cc = 0; cc < kEpiCols / 32; ++cc) {
                 const int c = slot * (kEpiCols / 32) + cc;
                 float v[32];
@@ -395,9 +457,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                     // this warp has read its part of the accumulator: release the buffer
                     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                     __syncwarp();
-                    if (lane == 0) mbar_arrive(&acce_bar[buf]);
+                    if (lane == 0) mbar_arrive_cluster(buf ? acce_r1 : acce_r0);
                 }
-                float e[32];
+                float e[32];  // energy terms: FP32 (real couplings)
+                int ei[32];   // energy terms: exact integers (+-1 couplings)
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
                     const int rq = r0 + c * 32 + 4 * q;
@@ -411,12 +474,23 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                             for (int b = 0; b < 4; ++b)
                                 if (rq + b < job.R) fields_out[(size_t)(rq + b) * 2 * n + side * n + i] = F[b];
                         } else if (decide) {
-                            const U4 w = philox10((uint32_t)i, (uint32_t)s, (uint32_t)(rq >> 2),
-                                                  (kTagDecision << 24) | (uint32_t)side, job.key0, job.key1);
+                            const U4 w = philox_c2((uint32_t)(rq >> 2), pf, job.key0, job.key1);
                             const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
                             for (int b = 0; b < 4; ++b) {
-                                mn[b] = pm1 ? (ws[b] >= tab[(int)F[b] - job.fmin]) : (decide_f32(ws[b], F[b], cexp) != 0u);
+                                if (pm1) {
+                                    const int f = (int)F[b] - job.fmin;
+                                    uint32_t T;
+                                    if (TABMODE == 2)
+                                        T = stab[(min(max(f, wlo), wlo + ww - 1) - wlo) * 32 + lane];
+                                    else if (TABMODE == 1)
+                                        T = stab[f];
+                                    else
+                                        T = __ldg(trow + f);
+                                    mn[b] = ws[b] >= T;
+                                } else {
+                                    mn[b] = decide_f32(ws[b], F[b], cexp) != 0u;
+                                }
                                 const size_t off = (size_t)(rq + b) * job.ld + i;
                                 if (pm1)
                                     static_cast<uint8_t*>(job.spins[side])[off] = mn[b] ? kE4m3Minus : kE4m3Plus;
@@ -437,11 +511,28 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                         // side 1: -m F (F includes h);  side 0: -h m
                         const float x = (side == 1) ? F[b] : hv;
                         e[4 * q + b] = live ? (mn[b] ? x : -x) : 0.0f;
+                        const int xi = (int)x;
+                        ei[4 * q + b] = live ? (mn[b] ? xi : -xi) : 0;
                     }
                 }
-                if (!fields_out) red[quarter * TBN + c * 32 + lane] = warp_transpose_sum(e, lane);
+                if (energy) {
+                    float colsum;
+                    if (pm1) {
+                        // column sums over the warp's 32 rows, one integer reduction per column
+                        int mine = 0;
+#pragma unroll
+                        for (int k = 0; k < 32; ++k) {
+                            const int t = __reduce_add_sync(0xFFFFFFFFu, ei[k]);
+                            if (lane == k) mine = t;
+                        }
+                        colsum = (float)mine;  // |sum| <= 32 (n + |h|) < 2^24: exact
+                    } else {
+                        colsum = warp_transpose_sum(e, lane);
+                    }
+                    red[quarter * TBN + c * 32 + lane] = colsum;
+                }
             }
-            if (!fields_out) {
+            if (energy) {
                 asm volatile("bar.sync 1, %0;" ::"r"(ET) : "memory");
                 for (int col = et; col < TBN; col += ET) {
                     const float sum = red[col] + red[TBN + col] + red[2 * TBN + col] + red[3 * TBN + col];
@@ -460,7 +551,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     cluster_sync();  // no CTA leaves while its peer may still signal its barriers
     if (warp == 1) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TBN));
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TBN));
     }
 }
 
@@ -506,8 +597,8 @@ int tc_active_clusters(int kind)
     at.val.clusterDim.z = 1;
     cfg.attrs = &at;
     cfg.numAttrs = 1;
-    const cudaError_t e = kind == 0 ? cudaOccupancyMaxActiveClusters(&n, bq_tc_half_kernel<0>, &cfg)
-                                    : cudaOccupancyMaxActiveClusters(&n, bq_tc_half_kernel<1>, &cfg);
+    const cudaError_t e = kind == 0 ? cudaOccupancyMaxActiveClusters(&n, bq_tc_half_kernel<0, 2>, &cfg)
+                                    : cudaOccupancyMaxActiveClusters(&n, bq_tc_half_kernel<1, 0>, &cfg);
     if (e != cudaSuccess || n < 1) {
         (void)cudaGetLastError();
         n = std::max(1, sms / 2);
@@ -544,10 +635,16 @@ cudaError_t bq_tc_make_map(CUtensorMap* map, const void* base, int elem_bytes, u
 
 cudaError_t bq_tc_set_smem()
 {
-    cudaError_t e = cudaFuncSetAttribute(bq_tc_half_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(bq_tc_half_kernel<0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)bq_tc_smem_bytes(0));
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(bq_tc_half_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(bq_tc_half_kernel<0, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)bq_tc_smem_bytes(0));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(bq_tc_half_kernel<0, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)bq_tc_smem_bytes(0));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(bq_tc_half_kernel<1, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)bq_tc_smem_bytes(1));
     if (e != cudaSuccess) return e;
     tc_active_clusters(0);  // occupancy queries outside any stream capture
@@ -556,7 +653,7 @@ cudaError_t bq_tc_set_smem()
 }
 
 cudaError_t bq_launch_tc_half(const BqTcMaps& maps, const BqJob& job, int side, int s, int decide, float* fields_out,
-                              int* err, cudaStream_t st)
+                              int* err, int wlo, int ww, cudaStream_t st)
 {
     const int kind = job.inst.jtype == PB_J_PM1_I8 ? 0 : 1;
     const size_t smem = bq_tc_smem_bytes(kind);
@@ -567,10 +664,15 @@ cudaError_t bq_launch_tc_half(const BqTcMaps& maps, const BqJob& job, int side, 
     const CUtensorMap& A = side == 0 ? maps.a[0] : maps.a[2];
     const CUtensorMap& A2 = side == 0 ? maps.a[1] : maps.a[3];
     const CUtensorMap& B = maps.b[1 - side];
-    if (kind == 0)
-        bq_tc_half_kernel<0><<<grid, kThreads, smem, st>>>(A, A2, B, job, side, s, decide, fields_out, err);
+    const bool use_win = decide && ww > 0 && ww <= kBqTcWindowMax && wlo >= 0 && wlo + ww <= job.nF;
+    if (kind == 0 && use_win)
+        bq_tc_half_kernel<0, 2><<<grid, kThreads, smem, st>>>(A, A2, B, job, side, s, decide, fields_out, err, wlo, ww);
+    else if (kind == 0 && job.nF * 4 <= TcCfg<0>::TAB_BYTES)
+        bq_tc_half_kernel<0, 1><<<grid, kThreads, smem, st>>>(A, A2, B, job, side, s, decide, fields_out, err, 0, 0);
+    else if (kind == 0)
+        bq_tc_half_kernel<0, 0><<<grid, kThreads, smem, st>>>(A, A2, B, job, side, s, decide, fields_out, err, 0, 0);
     else
-        bq_tc_half_kernel<1><<<grid, kThreads, smem, st>>>(A, A2, B, job, side, s, decide, fields_out, err);
+        bq_tc_half_kernel<1, 0><<<grid, kThreads, smem, st>>>(A, A2, B, job, side, s, decide, fields_out, err, 0, 0);
     return cudaGetLastError();
 }
 

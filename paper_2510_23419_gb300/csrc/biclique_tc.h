@@ -17,12 +17,15 @@ struct BqTcMaps {
 
 constexpr int kBqTcRows = 128;   // rows of a tile (tensor-memory lanes)
 constexpr int kBqTcReps = 256;   // replicas of a tile (accumulator columns)
+constexpr int kBqTcWindowMax = 256;  // widest threshold window kept as 32 conflict-free copies
 
 size_t bq_tc_smem_bytes(int kind);
 cudaError_t bq_tc_set_smem();
 cudaError_t bq_tc_make_map(CUtensorMap* map, const void* base, int elem_bytes, uint64_t cols, uint64_t rows,
                            uint64_t ld_bytes, int box_rows);
+// wlo, ww: the unsaturated window of the threshold row of sweep s's level
+// (first index and width, see the kernel); ww = 0 when not known.
 cudaError_t bq_launch_tc_half(const BqTcMaps& maps, const BqJob& job, int side, int s, int decide, float* fields_out,
-                              int* err, cudaStream_t st);
+                              int* err, int wlo, int ww, cudaStream_t st);
 
 }  // namespace pb

@@ -142,3 +142,20 @@ def test_tensor_sampled_large(pb, orc):
         o = orc.anneal(eu, ev, Jd, None, col, ob, 1, 9, r_first=r)
         assert np.array_equal(o["final_state"][0], g["final_state"][r])
         assert o["best_E"][0] == g["best_E"][r] and o["best_sweep"][0] == g["best_sweep"][r]
+
+
+def test_tensor_threshold_row_in_global_memory(pb, orc):
+    """n = 4300 at small beta: the threshold row (2n + 1 entries) is larger than the
+    shared-memory table region and its unsaturated window is wider than 256, so the
+    decisions read it from global memory.  Two replicas replayed on the oracle."""
+    n, R, S = 4300, 256, 3
+    J = pb.pb_generate_biclique(n, pb.PB_DIST_PM1, 15)
+    sc = pb.make_schedule(pb.PB_SCHED_LINEAR, S, 0.001, 0.004)
+    g = _gpu(pb, n, J, None, sc, R, 19, "tensor")
+    ob = orc.schedule(orc.SCHED_LINEAR, 0.001, 0.004, S)
+    eu, ev, col = orc.biclique_graph(n)
+    Jd = J.astype(np.float64).reshape(-1)
+    for r in (0, 255):
+        o = orc.anneal(eu, ev, Jd, None, col, ob, 1, 19, r_first=r)
+        assert np.array_equal(o["final_state"][0], g["final_state"][r])
+        assert o["best_E"][0] == g["best_E"][r] and o["best_sweep"][0] == g["best_sweep"][r]
