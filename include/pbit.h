@@ -159,14 +159,79 @@ pb_status pb_anneal(pb_instance* inst, const pb_schedule* sched, int32_t replica
 pb_status pb_anneal_ex(pb_instance* inst, const pb_schedule* sched, int32_t replicas, uint64_t seed,
                        const pb_anneal_opts* opts, void* stream, pb_run** out);
 
-/* Start `count` anneals that share ONE persistent launch on `stream` (EA
- * resident form; every instance must be EA).  Replica blocks of all jobs are
- * scheduled longest-first over all SMs.  Arrays have `count` entries; `opts`
- * may be NULL; outs[k] receives the run of job k.  Results are identical to
- * running each job alone.  Errors as pb_anneal; on error no run is returned. */
+/* Start `count` independent anneals of any topology as one batch, ordered on
+ * `stream` like a single launch (the batch starts after the work queued on
+ * `stream`, and `stream` waits for all of it).  All EA jobs that fit the
+ * resident form share ONE persistent, graph-captured launch whose replica
+ * blocks are scheduled longest first over all SMs; every biclique job, and EA
+ * jobs too large for the resident form, run as one graph-captured anneal each,
+ * spread longest first over the library's launch streams so that small jobs
+ * run side by side.  Forms left at PB_FORM_AUTO come from the autotuner's
+ * table (pb_autotune) when it has an entry for the job's shape.  Arrays have
+ * `count` entries; `opts` may be NULL; outs[k] receives the run of job k.
+ * Results are identical to running each job alone.  Errors as pb_anneal; on
+ * error no run is returned. */
 pb_status pb_anneal_batch(int32_t count, pb_instance* const* insts, const pb_schedule* scheds,
                           const int32_t* replicas, const uint64_t* seeds, const pb_anneal_opts* opts,
                           void* stream, pb_run** outs);
+
+/* Autotuner.  Times each candidate launch choice for `inst` with `replicas`
+ * replicas on a short probe anneal of `probe_sweeps` sweeps (linear beta
+ * 0.1 -> 3.0) on `stream`: EA resident form with every valid tile width (replica
+ * words per tile) and the plain form; biclique tensor and CUDA-core forms.  The
+ * cost of a candidate is its sweep-loop time times the SMs it keeps busy (a
+ * batch fills the SMs that a small job leaves idle); the cheapest is returned
+ * and stored in a process-wide table keyed by (topology, L or n, coupling type,
+ * field present, ceil(log2 replicas)), which PB_FORM_AUTO jobs of pb_anneal_ex
+ * and pb_anneal_batch then use.  Synchronous. */
+typedef struct pb_tune_result {
+    int32_t form;              /* chosen pb_form */
+    int32_t tile_width;        /* EA resident: replica words (4 replicas each) per tile; else 0 */
+    int32_t n_candidates;
+    int32_t candidate_form[8];
+    int32_t candidate_wt[8];
+    float probe_ms[8];         /* sweep-loop time of each candidate */
+} pb_tune_result;
+pb_status pb_autotune(pb_instance* inst, int32_t replicas, int32_t probe_sweeps, void* stream, pb_tune_result* out);
+/* Forget every autotuner entry. */
+void pb_autotune_clear(void);
+
+/* Device bytes that a run of `inst` with these arguments holds (state, best
+ * states, tables, readout buffers), as used by the request server's admission.
+ * Returns -1 on invalid arguments. */
+int64_t pb_run_footprint(const pb_instance* inst, const pb_schedule* sched, int32_t replicas, const pb_anneal_opts* opts);
+
+/* Request server with continuous batching.  A loop thread admits submitted
+ * anneals in arrival order while their device footprint fits the budget and
+ * fewer than max_inflight are on the device; every admission round is one
+ * batch (pb_anneal_batch semantics, no join), started on the library's launch
+ * streams while earlier rounds are still running, so arrivals overlap with work
+ * in flight.  Run state stays on the device until the caller takes the run.
+ * Results are the same as the same anneal run alone. */
+typedef struct pb_server pb_server;
+typedef struct pb_server_opts {
+    int64_t max_device_bytes;  /* admission budget; 0 = 80% of the device memory free at creation */
+    int32_t max_inflight;      /* 0 = 1024 */
+    int32_t gather_us;         /* a round waits this long for more arrivals after the first (0 = none) */
+} pb_server_opts;
+typedef struct pb_server_stats {
+    int64_t submitted, admitted, completed, failed, queued, inflight;
+    int64_t inflight_bytes, peak_inflight_bytes, rounds;
+    double p50_ms, p99_ms, mean_ms, max_ms;  /* latency from submit to result ready, completed jobs */
+} pb_server_stats;
+pb_status pb_server_create(const pb_server_opts* opts, pb_server** out);
+/* Queue an anneal; the instance (and an explicit schedule's betas) must stay
+ * valid until the ticket is waited for.  PB_EINVAL if the job alone exceeds the
+ * budget. */
+pb_status pb_server_submit(pb_server* sv, pb_instance* inst, const pb_schedule* sched, int32_t replicas,
+                           uint64_t seed, const pb_anneal_opts* opts, int64_t* ticket);
+/* Wait for a ticket: PB_OK and the finished run (owned by the caller, destroy
+ * with pb_run_destroy) and its latency in ms; PB_ETIMEOUT after timeout_ms
+ * (< 0 = no limit); the run's own error if it failed.  A ticket is waited for once. */
+pb_status pb_server_wait(pb_server* sv, int64_t ticket, int32_t timeout_ms, pb_run** run, double* latency_ms);
+pb_status pb_server_stats_get(pb_server* sv, pb_server_stats* out);
+/* Stop admitting, wait for the work on the device, destroy unclaimed runs. */
+void pb_server_destroy(pb_server* sv);
 
 /* Wait for a run (host side): PB_OK when finished, PB_ETIMEOUT after timeout_ms
  * (< 0 = no limit), PB_EDEVICE if a kernel of the run failed. */

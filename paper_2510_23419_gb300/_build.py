@@ -18,7 +18,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpbit.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
-SOURCES = ["ea.cu", "biclique.cu", "biclique_tc.cu", "noalloc.cu", "host_api.cpp", "biclique_host.cpp"]
+SOURCES = ["ea.cu", "biclique.cu", "biclique_tc.cu", "noalloc.cu", "host_api.cpp", "biclique_host.cpp", "pool.cpp",
+           "batch.cpp", "server.cpp"]
 
 
 def _nvcc() -> str:
@@ -67,7 +68,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
     with cf.ThreadPoolExecutor(max_workers=min(8, len(SOURCES))) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc, ARCH, "-shared", "-o", tmp] + objs + ["-cudart", "static"]
+    cmd = [nvcc, ARCH, "-shared", "-o", tmp] + objs + ["-cudart", "static", "-lpthread"]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"link failed:\n{res.stdout}\n{res.stderr}")

@@ -1,0 +1,366 @@
+// batch.cpp -- batched anneals of mixed topology and the autotuner
+// (arXiv 2510.23419: many independent annealing runs, Sec. 1.2.2 update
+// groups, the instance families of Sec. 2 and Sec. 3).
+//
+// A batch prepares every job first (allocations, threshold tables, copies on
+// the caller's stream, one synchronisation), then launches:
+//   * all EA jobs that fit the resident form share ONE persistent launch,
+//     graph-captured, whose replica tiles are scheduled longest first;
+//   * every biclique job (and every EA job too large for the resident form) is
+//     one graph-captured anneal, spread longest-first over the library's
+//     launch streams so that small jobs run side by side on separate SMs.
+// The launch streams wait for the caller's stream before they start and the
+// caller's stream waits for all of them at the end, so the batch is ordered
+// on the caller's stream like a single launch.
+//
+// The autotuner times candidate launch choices of an instance on a short probe
+// anneal and keeps the cheapest per (topology, size, coupling type, field,
+// replica bucket) in a process-wide table that pb_anneal_ex and
+// pb_anneal_batch read when the caller leaves the form to the library.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "pb_handles.h"
+
+namespace pb {
+
+namespace {
+
+// ------------------------------------------------------------------ tuning table
+using TuneKey = std::tuple<int, int, int, int, int>;  // topo, size, jtype, has_h, ceil(log2 R)
+
+struct TuneEntry {
+    int form = PB_FORM_AUTO;
+    int wt = 0;
+};
+
+std::mutex g_tune_mutex;
+std::map<TuneKey, TuneEntry> g_tune;
+
+int log2_bucket(int R)
+{
+    int b = 0;
+    while ((1 << b) < R && b < 30) ++b;
+    return b;
+}
+
+TuneKey tune_key(const pb_instance* I, int R)
+{
+    return TuneKey{I->topo, I->topo == PB_TOPO_EA3D ? I->L : I->n, I->jtype, I->has_h, log2_bucket(R)};
+}
+
+bool tune_lookup(const pb_instance* I, int R, TuneEntry& out)
+{
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tune.find(tune_key(I, R));
+    if (it == g_tune.end()) return false;
+    out = it->second;
+    return true;
+}
+
+// ------------------------------------------------------------------ cost model
+// Rough device-time estimate (seconds) of a job, only used to order work
+// longest first; rates are round figures of the forms on one GB300.
+double est_cost(const pb_instance* I, int R, int S, int form)
+{
+    const double upd = (double)I->N * R * std::max(1, S);
+    if (I->topo == PB_TOPO_EA3D) return upd / (form == PB_FORM_PLAIN ? 9e10 : 7e11);
+    const double flop = upd * 2.0 * I->n * (I->jtype == PB_J_F32 ? 2.0 : 1.0);
+    const double rate = form == PB_FORM_CUDACORE ? 2.5e13 : (I->jtype == PB_J_F32 ? 1.5e15 : 1.8e15);
+    // small instances fill a fraction of the tensor tiles
+    const double fill = form == PB_FORM_TENSOR ? std::min(1.0, (double)I->n / 256.0) * std::min(1.0, R / 256.0) : 1.0;
+    return flop / (rate * std::max(0.02, fill)) + 3.0 * std::max(1, S) * 2e-6;
+}
+
+struct Job {
+    int q;
+    pb_instance* I;
+    int R, S, form, wt;
+    double cost;
+};
+
+}  // namespace
+
+// Form and tile width the library picks for a job whose caller left the form open.
+void choose_form(const pb_instance* I, int R, int requested, int& form, int& wt)
+{
+    form = requested;
+    wt = 0;
+    TuneEntry te;
+    const bool tuned = requested == PB_FORM_AUTO && tune_lookup(I, R, te);
+    if (I->topo == PB_TOPO_EA3D) {
+        const int nF = 2 * (6 + I->hmax) + 1;
+        const int wmax = ea_choose_wt(I, R, nF);
+        if (tuned) {
+            form = te.form;
+            wt = std::min(te.wt, wmax);
+            if (form == PB_FORM_RESIDENT && wt < 1) form = PB_FORM_AUTO;
+            if (form != PB_FORM_AUTO) return;
+        }
+        if (form == PB_FORM_AUTO || form == PB_FORM_RESIDENT) {
+            if (wmax > 0) {
+                form = PB_FORM_RESIDENT;
+                wt = wmax;
+            } else {
+                form = requested == PB_FORM_RESIDENT ? PB_FORM_RESIDENT : PB_FORM_PLAIN;
+            }
+        }
+    } else {
+        if (tuned) form = te.form;
+        if (form == PB_FORM_AUTO) form = PB_FORM_TENSOR;
+    }
+}
+
+// Set up and launch a batch.  Set-up runs on `setup_st`; jobs start after the
+// work already queued on `setup_st`.  With `join`, `setup_st` waits for every
+// job at the end.  `load` (per launch stream, seconds of queued work) picks the
+// stream of each job and is updated with the job's estimated cost; `costs`
+// receives each job's estimate.
+pb_status batch_start(int count, pb_instance* const* insts, const pb_schedule* scheds, const int32_t* replicas,
+                      const uint64_t* seeds, const pb_anneal_opts* opts, cudaStream_t setup_st, bool join,
+                      std::vector<double>* load_io, std::vector<std::unique_ptr<pb_run>>& runs_out,
+                      std::vector<double>* costs, std::vector<int>* stream_of)
+{
+    if (count < 1 || !insts || !scheds || !replicas || !seeds) return fail(PB_EINVAL, "null or empty batch");
+    cudaStream_t st = setup_st;
+    std::vector<Job> jobs;
+    for (int q = 0; q < count; ++q) {
+        pb_instance* I = insts[q];
+        if (!I) return fail(PB_EINVAL, "null instance in batch");
+        if (replicas[q] < 1) return fail(PB_EINVAL, "replicas must be >= 1");
+        int form = 0, wt = 0;
+        choose_form(I, replicas[q], opts ? opts[q].form : PB_FORM_AUTO, form, wt);
+        if (I->topo == PB_TOPO_EA3D) {
+            if (form == PB_FORM_RESIDENT && wt == 0) return fail(PB_EUNSUPPORTED, "lattice too large for the resident form");
+            if (form != PB_FORM_RESIDENT && form != PB_FORM_PLAIN)
+                return fail(PB_EUNSUPPORTED, "form not available for EA instances");
+        } else if (form != PB_FORM_TENSOR && form != PB_FORM_CUDACORE) {
+            return fail(PB_EUNSUPPORTED, "form not available for biclique instances");
+        }
+        jobs.push_back(Job{q, I, replicas[q], scheds[q].n_sweeps, form, wt, est_cost(I, replicas[q], scheds[q].n_sweeps, form)});
+    }
+    // EA resident jobs: too few tiles for the SMs -> halve the widest replica blocks
+    {
+        const int sms = sm_count();
+        long long tiles = 0;
+        for (const Job& j : jobs)
+            if (j.form == PB_FORM_RESIDENT) tiles += ((j.R + 3) / 4 + j.wt - 1) / j.wt;
+        while (tiles > 0 && tiles < sms) {
+            Job* wide = nullptr;
+            for (Job& j : jobs)
+                if (j.form == PB_FORM_RESIDENT && j.wt > 1 && (!wide || j.wt > wide->wt)) wide = &j;
+            if (!wide) break;
+            const int Rw = (wide->R + 3) / 4;
+            tiles -= (Rw + wide->wt - 1) / wide->wt;
+            wide->wt /= 2;
+            tiles += (Rw + wide->wt - 1) / wide->wt;
+        }
+    }
+
+    // ---- set-up of every job on the caller's stream
+    std::vector<std::unique_ptr<pb_run>> runs(count);
+    std::vector<pb_run*> resident;
+    for (const Job& j : jobs) {
+        runs[j.q].reset(new (std::nothrow) pb_run());
+        if (!runs[j.q]) return fail(PB_ENOMEM, "host allocation failed");
+        pb_run* r = runs[j.q].get();
+        const pb_anneal_opts* o = opts ? &opts[j.q] : nullptr;
+        pb_status ps;
+        if (j.I->topo == PB_TOPO_EA3D) {
+            ps = ea_prepare_run(r, j.I, &scheds[j.q], j.R, seeds[j.q], o, j.form, j.wt, st);
+            if (ps == PB_OK && j.form == PB_FORM_RESIDENT) resident.push_back(r);
+        } else {
+            pb_anneal_opts oo = o ? *o : pb_anneal_opts{PB_FORM_AUTO, 0, NAN};
+            oo.form = j.form;
+            ps = bq_setup(r, j.I, &scheds[j.q], j.R, seeds[j.q], &oo, st);
+        }
+        if (ps != PB_OK) return ps;
+    }
+    std::shared_ptr<BatchShared> ea_shared;
+    if (!resident.empty()) {
+        pb_status ps = ea_batch_setup(resident, st, ea_shared);
+        if (ps != PB_OK) return ps;
+    }
+
+    // ---- launch: fork from the caller's stream, one stream for the EA batch,
+    //      the other jobs longest first onto the least loaded stream
+    cudaEvent_t fork = nullptr;
+    PB_CUDA_TRY(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    PB_CUDA_TRY(cudaEventRecord(fork, st));
+    const int ns = pool_streams();
+    std::vector<double> local_load(ns, 0.0);
+    std::vector<double>& load = load_io ? *load_io : local_load;
+    if ((int)load.size() < ns) load.resize(ns, 0.0);
+    if (costs) costs->assign(count, 0.0);
+    if (stream_of) stream_of->assign(count, -1);
+    std::vector<char> used(ns, 0);
+    auto start_on = [&](int k) -> pb_status {
+        if (!used[k]) {
+            PB_CUDA_TRY(cudaStreamWaitEvent(pool_stream(k), fork, 0));
+            used[k] = 1;
+        }
+        return PB_OK;
+    };
+    int ea_k = -1;
+    if (!resident.empty()) {
+        ea_k = 0;
+        for (int c = 1; c < ns; ++c)
+            if (load[c] < load[ea_k]) ea_k = c;
+        pb_status ps = start_on(ea_k);
+        if (ps != PB_OK) return ps;
+        for (const Job& j : jobs)
+            if (j.form == PB_FORM_RESIDENT) {
+                load[ea_k] += j.cost;
+                if (costs) (*costs)[j.q] = j.cost;
+                if (stream_of) (*stream_of)[j.q] = ea_k;
+            }
+        for (pb_run* r : resident) r->stream = pool_stream(ea_k);
+        ps = ea_batch_launch(resident, ea_shared, pool_stream(ea_k));
+        if (ps != PB_OK) return ps;
+    }
+    std::vector<const Job*> rest;
+    for (const Job& j : jobs)
+        if (j.form != PB_FORM_RESIDENT) rest.push_back(&j);
+    std::stable_sort(rest.begin(), rest.end(), [](const Job* a, const Job* b) { return a->cost > b->cost; });
+    for (const Job* j : rest) {
+        int k = -1;
+        for (int c = 0; c < ns; ++c)
+            if (c != ea_k && (k < 0 || load[c] < load[k])) k = c;
+        pb_status ps = start_on(k);
+        if (ps != PB_OK) return ps;
+        load[k] += j->cost;
+        if (costs) (*costs)[j->q] = j->cost;
+        if (stream_of) (*stream_of)[j->q] = k;
+        pb_run* r = runs[j->q].get();
+        r->stream = pool_stream(k);
+        ps = (j->I->topo == PB_TOPO_EA3D) ? ea_enqueue_plain(r, pool_stream(k)) : bq_launch(r, pool_stream(k));
+        if (ps != PB_OK) return ps;
+    }
+    // ---- join back into the caller's stream
+    for (int k = 0; k < ns && join; ++k) {
+        if (!used[k]) continue;
+        cudaEvent_t join = nullptr;
+        PB_CUDA_TRY(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
+        PB_CUDA_TRY(cudaEventRecord(join, pool_stream(k)));
+        PB_CUDA_TRY(cudaStreamWaitEvent(st, join, 0));
+        cudaEventDestroy(join);  // released once it has completed
+    }
+    cudaEventDestroy(fork);
+    runs_out = std::move(runs);
+    return PB_OK;
+}
+
+}  // namespace pb
+
+using namespace pb;
+
+extern "C" {
+
+pb_status pb_anneal_batch(int32_t count, pb_instance* const* insts, const pb_schedule* scheds, const int32_t* replicas,
+                          const uint64_t* seeds, const pb_anneal_opts* opts, void* stream, pb_run** outs)
+{
+    if (count < 1 || !outs) return fail(PB_EINVAL, "null or empty batch");
+    for (int q = 0; q < count; ++q) outs[q] = nullptr;
+    std::vector<std::unique_ptr<pb_run>> runs;
+    pb_status ps = batch_start(count, insts, scheds, replicas, seeds, opts, static_cast<cudaStream_t>(stream), true,
+                               nullptr, runs, nullptr, nullptr);
+    if (ps != PB_OK) return ps;
+    for (int q = 0; q < count; ++q) outs[q] = runs[q].release();
+    return PB_OK;
+}
+
+
+
+pb_status pb_autotune(pb_instance* I, int32_t R, int32_t probe_sweeps, void* stream, pb_tune_result* out)
+{
+    if (!I || !out) return fail(PB_EINVAL, "null argument");
+    if (R < 1) return fail(PB_EINVAL, "replicas must be >= 1");
+    const int S = std::max(2, std::min(probe_sweeps > 0 ? probe_sweeps : 8, 1000));
+    *out = pb_tune_result{};
+    for (int c = 0; c < 8; ++c) out->probe_ms[c] = NAN;
+    std::vector<std::pair<int, int>> cand;  // form, WT
+    if (I->topo == PB_TOPO_EA3D) {
+        const int nF = 2 * (6 + I->hmax) + 1;
+        const int wmax = ea_choose_wt(I, R, nF);
+        for (int w = 1; w <= wmax && cand.size() < 7; w *= 2) cand.push_back({PB_FORM_RESIDENT, w});
+        cand.push_back({PB_FORM_PLAIN, 0});
+    } else {
+        cand.push_back({PB_FORM_TENSOR, 0});
+        cand.push_back({PB_FORM_CUDACORE, 0});
+    }
+    pb_schedule sc{};
+    sc.kind = PB_SCHED_LINEAR;
+    sc.n_sweeps = S;
+    sc.step_duration = 1;
+    sc.beta0 = 0.1;
+    sc.beta1 = 3.0;
+    const int sms = sm_count();
+    double best = INFINITY;
+    int bi = -1;
+    for (size_t c = 0; c < cand.size(); ++c) {
+        const int form = cand[c].first, wt = cand[c].second;
+        pb_anneal_opts o{form, 0, NAN};
+        std::unique_ptr<pb_run> run(new (std::nothrow) pb_run());
+        if (!run) return fail(PB_ENOMEM, "host allocation failed");
+        cudaStream_t st = static_cast<cudaStream_t>(stream);
+        pb_status ps;
+        int units = sms;  // SMs the form keeps busy
+        if (I->topo == PB_TOPO_EA3D) {
+            ps = ea_prepare_run(run.get(), I, &sc, R, 1, &o, form, wt, st);
+            if (ps == PB_OK && form == PB_FORM_RESIDENT) {
+                std::vector<pb_run*> v{run.get()};
+                std::shared_ptr<BatchShared> sh;
+                ps = ea_batch_setup(v, st, sh);
+                if (ps == PB_OK) ps = ea_batch_launch(v, sh, st);
+                units = std::min(sms, run->job.n_tiles);
+            } else if (ps == PB_OK) {
+                ps = ea_enqueue_plain(run.get(), st);
+            }
+        } else {
+            ps = bq_setup(run.get(), I, &sc, R, 1, &o, st);
+            if (ps == PB_OK) ps = bq_launch(run.get(), st);
+            if (form == PB_FORM_TENSOR) {
+                const int nrp = ((I->n + 127) / 128 + 1) / 2;
+                units = std::min(sms, 2 * nrp * ((R + 255) / 256));
+            } else {
+                units = std::min(sms, ((I->n + 63) / 64) * ((R + 63) / 64));
+            }
+        }
+        if (ps != PB_OK) return ps;
+        ps = wait_run(run.get(), -1);
+        if (ps != PB_OK) return ps;
+        float ms = 0.0f;
+        PB_CUDA_TRY(cudaEventElapsedTime(&ms, run->batch && run->batch->ev_k0 ? run->batch->ev_k0 : run->ev_k0,
+                                         run->batch && run->batch->ev_k1 ? run->batch->ev_k1 : run->ev_k1));
+        out->candidate_form[c] = form;
+        out->candidate_wt[c] = wt;
+        out->probe_ms[c] = ms;
+        // cost in SM-time: a batch fills the SMs a small job leaves idle
+        const double cost = (double)ms * units;
+        if (cost < best) {
+            best = cost;
+            bi = (int)c;
+        }
+    }
+    out->n_candidates = (int32_t)cand.size();
+    out->form = cand[bi].first;
+    out->tile_width = cand[bi].second;
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune[tune_key(I, R)] = TuneEntry{out->form, out->tile_width};
+    return PB_OK;
+}
+
+void pb_autotune_clear(void)
+{
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune.clear();
+}
+
+}  // extern "C"

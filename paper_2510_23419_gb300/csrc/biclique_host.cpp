@@ -317,22 +317,27 @@ static pb_status bq_enqueue_body(pb_run* run, cudaStream_t st)
     return PB_OK;
 }
 
-pb_status bq_anneal(pb_run* run, pb_instance* I, const pb_schedule* sc, int R, uint64_t seed,
-                    const pb_anneal_opts* opts, cudaStream_t st)
+pb_status bq_setup(pb_run* run, pb_instance* I, const pb_schedule* sc, int R, uint64_t seed,
+                   const pb_anneal_opts* opts, cudaStream_t st)
 {
     int form = opts ? opts->form : PB_FORM_AUTO;
     if (form == PB_FORM_AUTO) form = PB_FORM_TENSOR;
     if (form != PB_FORM_TENSOR && form != PB_FORM_CUDACORE)
         return fail(PB_EUNSUPPORTED, "form not available for biclique instances");
-    pb_status ps = bq_prepare(run, I, sc, R, seed, opts, form, st);
-    if (ps != PB_OK) return ps;
+    return bq_prepare(run, I, sc, R, seed, opts, form, st);
+}
+
+// The whole anneal (initial state, sweeps, readout) as one CUDA graph when the
+// stream allows capture.
+pb_status bq_launch(pb_run* run, cudaStream_t st)
+{
     PB_CUDA_TRY(cudaEventRecord(run->ev_start, st));
     const bool capture = st != nullptr && st != cudaStreamLegacy && st != cudaStreamPerThread;
     if (capture) {
         auto shared = std::make_shared<BatchShared>();
         cudaGraph_t graph = nullptr;
         PB_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-        ps = bq_enqueue_body(run, st);
+        pb_status ps = bq_enqueue_body(run, st);
         cudaError_t e = cudaStreamEndCapture(st, &graph);
         if (ps != PB_OK) {
             if (graph) cudaGraphDestroy(graph);
@@ -345,11 +350,19 @@ pb_status bq_anneal(pb_run* run, pb_instance* I, const pb_schedule* sc, int R, u
         PB_CUDA_TRY(cudaGraphLaunch(shared->exec, st));
         run->batch = shared;
     } else {
-        ps = bq_enqueue_body(run, st);
+        pb_status ps = bq_enqueue_body(run, st);
         if (ps != PB_OK) return ps;
     }
     PB_CUDA_TRY(cudaEventRecord(run->ev_stop, st));
     return PB_OK;
+}
+
+pb_status bq_anneal(pb_run* run, pb_instance* I, const pb_schedule* sc, int R, uint64_t seed,
+                    const pb_anneal_opts* opts, cudaStream_t st)
+{
+    pb_status ps = bq_setup(run, I, sc, R, seed, opts, st);
+    if (ps != PB_OK) return ps;
+    return bq_launch(run, st);
 }
 
 pb_status bq_fields(pb_instance* I, const int8_t* d_states, int R, int form, float* d_out, cudaStream_t st)

@@ -240,7 +240,7 @@ static pb_status ea_build(pb_instance* I, const pb_instance_desc* d, cudaStream_
 // ---------------------------------------------------------------------------
 // EA runs
 // ---------------------------------------------------------------------------
-static pb_status ea_prepare_run(pb_run* run, pb_instance* I, const pb_schedule* sc, int R, uint64_t seed,
+pb_status ea_prepare_run(pb_run* run, pb_instance* I, const pb_schedule* sc, int R, uint64_t seed,
                                 const pb_anneal_opts* opts, int form, int WT, cudaStream_t st)
 {
     std::vector<double> betas;
@@ -325,7 +325,7 @@ static pb_status ea_enqueue_readout(pb_run* run, cudaStream_t st)
     return PB_OK;
 }
 
-static pb_status ea_enqueue_plain(pb_run* run, cudaStream_t st)
+pb_status ea_enqueue_plain(pb_run* run, cudaStream_t st)
 {
     const EaJob& j = run->job;
     PB_CUDA_TRY(cudaEventCreate(&run->ev_k0));
@@ -350,8 +350,10 @@ struct TileCost {
     double cost;
 };
 
-// One persistent launch for all jobs: tiles ordered longest first.
-static pb_status ea_enqueue_resident(std::vector<pb_run*>& runs, cudaStream_t st)
+// One persistent launch for all jobs: tiles ordered longest first.  Set-up
+// (device arrays of jobs and work items) and launch are separate so that a
+// batch can prepare all of its jobs before any of them starts.
+pb_status ea_batch_setup(std::vector<pb_run*>& runs, cudaStream_t st, std::shared_ptr<BatchShared>& out)
 {
     auto shared = std::make_shared<BatchShared>();
     PB_CUDA_TRY(cudaEventCreate(&shared->ev_k0));
@@ -375,9 +377,16 @@ static pb_status ea_enqueue_resident(std::vector<pb_run*>& runs, cudaStream_t st
     PB_CUDA_TRY(cudaMemcpyAsync(shared->jobs.p, jobs.data(), jobs.size() * sizeof(EaJob), cudaMemcpyHostToDevice, st));
     PB_CUDA_TRY(cudaMemcpyAsync(shared->work.p, work.data(), work.size() * sizeof(EaWork), cudaMemcpyHostToDevice, st));
     PB_CUDA_TRY(cudaStreamSynchronize(st));
-    const int grid = std::max(1, std::min<int>((int)work.size(), sm_count()));
+    shared->n_work = (int)work.size();
+    shared->grid = std::max(1, std::min<int>((int)work.size(), sm_count()));
+    shared->smem = smem;
     PB_CUDA_TRY(ea_resident_set_smem(smem));
+    out = shared;
+    return PB_OK;
+}
 
+pb_status ea_batch_launch(std::vector<pb_run*>& runs, const std::shared_ptr<BatchShared>& shared, cudaStream_t st)
+{
     // The launch sequence (counter reset, persistent kernel, readouts) is
     // captured into a CUDA graph when the stream allows capture.
     const bool capture = st != nullptr && st != cudaStreamLegacy && st != cudaStreamPerThread;
@@ -389,8 +398,8 @@ static pb_status ea_enqueue_resident(std::vector<pb_run*>& runs, cudaStream_t st
         // inside a capture an event becomes a graph node only when recorded as external
         const unsigned evf = capture ? cudaEventRecordExternal : cudaEventRecordDefault;
         PB_CUDA_TRY(cudaEventRecordWithFlags(shared->ev_k0, st, evf));
-        PB_CUDA_TRY(ea_launch_resident(shared->jobs.as<EaJob>(), shared->work.as<EaWork>(), (int)work.size(),
-                                       shared->counter.as<int>(), smem, grid, st));
+        PB_CUDA_TRY(ea_launch_resident(shared->jobs.as<EaJob>(), shared->work.as<EaWork>(), shared->n_work,
+                                       shared->counter.as<int>(), shared->smem, shared->grid, st));
         PB_CUDA_TRY(cudaEventRecordWithFlags(shared->ev_k1, st, evf));
         for (pb_run* r : runs) {
             pb_status ps = ea_enqueue_readout(r, st);
@@ -422,12 +431,20 @@ static pb_status ea_enqueue_resident(std::vector<pb_run*>& runs, cudaStream_t st
     return PB_OK;
 }
 
-static int ea_choose_wt(const pb_instance* I, int R, int nF)
+static pb_status ea_enqueue_resident(std::vector<pb_run*>& runs, cudaStream_t st)
+{
+    std::shared_ptr<BatchShared> shared;
+    pb_status ps = ea_batch_setup(runs, st, shared);
+    if (ps != PB_OK) return ps;
+    return ea_batch_launch(runs, shared, st);
+}
+
+int ea_choose_wt(const pb_instance* I, int R, int nF)
 {
     return ea_resident_pick_wt(I->L, I->jtype, I->has_h, nF, (R + 3) / 4);
 }
 
-static pb_status wait_run(pb_run* run, int32_t timeout_ms)
+pb_status wait_run(pb_run* run, int32_t timeout_ms)
 {
     const auto t0 = std::chrono::steady_clock::now();
     for (;;) {
@@ -534,20 +551,13 @@ pb_status pb_anneal_ex(pb_instance* I, const pb_schedule* sc, int32_t R, uint64_
     std::unique_ptr<pb_run> run(new (std::nothrow) pb_run());
     if (!run) return fail(PB_ENOMEM, "host allocation failed");
     if (I->topo == PB_TOPO_EA3D) {
-        const int nF = 2 * (6 + I->hmax) + 1;
-        int f = form;
-        int WT = 0;
-        if (f == PB_FORM_AUTO || f == PB_FORM_RESIDENT) {
-            WT = ea_choose_wt(I, R, nF);
-            if (WT == 0) {
-                if (f == PB_FORM_RESIDENT) return fail(PB_EUNSUPPORTED, "lattice too large for the resident form");
-                f = PB_FORM_PLAIN;
-            } else {
-                f = PB_FORM_RESIDENT;
-                // enough tiles for the SMs: split replica blocks of a lone job
-                const int sms = sm_count();
-                while (WT > 1 && ((R + 3) / 4 + WT - 1) / WT < sms) WT /= 2;
-            }
+        int f = 0, WT = 0;
+        choose_form(I, R, form, f, WT);
+        if (f == PB_FORM_RESIDENT) {
+            if (WT == 0) return fail(PB_EUNSUPPORTED, "lattice too large for the resident form");
+            // enough tiles for the SMs: split replica blocks of a lone job
+            const int sms = sm_count();
+            while (WT > 1 && ((R + 3) / 4 + WT - 1) / WT < sms) WT /= 2;
         }
         if (f != PB_FORM_PLAIN && f != PB_FORM_RESIDENT) return fail(PB_EUNSUPPORTED, "form not available for EA instances");
         pb_status ps = ea_prepare_run(run.get(), I, sc, R, seed, opts, f, WT, st);
@@ -560,7 +570,11 @@ pb_status pb_anneal_ex(pb_instance* I, const pb_schedule* sc, int32_t R, uint64_
         }
         if (ps != PB_OK) return ps;
     } else {
-        pb_status ps = bq_anneal(run.get(), I, sc, R, seed, opts, st);
+        int f = 0, wt = 0;
+        choose_form(I, R, form, f, wt);
+        pb_anneal_opts o = opts ? *opts : pb_anneal_opts{PB_FORM_AUTO, 0, NAN};
+        o.form = f;
+        pb_status ps = bq_anneal(run.get(), I, sc, R, seed, &o, st);
         if (ps != PB_OK) return ps;
     }
     *out = run.release();
@@ -571,52 +585,6 @@ pb_status pb_anneal(pb_instance* inst, const pb_schedule* sched, int32_t replica
                     pb_run** out)
 {
     return pb_anneal_ex(inst, sched, replicas, seed, nullptr, stream, out);
-}
-
-pb_status pb_anneal_batch(int32_t count, pb_instance* const* insts, const pb_schedule* scheds, const int32_t* replicas,
-                          const uint64_t* seeds, const pb_anneal_opts* opts, void* stream, pb_run** outs)
-{
-    if (count < 1 || !insts || !scheds || !replicas || !seeds || !outs) return fail(PB_EINVAL, "null or empty batch");
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    std::vector<std::unique_ptr<pb_run>> runs;
-    std::vector<int> wts(count);
-    long long total_tiles = 0;
-    for (int q = 0; q < count; ++q) {
-        pb_instance* I = insts[q];
-        if (!I) return fail(PB_EINVAL, "null instance in batch");
-        if (I->topo != PB_TOPO_EA3D) return fail(PB_EUNSUPPORTED, "batched launches take EA instances only");
-        if (replicas[q] < 1) return fail(PB_EINVAL, "replicas must be >= 1");
-        const int nF = 2 * (6 + I->hmax) + 1;
-        wts[q] = ea_choose_wt(I, replicas[q], nF);
-        if (wts[q] == 0) return fail(PB_EUNSUPPORTED, "lattice too large for the resident form");
-        total_tiles += ((replicas[q] + 3) / 4 + wts[q] - 1) / wts[q];
-    }
-    // too few tiles for the SMs: halve the widest replica blocks
-    const int sms = sm_count();
-    while (total_tiles < sms) {
-        int qmax = -1;
-        for (int q = 0; q < count; ++q)
-            if (wts[q] > 1 && (qmax < 0 || wts[q] > wts[qmax])) qmax = q;
-        if (qmax < 0) break;
-        const int Rw = (replicas[qmax] + 3) / 4;
-        total_tiles -= (Rw + wts[qmax] - 1) / wts[qmax];
-        wts[qmax] /= 2;
-        total_tiles += (Rw + wts[qmax] - 1) / wts[qmax];
-    }
-    for (int q = 0; q < count; ++q) {
-        std::unique_ptr<pb_run> run(new (std::nothrow) pb_run());
-        if (!run) return fail(PB_ENOMEM, "host allocation failed");
-        pb_status ps = ea_prepare_run(run.get(), insts[q], &scheds[q], replicas[q], seeds[q], opts ? &opts[q] : nullptr,
-                                      PB_FORM_RESIDENT, wts[q], st);
-        if (ps != PB_OK) return ps;
-        runs.push_back(std::move(run));
-    }
-    std::vector<pb_run*> raw;
-    for (auto& r : runs) raw.push_back(r.get());
-    pb_status ps = ea_enqueue_resident(raw, st);
-    if (ps != PB_OK) return ps;
-    for (int q = 0; q < count; ++q) outs[q] = runs[q].release();
-    return PB_OK;
 }
 
 pb_status pb_wait(pb_run* run, int32_t timeout_ms)

@@ -14,8 +14,15 @@
 namespace pb {
 
 // ---------------------------------------------------------------------------
-// Device buffer owned by a handle.
+// Device memory of the handles comes from a library-owned stream-ordered pool
+// (per device), allocated and freed on an internal non-blocking stream: a free
+// never synchronises the device, so releasing a finished run does not wait for
+// work that other runs still have in flight.  Buffers are released only when
+// no launch that uses them is pending (pb_run_destroy waits for its run).
 // ---------------------------------------------------------------------------
+cudaError_t pool_alloc(void** p, size_t n);
+void pool_free(void* p);
+
 struct DevBuf {
     void* p = nullptr;
     size_t bytes = 0;
@@ -24,12 +31,14 @@ struct DevBuf {
     DevBuf& operator=(const DevBuf&) = delete;
     ~DevBuf()
     {
-        if (p) cudaFree(p);
+        if (p) pool_free(p);
     }
     cudaError_t alloc(size_t n)
     {
+        if (p) pool_free(p);
+        p = nullptr;
         bytes = n;
-        return cudaMalloc(&p, n ? n : 16);
+        return pool_alloc(&p, n ? n : 16);
     }
     template <typename T>
     T* as() const
@@ -37,6 +46,11 @@ struct DevBuf {
         return static_cast<T*>(p);
     }
 };
+
+// Launch streams of batches and of the request server: a per-device set of
+// non-blocking streams owned by the library.
+cudaStream_t pool_stream(int k);
+int pool_streams();
 
 #define PB_ALLOC(buf, n)                                                  \
     do {                                                                  \
@@ -61,6 +75,8 @@ struct pb_instance {
 namespace pb {
 struct BatchShared {
     DevBuf jobs, work, counter;
+    int n_work = 0, grid = 0;
+    size_t smem = 0;
     cudaGraphExec_t exec = nullptr;
     cudaEvent_t ev_k0 = nullptr, ev_k1 = nullptr;  // around the shared persistent launch
     ~BatchShared()
@@ -109,4 +125,23 @@ pb_status bq_build(pb_instance* I, const pb_instance_desc* d, cudaStream_t st);
 pb_status bq_anneal(pb_run* run, pb_instance* I, const pb_schedule* sc, int R, uint64_t seed,
                     const pb_anneal_opts* opts, cudaStream_t st);
 pb_status bq_fields(pb_instance* I, const int8_t* d_states, int R, int form, float* d_out, cudaStream_t st);
+// Split forms of the anneal: set-up (allocations, tables, copies; may synchronise
+// `st`) and launch (graph capture and launch on `st`, no synchronisation).
+pb_status ea_prepare_run(pb_run* run, pb_instance* I, const pb_schedule* sc, int R, uint64_t seed,
+                         const pb_anneal_opts* opts, int form, int WT, cudaStream_t st);
+pb_status ea_enqueue_plain(pb_run* run, cudaStream_t st);
+pb_status ea_batch_setup(std::vector<pb_run*>& runs, cudaStream_t st, std::shared_ptr<BatchShared>& out);
+pb_status ea_batch_launch(std::vector<pb_run*>& runs, const std::shared_ptr<BatchShared>& shared, cudaStream_t st);
+int ea_choose_wt(const pb_instance* I, int R, int nF);
+pb_status bq_setup(pb_run* run, pb_instance* I, const pb_schedule* sc, int R, uint64_t seed,
+                   const pb_anneal_opts* opts, cudaStream_t st);
+pb_status bq_launch(pb_run* run, cudaStream_t st);
+pb_status wait_run(pb_run* run, int32_t timeout_ms);
+// Form (and EA tile width) for a job: the caller's choice, else the autotuner's
+// table entry for the job's shape, else the built-in rule.
+void choose_form(const pb_instance* I, int R, int requested, int& form, int& wt);
+pb_status batch_start(int count, pb_instance* const* insts, const pb_schedule* scheds, const int32_t* replicas,
+                      const uint64_t* seeds, const pb_anneal_opts* opts, cudaStream_t setup_st, bool join,
+                      std::vector<double>* load_io, std::vector<std::unique_ptr<pb_run>>& runs_out,
+                      std::vector<double>* costs, std::vector<int>* stream_of);
 }  // namespace pb

@@ -48,6 +48,24 @@ class pb_anneal_opts(ctypes.Structure):
     _fields_ = [("form", ctypes.c_int32), ("flags", ctypes.c_int32), ("target_energy", ctypes.c_double)]
 
 
+class pb_tune_result(ctypes.Structure):
+    _fields_ = [("form", ctypes.c_int32), ("tile_width", ctypes.c_int32), ("n_candidates", ctypes.c_int32),
+                ("candidate_form", ctypes.c_int32 * 8), ("candidate_wt", ctypes.c_int32 * 8),
+                ("probe_ms", ctypes.c_float * 8)]
+
+
+class pb_server_opts(ctypes.Structure):
+    _fields_ = [("max_device_bytes", ctypes.c_int64), ("max_inflight", ctypes.c_int32), ("gather_us", ctypes.c_int32)]
+
+
+class pb_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("admitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("failed", ctypes.c_int64), ("queued", ctypes.c_int64), ("inflight", ctypes.c_int64),
+                ("inflight_bytes", ctypes.c_int64), ("peak_inflight_bytes", ctypes.c_int64), ("rounds", ctypes.c_int64),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
+                ("max_ms", ctypes.c_double)]
+
+
 _lib = None
 
 
@@ -89,6 +107,14 @@ def load():
         "pb_fields": ([P, P, I32, P, I64, P], st),
         "pb_fields_ex": ([P, P, I32, I32, P, I64, P], st),
         "pb_anneal_ea_noalloc": ([I32, P, P, I32, U64, P, P, P, P, P, P], st),
+        "pb_autotune": ([P, I32, I32, P, P], st),
+        "pb_autotune_clear": ([], None),
+        "pb_run_footprint": ([P, P, I32, P], I64),
+        "pb_server_create": ([P, P], st),
+        "pb_server_submit": ([P, P, P, I32, U64, P, P], st),
+        "pb_server_wait": ([P, I64, I32, P, P], st),
+        "pb_server_stats_get": ([P, P], st),
+        "pb_server_destroy": ([P], None),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -285,6 +311,56 @@ def pb_anneal_ea_noalloc(L: int, J_dev: int, sched: pb_schedule, replicas: int, 
                                        ctypes.c_void_p(best_E_dev), ctypes.c_void_p(best_sweep_dev),
                                        ctypes.c_void_p(best_states_dev), ctypes.c_void_p(final_E_dev),
                                        ctypes.c_void_p(final_states_dev), _stream(stream)))
+
+
+# ------------------------------------------------------- autotuner, server
+def pb_autotune(inst, replicas: int, probe_sweeps: int = 8, stream=None) -> pb_tune_result:
+    r = pb_tune_result()
+    _check(load().pb_autotune(inst, replicas, probe_sweeps, _stream(stream), ctypes.byref(r)))
+    return r
+
+
+def pb_autotune_clear():
+    load().pb_autotune_clear()
+
+
+def pb_run_footprint(inst, sched: pb_schedule, replicas: int, opts: pb_anneal_opts | None = None) -> int:
+    return int(load().pb_run_footprint(inst, ctypes.byref(sched), replicas,
+                                       None if opts is None else ctypes.byref(opts)))
+
+
+def pb_server_create(max_device_bytes: int = 0, max_inflight: int = 0, gather_us: int = 0) -> ctypes.c_void_p:
+    o = pb_server_opts(max_device_bytes=max_device_bytes, max_inflight=max_inflight, gather_us=gather_us)
+    out = ctypes.c_void_p()
+    _check(load().pb_server_create(ctypes.byref(o), ctypes.byref(out)))
+    return out
+
+
+def pb_server_submit(sv, inst, sched: pb_schedule, replicas: int, seed: int,
+                     opts: pb_anneal_opts | None = None) -> int:
+    t = ctypes.c_int64()
+    _check(load().pb_server_submit(sv, inst, ctypes.byref(sched), replicas, seed,
+                                   None if opts is None else ctypes.byref(opts), ctypes.byref(t)))
+    return int(t.value)
+
+
+def pb_server_wait(sv, ticket: int, timeout_ms: int = -1):
+    """(run, latency_ms) of a finished ticket; the caller owns the run."""
+    run = ctypes.c_void_p()
+    lat = ctypes.c_double()
+    _check(load().pb_server_wait(sv, ticket, timeout_ms, ctypes.byref(run), ctypes.byref(lat)))
+    return run, float(lat.value)
+
+
+def pb_server_stats_get(sv) -> pb_server_stats:
+    s = pb_server_stats()
+    _check(load().pb_server_stats_get(sv, ctypes.byref(s)))
+    return s
+
+
+def pb_server_destroy(sv):
+    if sv:
+        load().pb_server_destroy(sv)
 
 
 # ------------------------------------------------------- convenience layer

@@ -51,6 +51,9 @@ int main(void) {
   printf("%zu %zu %zu %zu\n", sizeof(pb_instance_desc), offsetof(pb_instance_desc, J), offsetof(pb_instance_desc, colour), 0);
   printf("%zu %zu %zu %zu\n", sizeof(pb_schedule), offsetof(pb_schedule, beta0), offsetof(pb_schedule, betas), 0);
   printf("%zu %zu %zu %zu\n", sizeof(pb_anneal_opts), offsetof(pb_anneal_opts, target_energy), 0, 0);
+  printf("%zu %zu %zu %zu\n", sizeof(pb_tune_result), offsetof(pb_tune_result, candidate_wt), offsetof(pb_tune_result, probe_ms), 0);
+  printf("%zu %zu %zu %zu\n", sizeof(pb_server_opts), offsetof(pb_server_opts, gather_us), 0, 0);
+  printf("%zu %zu %zu %zu\n", sizeof(pb_server_stats), offsetof(pb_server_stats, rounds), offsetof(pb_server_stats, max_ms), 0);
   return 0; }''')
     exe = tmp_path / "sz"
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)])
@@ -59,6 +62,10 @@ int main(void) {
     assert rows[0][:3] == [ctypes.sizeof(D), D.J.offset, D.colour.offset]
     assert rows[1][:3] == [ctypes.sizeof(S), S.beta0.offset, S.betas.offset]
     assert rows[2][:2] == [ctypes.sizeof(O), O.target_energy.offset]
+    T, SO, SS = native.pb_tune_result, native.pb_server_opts, native.pb_server_stats
+    assert rows[3][:3] == [ctypes.sizeof(T), T.candidate_wt.offset, T.probe_ms.offset]
+    assert rows[4][:2] == [ctypes.sizeof(SO), SO.gather_us.offset]
+    assert rows[5][:3] == [ctypes.sizeof(SS), SS.rounds.offset, SS.max_ms.offset]
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):
