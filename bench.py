@@ -30,6 +30,11 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
+# Batches and the request server run many graph-captured anneals on the library's
+# launch streams at once: give the process more hardware work queues than the
+# default 8 so that independent streams do not share one (set before CUDA starts).
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 METRIC = "p-bit updates/s"
 UNIT = "updates/s"
 S_SWEEPS = 10000
@@ -218,6 +223,179 @@ def biclique_block(pb, stream, peaks):
     return out
 
 
+# ------------------------------------------------------ mixed batch, served
+def mixed_jobs(count: int, seed: int, s_lo: float, s_hi: float):
+    """Jobs of the mixed workload: half EA cubes L in {8,12,16,24}, half bicliques
+    n in {128,...,2048}; half +-1, half N(0,1); replicas 2^5..2^10 and sweep budgets
+    log-uniform; geometric beta 0.1 -> 5.0."""
+    rng = np.random.default_rng(seed)
+    jobs = []
+    for q in range(count):
+        topo = "ea" if rng.random() < 0.5 else "bq"
+        size = int(rng.choice([8, 12, 16, 24])) if topo == "ea" else int(rng.choice([128, 256, 512, 1024, 2048]))
+        law = "pm1" if rng.random() < 0.5 else "gauss"
+        R = int(2 ** rng.integers(5, 11))
+        S = int(round(math.exp(rng.uniform(math.log(s_lo), math.log(s_hi)))))
+        jobs.append((topo, size, law, R, S, 7000 + q))
+    return jobs
+
+
+def job_updates(j):
+    topo, size, law, R, S, _ = j
+    return (size ** 3 if topo == "ea" else 2 * size) * R * S
+
+
+def make_instances(pb, jobs, stream):
+    cache = {}
+    insts = []
+    for topo, size, law, R, S, iseed in jobs:
+        key = (topo, size, law, iseed)
+        if key not in cache:
+            dist = pb.PB_DIST_PM1 if law == "pm1" else pb.PB_DIST_GAUSS
+            if topo == "ea":
+                cache[key] = pb.pb_create_instance(pb.PB_TOPO_EA3D, pb.pb_generate_ea(size, dist, iseed), None,
+                                                   L=size, stream=stream)
+            else:
+                cache[key] = pb.pb_create_instance(pb.PB_TOPO_BICLIQUE, pb.pb_generate_biclique(size, dist, iseed),
+                                                   None, n=size, stream=stream)
+        insts.append(cache[key])
+    return insts, list(cache.values())
+
+
+def mixed_block(pb, stream):
+    """200 mixed instances in one batch (EA jobs in one persistent graph-captured launch,
+    bicliques as graph-captured anneals side by side), forms from the autotuner; against
+    the plain per-instance forms (EA plain, biclique CUDA-core) run one after another on
+    every 4th job."""
+    import torch
+    jobs = mixed_jobs(200, 7, 500, 1e4)
+    insts, owned = make_instances(pb, jobs, stream)
+    scheds = [pb.make_schedule(pb.PB_SCHED_GEOMETRIC, j[4], BETA0, BETA1) for j in jobs]
+    seeds = [50000 + q for q in range(len(jobs))]
+    reps = [j[3] for j in jobs]
+    # autotuner: one probe per distinct shape (untimed)
+    t0 = time.perf_counter()
+    tuned = {}
+    for j, i in zip(jobs, insts):
+        key = (j[0], j[1], j[2], int(math.ceil(math.log2(j[3]))))
+        if key not in tuned:
+            t = pb.pb_autotune(i, j[3], 8, stream=stream)
+            tuned[key] = (t.form, t.tile_width)
+    tune_s = time.perf_counter() - t0
+
+    def timed_batch(idx):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        w0 = time.perf_counter()
+        e0.record(stream)
+        runs = pb.pb_anneal_batch([insts[q] for q in idx], [scheds[q] for q in idx], [reps[q] for q in idx],
+                                  [seeds[q] for q in idx], stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        wall = time.perf_counter() - w0
+        best = [pb.pb_energy(r, reps[q])[1] for r, q in zip(runs, idx)]
+        for r in runs:
+            pb.pb_run_destroy(r)
+        return e0.elapsed_time(e1), wall, best
+
+    allq = list(range(len(jobs)))
+    timed_batch(allq)  # warm-up (graphs, pools)
+    ms, wall, _ = timed_batch(allq)
+    upd = sum(job_updates(j) for j in jobs)
+    sub = allq[::4]
+    sub_upd = sum(job_updates(jobs[q]) for q in sub)
+    sms, _, sbest = timed_batch(sub)
+    # plain per-instance forms, one job after another
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    pruns = []
+    for q in sub:
+        f = pb.PB_FORM_PLAIN if jobs[q][0] == "ea" else pb.PB_FORM_CUDACORE
+        pruns.append(pb.pb_anneal(insts[q], scheds[q], reps[q], seeds[q], pb.make_opts(f), stream=stream))
+    e1.record(stream)
+    e1.synchronize()
+    pms = e0.elapsed_time(e1)
+    pbest = [pb.pb_energy(r, reps[q])[1] for r, q in zip(pruns, sub)]
+    for r in pruns:
+        pb.pb_run_destroy(r)
+    # +-1 jobs: the same trajectories bit for bit; N(0,1) jobs (split BF16 tensor
+    # products vs FP32 CUDA-core fields round differently): mean best energy per
+    # spin within 3 standard errors
+    pm1_same, g_ok, g_n = True, 0, 0
+    for q, a, b in zip(sub, sbest, pbest):
+        if jobs[q][2] == "pm1":
+            pm1_same &= bool(np.array_equal(a, b))
+        else:
+            g_n += 1
+            se = math.sqrt(a.var(ddof=1) / a.size + b.var(ddof=1) / b.size) if a.size > 1 else 0.0
+            g_ok += int(abs(a.mean() - b.mean()) <= 3 * se + 1e-9 * abs(a.mean()))
+    for i in owned:
+        pb.pb_instance_destroy(i)
+    return {"workload": "200 instances, seed 7: EA L in {8,12,16,24} / biclique n in {128,...,2048}, +-1 / N(0,1), "
+                        "replicas 32..1024 (powers of 2, log-uniform), sweeps log-uniform in [500, 1e4], geometric "
+                        "beta 0.1->5.0",
+            "updates": upd, "ms": ms, "wall_ms": 1e3 * wall, "value": upd / (ms / 1e3), "unit": UNIT,
+            "autotune": {"shapes": len(tuned), "seconds": tune_s},
+            "plain_vs_batched_on_every_4th_job": {
+                "jobs": len(sub), "updates": sub_upd, "batched_ms": sms, "plain_ms": pms,
+                "batched_value": sub_upd / (sms / 1e3), "plain_value": sub_upd / (pms / 1e3), "speedup": pms / sms,
+                "pm1_jobs_identical": pm1_same, "gauss_jobs_mean_within_3se": f"{g_ok}/{g_n}",
+                "plain_forms": "EA plain (one launch per colour and sweep), biclique FP32 CUDA-core"}}
+
+
+def served_block(pb, stream, n_req: int):
+    """Poisson arrivals (500 requests/s, seed 11) of jobs drawn like the mixed batch with
+    sweep budgets log-uniform in [50, 1000], served with continuous batching; latency from
+    submit to result ready."""
+    import torch
+    jobs = mixed_jobs(n_req, 11, 50, 1000)
+    # a pool of 48 distinct instances (instance seed reused), requests pick their own R, S, seed
+    pool = {}
+    for q, j in enumerate(jobs):
+        key = (j[0], j[1], j[2])
+        pool.setdefault(key, 11000 + len(pool))
+    jobs = [(t, sz, law, R, S, pool[(t, sz, law)]) for t, sz, law, R, S, _ in jobs]
+    insts, owned = make_instances(pb, jobs, stream)
+    scheds = [pb.make_schedule(pb.PB_SCHED_GEOMETRIC, j[4], BETA0, BETA1) for j in jobs]
+    rng = np.random.default_rng(11)
+    gaps = rng.exponential(1.0 / 500.0, size=n_req)
+    torch.cuda.synchronize()
+    sv = pb.pb_server_create(max_inflight=512, gather_us=0)
+    tickets = [None] * n_req
+    t_start = time.perf_counter()
+
+    def submitter():
+        t = t_start
+        for q in range(n_req):
+            t += gaps[q]
+            d = t - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            tickets[q] = pb.pb_server_submit(sv, insts[q], scheds[q], jobs[q][3], 90000 + q)
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    th.join()
+    for q in range(n_req):
+        run, _ = pb.pb_server_wait(sv, tickets[q], -1)
+        pb.pb_run_destroy(run)
+    t_end = time.perf_counter()
+    st = pb.pb_server_stats_get(sv)
+    pb.pb_server_destroy(sv)
+    for i in owned:
+        pb.pb_instance_destroy(i)
+    upd = sum(job_updates(j) for j in jobs)
+    span = t_end - t_start
+    return {"workload": "Poisson arrivals 500/s (seed 11) of mixed jobs (EA L in {8,12,16,24} / biclique n in "
+                        "{128,...,2048}, +-1 / N(0,1), replicas 32..1024, sweeps log-uniform in [50, 1000]), "
+                        "48 distinct instances",
+            "requests": n_req, "seconds": span, "throughput_updates_per_s": upd / span,
+            "requests_per_s": n_req / span, "offered_req_per_s": 500.0,
+            "p50_ms": st.p50_ms, "p99_ms": st.p99_ms, "mean_ms": st.mean_ms, "max_ms": st.max_ms,
+            "rounds": st.rounds, "peak_inflight_bytes": st.peak_inflight_bytes, "failed": st.failed}
+
+
 # ------------------------------------------------- small profiling cases
 CASES = {
     # name: (topology, L or n, law, replicas, sweeps, form)
@@ -269,6 +447,9 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-form comparison run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-biclique", action="store_true", help="skip the biclique tensor-core measurement")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the 200-instance mixed batch")
+    ap.add_argument("--no-serve", action="store_true", help="skip the served Poisson stream")
+    ap.add_argument("--serve-requests", type=int, default=1500, help="requests of the served stream")
     ap.add_argument("--case", default=None, choices=sorted(CASES),
                     help="run one small launch of a hot-path kernel (for ncu) and exit")
     args = ap.parse_args()
@@ -436,6 +617,10 @@ def main():
 
     if rank == 0 and not args.no_biclique:
         line["biclique"] = biclique_block(pb, stream, peaks)
+    if rank == 0 and not args.no_mixed:
+        line["mixed_batch"] = mixed_block(pb, stream)
+    if rank == 0 and not args.no_serve:
+        line["served"] = served_block(pb, stream, args.serve_requests)
 
     if rank == 0 and not args.no_cpu and world == 1:
         from oracle import oracle as orc

@@ -187,6 +187,18 @@ pb_status batch_start(int count, pb_instance* const* insts, const pb_schedule* s
     if (!resident.empty()) {
         pb_status ps = ea_batch_setup(resident, st, ea_shared);
         if (ps != PB_OK) return ps;
+        // The persistent EA launch keeps every SM it is given until its last tile
+        // ends.  With other jobs in the batch it gets three quarters of the SMs
+        // (fewer if its own work is the smaller part), so that the other jobs --
+        // mostly short launches, bounded by latency more than by SMs -- run
+        // beside it instead of after it.
+        double ea_cost = 0.0, other = 0.0;
+        for (const Job& j : jobs) (j.form == PB_FORM_RESIDENT ? ea_cost : other) += j.cost;
+        if (other > 0.0) {
+            const int sms = sm_count();
+            const int share = ea_cost >= other ? (3 * sms + 3) / 4 : std::max(sms / 4, (sms + 1) / 2);
+            ea_shared->grid = std::max(1, std::min(ea_shared->grid, share));
+        }
     }
 
     // ---- launch: fork from the caller's stream, one stream for the EA batch,

@@ -73,8 +73,11 @@ __global__ void __launch_bounds__(256) bq_encode_kernel(BqJob job, const int8_t*
 constexpr int BM = kBqTileRows, BN = kBqTileReps, BK = 32;
 
 template <int SB>
-__global__ void __launch_bounds__(256) bq_cc_half_kernel(BqJob job, int side, int s, int decide, float* fields_out)
+__global__ void __launch_bounds__(256) bq_cc_half_kernel(BqJob job, int side, int s_arg, const int32_t* sp, int decide,
+                                                        float* fields_out)
 {
+    const int s = sp ? *sp : s_arg;
+    if (decide && s >= job.S) return;
     using SC = SpinCode<SB>;
     using ST = typename SC::T;
     __shared__ __align__(16) float As[BK][BM + 4];
@@ -133,8 +136,13 @@ __global__ void __launch_bounds__(256) bq_cc_half_kernel(BqJob job, int side, in
     const bool pm1 = job.inst.jtype == PB_J_PM1_I8;
     const uint32_t* trow = nullptr;
     float cexp = 0.0f;
+    TabWindow win{0, 0, 1};
+    if (pm1 && decide) {
+        const int l = s / job.step;
+        win = TabWindow{job.win[3 * l + 2], job.win[3 * l], job.win[3 * l + 1]};
+    }
     if (pm1)
-        trow = job.table + (size_t)(s / job.step) * job.nF;
+        trow = job.table + win.off;
     else
         cexp = f32_cexp(job.betaf[s / job.step]);
     float e_field[4] = {0.f, 0.f, 0.f, 0.f};  // -m F  (side B)
@@ -161,7 +169,8 @@ __global__ void __launch_bounds__(256) bq_cc_half_kernel(BqJob job, int side, in
             const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
-                mn[b] = pm1 ? (ws[b] >= trow[(int)F[b] - job.fmin]) : (decide_f32(ws[b], F[b], cexp) != 0u);
+                mn[b] = pm1 ? (ws[b] >= trow[min(max((int)F[b] - job.fmin, win.lo), win.lo + win.width - 1) - win.lo])
+                            : (decide_f32(ws[b], F[b], cexp) != 0u);
                 own[(size_t)(rq + b) * job.ld + i] = SC::enc(mn[b]);
             }
         } else {
@@ -204,8 +213,12 @@ __global__ void __launch_bounds__(256) bq_cc_half_kernel(BqJob job, int side, in
 // 16-byte loads and stores.
 constexpr int kEndReps = 32;
 
-__global__ void __launch_bounds__(256) bq_sweep_end_kernel(BqJob job, int s, int init)
+__global__ void __launch_bounds__(256) bq_sweep_end_kernel(BqJob job, int s_arg, int init, const int32_t* sp_read,
+                                                          int32_t* sp_write)
 {
+    const int s = sp_read ? *sp_read : s_arg;
+    if (sp_write && blockIdx.x == 0 && threadIdx.x == 0) *sp_write = s + 1;  // read by the next sweep's launches
+    if (!init && s >= job.S) return;
     __shared__ int s_imp[kEndReps];
     const int r0 = blockIdx.x * kEndReps;
     const bool pm1 = job.inst.jtype == PB_J_PM1_I8;
@@ -433,19 +446,21 @@ cudaError_t bq_launch_encode(const BqJob& job, const int8_t* d_states, cudaStrea
     return cudaGetLastError();
 }
 
-cudaError_t bq_launch_cc_half(const BqJob& job, int side, int s, int decide, float* fields_out, cudaStream_t st)
+cudaError_t bq_launch_cc_half(const BqJob& job, int side, int s, const int32_t* sp, int decide, float* fields_out,
+                              cudaStream_t st)
 {
     dim3 grid((unsigned)((job.inst.n + BM - 1) / BM), (unsigned)(job.Rpad / BN));
     if (job.inst.jtype == PB_J_PM1_I8)
-        bq_cc_half_kernel<1><<<grid, 256, 0, st>>>(job, side, s, decide, fields_out);
+        bq_cc_half_kernel<1><<<grid, 256, 0, st>>>(job, side, s, sp, decide, fields_out);
     else
-        bq_cc_half_kernel<2><<<grid, 256, 0, st>>>(job, side, s, decide, fields_out);
+        bq_cc_half_kernel<2><<<grid, 256, 0, st>>>(job, side, s, sp, decide, fields_out);
     return cudaGetLastError();
 }
 
-cudaError_t bq_launch_sweep_end(const BqJob& job, int s, int init, cudaStream_t st)
+cudaError_t bq_launch_sweep_end(const BqJob& job, int s, int init, const int32_t* sp_read, int32_t* sp_write,
+                                cudaStream_t st)
 {
-    bq_sweep_end_kernel<<<job.Rpad / kEndReps, 256, 0, st>>>(job, s, init);
+    bq_sweep_end_kernel<<<job.Rpad / kEndReps, 256, 0, st>>>(job, s, init, sp_read, sp_write);
     return cudaGetLastError();
 }
 

@@ -200,22 +200,41 @@ static pb_status bq_prepare(pb_run* run, pb_instance* I, const pb_schedule* sc, 
         const int fmax = n + I->hmax;
         j.fmin = -fmax;
         j.nF = 2 * fmax + 1;
-        std::vector<uint32_t> tab((size_t)nlev * j.nF, 0x80000000u);
-        for (size_t l = 0; l < betas.size(); ++l)
-            for (int f = 0; f < j.nF; ++f) tab[l * j.nF + f] = threshold_u32(betas[l], (double)(f + j.fmin));
-        // Per level, the window of the row outside which T is saturated: every entry
-        // below it is 0 and every entry above it 2^32 - 1 (T is nondecreasing in F),
-        // with one saturated entry kept on each side.
-        run->bq_win.assign((size_t)nlev * 2, 0);
-        for (size_t l = 0; l < betas.size(); ++l) {
-            const uint32_t* row = tab.data() + l * j.nF;
-            int lo = 0, hi = j.nF - 1;
-            while (lo + 1 < j.nF && row[lo + 1] == 0u) ++lo;
-            while (hi - 1 >= 0 && row[hi - 1] == 0xFFFFFFFFu) --hi;
-            if (hi < lo) hi = lo;
-            run->bq_win[2 * l] = lo;
-            run->bq_win[2 * l + 1] = hi - lo + 1;
+        // Threshold rows (Eq. 2, FP64 on the host), one per beta level, stored as the
+        // window of the row outside which T is saturated: T is nondecreasing in F, so
+        // every entry below the window is 0 and every entry above it 2^32 - 1, and the
+        // window keeps one saturated entry on each side; a lookup clamps F into the
+        // window.  The window edges are found by bisection, so a level costs
+        // O(width + log nF) evaluations instead of nF.
+        std::vector<uint32_t> tab;
+        run->bq_win.assign((size_t)nlev * 3, 0);
+        for (int l = 0; l < nlev; ++l) {
+            const double beta = betas.empty() ? 0.0 : betas[l];
+            auto T = [&](int f) { return threshold_u32(beta, (double)(f + j.fmin)); };
+            int a = 0, b = j.nF;  // first index with T > 0
+            while (a < b) {
+                const int m = (a + b) / 2;
+                if (T(m) > 0u) b = m; else a = m + 1;
+            }
+            const int lo = std::max(0, a - 1);
+            a = 0;
+            b = j.nF;  // first index with T = 2^32 - 1
+            while (a < b) {
+                const int m = (a + b) / 2;
+                if (T(m) == 0xFFFFFFFFu) b = m; else a = m + 1;
+            }
+            const int hi = std::max(lo, std::min(j.nF - 1, a));
+            run->bq_win[3 * l] = lo;
+            run->bq_win[3 * l + 1] = hi - lo + 1;
+            run->bq_win[3 * l + 2] = (int32_t)tab.size();
+            for (int f = lo; f <= hi; ++f) tab.push_back(T(f));
         }
+        int wmax = 0;
+        for (int l = 0; l < nlev; ++l) wmax = std::max(wmax, run->bq_win[3 * l + 1]);
+        j.tabmode = wmax <= kBqTcWindowMax ? 2 : (wmax * 4 <= 33 * 1024 ? 1 : 0);
+        PB_ALLOC(run->extra[7], run->bq_win.size() * 4);
+        PB_CUDA_TRY(cudaMemcpyAsync(run->extra[7].p, run->bq_win.data(), run->bq_win.size() * 4, cudaMemcpyHostToDevice, st));
+        j.win = run->extra[7].as<int32_t>();
         PB_ALLOC(run->table, tab.size() * 4);
         PB_CUDA_TRY(cudaMemcpyAsync(run->table.p, tab.data(), tab.size() * 4, cudaMemcpyHostToDevice, st));
         PB_CUDA_TRY(cudaStreamSynchronize(st));
@@ -258,7 +277,7 @@ static pb_status bq_prepare(pb_run* run, pb_instance* I, const pb_schedule* sc, 
     PB_ALLOC(run->E_out, (size_t)2 * R * 8);
     PB_ALLOC(run->extra[5], 16);
     PB_CUDA_TRY(cudaMemsetAsync(run->extra[5].p, 0, 16, st));
-    run->dev_err = run->extra[5].as<int>();
+    run->dev_err = run->extra[5].as<int>();  // [0] device error word, [2], [3] sweep counters
     PB_ALLOC(run->extra[6], (size_t)((n + 63) / 64) * R * 8);
     j.epart = run->extra[6].as<double>();
     if (tensor) {
@@ -281,39 +300,32 @@ static pb_status bq_prepare(pb_run* run, pb_instance* I, const pb_schedule* sc, 
     return PB_OK;
 }
 
-static cudaError_t bq_half(pb_run* run, int side, int s, int decide, float* fields_out, cudaStream_t st)
+static cudaError_t bq_half(pb_run* run, int side, int s, const int32_t* sp, int decide, float* fields_out,
+                           cudaStream_t st)
 {
     if (run->form == PB_FORM_TENSOR)
-    {
-        const size_t l = (size_t)(s / std::max(1, run->bjob.step));
-        const bool w = 2 * l + 1 < run->bq_win.size();
-        return bq_launch_tc_half(run->maps, run->bjob, side, s, decide, fields_out, run->dev_err,
-                                 w ? run->bq_win[2 * l] : 0, w ? run->bq_win[2 * l + 1] : 0, st);
-    }
-    return bq_launch_cc_half(run->bjob, side, s, decide, fields_out, st);
+        return bq_launch_tc_half(run->maps, run->bjob, side, s, sp, decide, fields_out, run->dev_err, st);
+    return bq_launch_cc_half(run->bjob, side, s, sp, decide, fields_out, st);
 }
 
-static pb_status bq_enqueue_body(pb_run* run, cudaStream_t st)
+// Sweeps per captured chunk (even: the two sweep counters alternate within it).
+constexpr int kChunkSweeps = 32;
+
+// One chunk of sweeps.  Sweep k of the chunk reads its index from counter
+// k % 2 and its sweep end stores the next index into the other counter, so no
+// launch reads a counter that a concurrent block writes.  Sweeps past S do
+// nothing, so the same chunk serves every part of the anneal.
+static pb_status bq_enqueue_chunk(pb_run* run, int nsweeps, cudaStream_t st)
 {
     const BqJob& j = run->bjob;
-    PB_CUDA_TRY(bq_launch_init(j, st));
-    // energy of the initial state: side B fields of the initial A, no decisions
-    PB_CUDA_TRY(bq_half(run, 0, 0, 0, nullptr, st));
-    PB_CUDA_TRY(bq_half(run, 1, 0, 0, nullptr, st));
-    PB_CUDA_TRY(bq_launch_sweep_end(j, -1, 1, st));
-    // events around the sweep loop (inside a capture they must be recorded as external nodes)
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    PB_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
-    const unsigned evf = cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
-    PB_CUDA_TRY(cudaEventRecordWithFlags(run->ev_k0, st, evf));
-    for (int s = 0; s < j.S; ++s) {
-        PB_CUDA_TRY(bq_half(run, 0, s, 1, nullptr, st));
-        PB_CUDA_TRY(bq_half(run, 1, s, 1, nullptr, st));
-        PB_CUDA_TRY(bq_launch_sweep_end(j, s, 0, st));
+    int32_t* ctr = run->dev_err + 2;
+    for (int k = 0; k < nsweeps; ++k) {
+        const int32_t* rd = ctr + (k & 1);
+        int32_t* wr = ctr + ((k + 1) & 1);
+        PB_CUDA_TRY(bq_half(run, 0, 0, rd, 1, nullptr, st));
+        PB_CUDA_TRY(bq_half(run, 1, 0, rd, 1, nullptr, st));
+        PB_CUDA_TRY(bq_launch_sweep_end(j, 0, 0, rd, wr, st));
     }
-    PB_CUDA_TRY(cudaEventRecordWithFlags(run->ev_k1, st, evf));
-    PB_CUDA_TRY(bq_launch_readout(j, 0, run->final_pm.as<int8_t>(), run->E_out.as<double>(), st));
-    PB_CUDA_TRY(bq_launch_readout(j, 1, run->best_pm.as<int8_t>(), run->E_out.as<double>() + run->R, st));
     return PB_OK;
 }
 
@@ -327,32 +339,52 @@ pb_status bq_setup(pb_run* run, pb_instance* I, const pb_schedule* sc, int R, ui
     return bq_prepare(run, I, sc, R, seed, opts, form, st);
 }
 
-// The whole anneal (initial state, sweeps, readout) as one CUDA graph when the
-// stream allows capture.
+// The anneal on `st`: initial state and its energy, the sweeps as repeated
+// launches of one captured chunk graph (kChunkSweeps sweeps; plain launches
+// when the stream cannot be captured), then the readout.  The sweep index lives
+// in device memory, so the chunk is the same for every part of the anneal and
+// the host work does not grow with the number of sweeps.
 pb_status bq_launch(pb_run* run, cudaStream_t st)
 {
+    const BqJob& j = run->bjob;
     PB_CUDA_TRY(cudaEventRecord(run->ev_start, st));
-    const bool capture = st != nullptr && st != cudaStreamLegacy && st != cudaStreamPerThread;
-    if (capture) {
-        auto shared = std::make_shared<BatchShared>();
-        cudaGraph_t graph = nullptr;
-        PB_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-        pb_status ps = bq_enqueue_body(run, st);
-        cudaError_t e = cudaStreamEndCapture(st, &graph);
-        if (ps != PB_OK) {
-            if (graph) cudaGraphDestroy(graph);
-            return ps;
+    PB_CUDA_TRY(cudaMemsetAsync(run->dev_err + 2, 0, 2 * sizeof(int32_t), st));
+    PB_CUDA_TRY(bq_launch_init(j, st));
+    // energy of the initial state: side B fields of the initial A, no decisions
+    PB_CUDA_TRY(bq_half(run, 0, 0, nullptr, 0, nullptr, st));
+    PB_CUDA_TRY(bq_half(run, 1, 0, nullptr, 0, nullptr, st));
+    PB_CUDA_TRY(bq_launch_sweep_end(j, -1, 1, nullptr, nullptr, st));
+    PB_CUDA_TRY(cudaEventRecord(run->ev_k0, st));
+    if (j.S > 0) {
+        const int chunk = std::min(kChunkSweeps, (j.S + 1) & ~1);
+        const int nchunks = (j.S + chunk - 1) / chunk;
+        const bool capture = st != nullptr && st != cudaStreamLegacy && st != cudaStreamPerThread;
+        if (capture) {
+            auto shared = std::make_shared<BatchShared>();
+            cudaGraph_t graph = nullptr;
+            PB_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            pb_status ps = bq_enqueue_chunk(run, chunk, st);
+            cudaError_t e = cudaStreamEndCapture(st, &graph);
+            if (ps != PB_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return ps;
+            }
+            if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+            e = cudaGraphInstantiate(&shared->exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+            for (int c = 0; c < nchunks; ++c) PB_CUDA_TRY(cudaGraphLaunch(shared->exec, st));
+            run->batch = shared;
+        } else {
+            for (int c = 0; c < nchunks; ++c) {
+                pb_status ps = bq_enqueue_chunk(run, chunk, st);
+                if (ps != PB_OK) return ps;
+            }
         }
-        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
-        e = cudaGraphInstantiate(&shared->exec, graph, 0);
-        cudaGraphDestroy(graph);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
-        PB_CUDA_TRY(cudaGraphLaunch(shared->exec, st));
-        run->batch = shared;
-    } else {
-        pb_status ps = bq_enqueue_body(run, st);
-        if (ps != PB_OK) return ps;
     }
+    PB_CUDA_TRY(cudaEventRecord(run->ev_k1, st));
+    PB_CUDA_TRY(bq_launch_readout(j, 0, run->final_pm.as<int8_t>(), run->E_out.as<double>(), st));
+    PB_CUDA_TRY(bq_launch_readout(j, 1, run->best_pm.as<int8_t>(), run->E_out.as<double>() + run->R, st));
     PB_CUDA_TRY(cudaEventRecord(run->ev_stop, st));
     return PB_OK;
 }
@@ -379,8 +411,8 @@ pb_status bq_fields(pb_instance* I, const int8_t* d_states, int R, int form, flo
     pb_status ps = bq_prepare(&run, I, &sc, R, 0, nullptr, form, st);
     if (ps != PB_OK) return ps;
     PB_CUDA_TRY(bq_launch_encode(run.bjob, d_states, st));
-    PB_CUDA_TRY(bq_half(&run, 0, 0, 0, d_out, st));
-    PB_CUDA_TRY(bq_half(&run, 1, 0, 0, d_out, st));
+    PB_CUDA_TRY(bq_half(&run, 0, 0, nullptr, 0, d_out, st));
+    PB_CUDA_TRY(bq_half(&run, 1, 0, nullptr, 0, d_out, st));
     PB_CUDA_TRY(cudaStreamSynchronize(st));
     int code = 0;
     PB_CUDA_TRY(cudaMemcpy(&code, run.dev_err, sizeof(int), cudaMemcpyDeviceToHost));

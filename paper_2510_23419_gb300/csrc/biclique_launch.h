@@ -35,7 +35,7 @@ struct BqJob {
     BqDevice inst;
     uint32_t key0, key1;
     int32_t S, step, nF, fmin;
-    const uint32_t* table;  // PM1 [levels][nF]
+    const uint32_t* table;  // PM1: the threshold windows of all levels, concatenated (see TabWindow)
     const float* betaf;     // F32 [levels]
     int32_t R, Rpad;        // replicas, padded to the replica tile
     int32_t ld;             // leading dimension of a spin row (>= n, padded for the tensor form)
@@ -50,6 +50,15 @@ struct BqJob {
     int32_t has_target, target_i;
     float target_f;
     double* epart;          // [ceil(n/64)][R] row-tile parts of the exact readout energy
+    const int32_t* win;     // PM1 [levels][3]: threshold window (lo, width, off) of each beta level
+    int32_t tabmode;        // tensor form: where the decisions read the windows (widest level decides)
+};
+
+// Threshold window of one beta level (+-1 couplings): the row T[F - F_min]
+// restricted to indices [lo, lo + width), stored at table + off; indices
+// outside the window take the value at its nearer edge.
+struct TabWindow {
+    int32_t off, lo, width;
 };
 
 constexpr int kBqTileRows = 64;   // CUDA-core field kernel: rows (spins of the updated side) per block
@@ -59,8 +68,14 @@ cudaError_t bq_launch_init(const BqJob& job, cudaStream_t st);
 // Field + decision of one side (side 0 = A uses J, side 1 = B uses J^T).
 // decide = 0: no update, only the energy partials of the current state.
 // fields_out != null: write F[r][side*n + i] (row stride 2n) and change nothing.
-cudaError_t bq_launch_cc_half(const BqJob& job, int side, int s, int decide, float* fields_out, cudaStream_t st);
-cudaError_t bq_launch_sweep_end(const BqJob& job, int s, int init, cudaStream_t st);
+// The sweep index is s, or, when sp is not null, the device value *sp (read at
+// kernel start; a decision launch whose sweep is >= S does nothing).
+cudaError_t bq_launch_cc_half(const BqJob& job, int side, int s, const int32_t* sp, int decide, float* fields_out,
+                              cudaStream_t st);
+// End of sweep s (or of sweep *sp_read): energies, running best, snapshots; with
+// sp_write, stores the next sweep index there.
+cudaError_t bq_launch_sweep_end(const BqJob& job, int s, int init, const int32_t* sp_read, int32_t* sp_write,
+                                cudaStream_t st);
 cudaError_t bq_launch_readout(const BqJob& job, int which /*0 final, 1 best*/, int8_t* out_pm, double* out_E,
                               cudaStream_t st);
 cudaError_t bq_launch_encode(const BqJob& job, const int8_t* d_states, cudaStream_t st);

@@ -269,21 +269,28 @@ __device__ __forceinline__ float warp_transpose_sum(float (&e)[32], int lane)
 // the epilogue of one tile (each CTA its 128 rows) overlaps the MMAs of the
 // next; a buffer is reused once the epilogue warps of both CTAs released it.
 //
-// TABMODE (+-1 couplings) says where the decisions read the threshold row
-// T[F - F_min] of the sweep's beta level:
-//   0  global memory (row too large for shared memory);
-//   1  the dense row, copied into shared memory once per launch;
-//   2  only the window [wlo, wlo + ww) of fields where T is neither 0 nor
-//      2^32 - 1 (plus one saturated entry on each side), copied 32 times so
-//      that lane l reads copy l: a conflict-free shared-memory load.  A field
-//      outside the window is clamped to its edge, which holds the saturated
-//      value, so every decision compares against the same table value.
+// TABMODE (+-1 couplings) says where the decisions read the threshold window
+// of the sweep's beta level (the row T[F - F_min] restricted to the indices
+// [lo, lo + width) outside which T is saturated; a field outside the window is
+// clamped to its edge, which holds the saturated value, so every decision
+// compares against the same table value):
+//   0  global memory (window too wide for shared memory);
+//   1  the window, copied into shared memory once per launch;
+//   2  the window copied 32 times (width <= 256) so that lane l reads copy l:
+//      a conflict-free shared-memory load.
 template <int KIND, int TABMODE>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     bq_tc_half_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmA2,
-                      const __grid_constant__ CUtensorMap tmB, BqJob job, int side, int s, int decide,
-                      float* fields_out, int* err, int wlo, int ww)
+                      const __grid_constant__ CUtensorMap tmB, BqJob job, int side, int s_arg, const int32_t* sp,
+                      int decide, float* fields_out, int* err)
 {
+    const int s = sp ? *sp : s_arg;
+    if (decide && s >= job.S) return;  // uniform over the grid: before any barrier or allocation
+    TabWindow win{0, 0, 1};
+    if (KIND == 0 && decide) {
+        const int l = s / job.step;
+        win = TabWindow{job.win[3 * l + 2], job.win[3 * l], job.win[3 * l + 1]};
+    }
     using Cfg = TcCfg<KIND>;
     constexpr int S = Cfg::STAGES;
     constexpr int NA = KIND == 1 ? 2 : 1;  // J operands per stage
@@ -402,26 +409,27 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
         const bool pm1 = KIND == 0;
         const uint32_t acce_r0 = map_rank(&acce_bar[0], 0), acce_r1 = map_rank(&acce_bar[1], 0);
         float cexp = 0.0f;
-        const uint32_t* trow = pm1 ? job.table + (size_t)(s / job.step) * job.nF : nullptr;
+        const uint32_t* trow = pm1 ? job.table + win.off : nullptr;
+        const int wlo = win.lo, ww = win.width;
         if (TABMODE == 2) {
             for (int f = et; f < ww; f += ET) {
-                const uint32_t v = __ldg(trow + wlo + f);
+                const uint32_t v = __ldg(trow + f);
 #pragma unroll 8
                 for (int c = 0; c < 32; ++c) stab[f * 32 + ((c + f) & 31)] = v;
             }
         }
         if (TABMODE == 1) {
-            for (int f0 = et; f0 < job.nF; f0 += ET * 4) {
+            for (int f0 = et; f0 < ww; f0 += ET * 4) {
                 uint32_t v[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int f = f0 + u * ET;
-                    v[u] = f < job.nF ? __ldg(trow + f) : 0u;
+                    v[u] = f < ww ? __ldg(trow + f) : 0u;
                 }
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int f = f0 + u * ET;
-                    if (f < job.nF) stab[f] = v[u];
+                    if (f < ww) stab[f] = v[u];
                 }
             }
         }
@@ -479,10 +487,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
 #pragma unroll
                             for (int b = 0; b < 4; ++b) {
                                 if (pm1) {
-                                    const int f = (int)F[b] - job.fmin;
+                                    const int f = min(max((int)F[b] - job.fmin, wlo), wlo + ww - 1) - wlo;
                                     uint32_t T;
                                     if (TABMODE == 2)
-                                        T = stab[(min(max(f, wlo), wlo + ww - 1) - wlo) * 32 + lane];
+                                        T = stab[f * 32 + lane];
                                     else if (TABMODE == 1)
                                         T = stab[f];
                                     else
@@ -652,8 +660,8 @@ cudaError_t bq_tc_set_smem()
     return cudaSuccess;
 }
 
-cudaError_t bq_launch_tc_half(const BqTcMaps& maps, const BqJob& job, int side, int s, int decide, float* fields_out,
-                              int* err, int wlo, int ww, cudaStream_t st)
+cudaError_t bq_launch_tc_half(const BqTcMaps& maps, const BqJob& job, int side, int s, const int32_t* sp, int decide,
+                              float* fields_out, int* err, cudaStream_t st)
 {
     const int kind = job.inst.jtype == PB_J_PM1_I8 ? 0 : 1;
     const size_t smem = bq_tc_smem_bytes(kind);
@@ -664,15 +672,14 @@ cudaError_t bq_launch_tc_half(const BqTcMaps& maps, const BqJob& job, int side, 
     const CUtensorMap& A = side == 0 ? maps.a[0] : maps.a[2];
     const CUtensorMap& A2 = side == 0 ? maps.a[1] : maps.a[3];
     const CUtensorMap& B = maps.b[1 - side];
-    const bool use_win = decide && ww > 0 && ww <= kBqTcWindowMax && wlo >= 0 && wlo + ww <= job.nF;
-    if (kind == 0 && use_win)
-        bq_tc_half_kernel<0, 2><<<grid, kThreads, smem, st>>>(A, A2, B, job, side, s, decide, fields_out, err, wlo, ww);
-    else if (kind == 0 && job.nF * 4 <= TcCfg<0>::TAB_BYTES)
-        bq_tc_half_kernel<0, 1><<<grid, kThreads, smem, st>>>(A, A2, B, job, side, s, decide, fields_out, err, 0, 0);
+    if (kind == 0 && job.tabmode == 2)
+        bq_tc_half_kernel<0, 2><<<grid, kThreads, smem, st>>>(A, A2, B, job, side, s, sp, decide, fields_out, err);
+    else if (kind == 0 && job.tabmode == 1)
+        bq_tc_half_kernel<0, 1><<<grid, kThreads, smem, st>>>(A, A2, B, job, side, s, sp, decide, fields_out, err);
     else if (kind == 0)
-        bq_tc_half_kernel<0, 0><<<grid, kThreads, smem, st>>>(A, A2, B, job, side, s, decide, fields_out, err, 0, 0);
+        bq_tc_half_kernel<0, 0><<<grid, kThreads, smem, st>>>(A, A2, B, job, side, s, sp, decide, fields_out, err);
     else
-        bq_tc_half_kernel<1, 0><<<grid, kThreads, smem, st>>>(A, A2, B, job, side, s, decide, fields_out, err, 0, 0);
+        bq_tc_half_kernel<1, 0><<<grid, kThreads, smem, st>>>(A, A2, B, job, side, s, sp, decide, fields_out, err);
     return cudaGetLastError();
 }
 

@@ -23,9 +23,10 @@ size_t bq_tc_smem_bytes(int kind);
 cudaError_t bq_tc_set_smem();
 cudaError_t bq_tc_make_map(CUtensorMap* map, const void* base, int elem_bytes, uint64_t cols, uint64_t rows,
                            uint64_t ld_bytes, int box_rows);
-// wlo, ww: the unsaturated window of the threshold row of sweep s's level
-// (first index and width, see the kernel); ww = 0 when not known.
-cudaError_t bq_launch_tc_half(const BqTcMaps& maps, const BqJob& job, int side, int s, int decide, float* fields_out,
-                              int* err, int wlo, int ww, cudaStream_t st);
+// The sweep index is s, or the device value *sp when sp is not null (see
+// bq_launch_cc_half); the threshold windows are read from job.win, from where
+// job.tabmode says (0 global, 1 shared, 2 shared with 32 copies).
+cudaError_t bq_launch_tc_half(const BqTcMaps& maps, const BqJob& job, int side, int s, const int32_t* sp, int decide,
+                              float* fields_out, int* err, cudaStream_t st);
 
 }  // namespace pb

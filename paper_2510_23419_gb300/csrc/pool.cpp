@@ -13,7 +13,7 @@ namespace pb {
 namespace {
 
 constexpr int kMaxDevices = 64;
-constexpr int kLaunchStreams = 16;
+constexpr int kLaunchStreams = 32;
 
 struct DeviceRes {
     bool init = false;
