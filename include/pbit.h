@@ -58,7 +58,7 @@ typedef enum pb_status {
     PB_EUNSUPPORTED = 7   /* valid request outside what this library implements */
 } pb_status;
 
-typedef enum pb_topology { PB_TOPO_EA3D = 0, PB_TOPO_BICLIQUE = 1 } pb_topology;
+typedef enum pb_topology { PB_TOPO_EA3D = 0, PB_TOPO_BICLIQUE = 1, PB_TOPO_CSR = 2 } pb_topology;
 
 /* Coupling storage of an instance.
  * PB_J_PM1_I8: int8 couplings in {-1, +1}; h (if any) int8, |h| <= 64.  Fields are
@@ -148,6 +148,34 @@ pb_status pb_create_instance(const pb_instance_desc* desc, void* stream, pb_inst
 void pb_instance_destroy(pb_instance* inst);
 /* Number of spins N of an instance (EA L^3, biclique 2n), or -1. */
 int64_t pb_instance_spins(const pb_instance* inst);
+
+/* General sparse instance (Eq. 1 on an arbitrary edge set): N spins, each
+ * undirected edge (eu[e], ev[e]) listed once with coupling J[e] (int8 +-1 or
+ * float; repeated pairs are separate edges), fields h ([N] or NULL).  The
+ * update groups (Sec. 1.2.2) are the classes of `colour` ([N], values 0..254,
+ * no edge inside a class: else PB_ECOLOUR) or, when colour is NULL, of the
+ * greedy colouring below; classes are updated in increasing colour order and a
+ * spin's Philox counter word 0 is its rank in its class (ascending index).
+ * Runs use the plain form (one launch per class and sweep).  Errors: PB_EINVAL
+ * (edge out of range, self-loop, PM1 value not +-1, |h| > 64), PB_ECOLOUR. */
+typedef struct pb_graph_desc {
+    int32_t N;
+    int32_t jtype;         /* pb_jtype */
+    int64_t n_edges;
+    const int32_t* eu;     /* [n_edges] */
+    const int32_t* ev;     /* [n_edges] */
+    const void* J;         /* [n_edges] int8 or float */
+    const void* h;         /* [N] int8 or float, NULL = 0 */
+    const int32_t* colour; /* [N] or NULL = greedy colouring */
+} pb_graph_desc;
+pb_status pb_create_graph_instance(const pb_graph_desc* desc, void* stream, pb_instance** out);
+/* Greedy colouring (host only, no device use): vertices by decreasing degree,
+ * ties by index, each takes the smallest colour unused by its coloured
+ * neighbours.  Writes colour_out[N]; returns the number of colours, or -1 on
+ * invalid arguments (edge out of range, self-loop). */
+int32_t pb_greedy_colouring(int32_t N, int64_t n_edges, const int32_t* eu, const int32_t* ev, int32_t* colour_out);
+/* Number of colour classes of an instance (2 for EA and biclique), or -1. */
+int32_t pb_instance_colours(const pb_instance* inst);
 
 /* Start an anneal of `replicas` independent replicas (Sec. 1.3.1) on `stream`.
  * Asynchronous: returns once the work is queued.  `opts` may be NULL (AUTO form,

@@ -72,6 +72,7 @@ double est_cost(const pb_instance* I, int R, int S, int form)
 {
     const double upd = (double)I->N * R * std::max(1, S);
     if (I->topo == PB_TOPO_EA3D) return upd / (form == PB_FORM_PLAIN ? 9e10 : 7e11);
+    if (I->topo == PB_TOPO_CSR) return upd * std::max(1, I->maxdeg) / 4e11 + 3.0 * std::max(1, S) * 2e-6;
     const double flop = upd * 2.0 * I->n * (I->jtype == PB_J_F32 ? 2.0 : 1.0);
     const double rate = form == PB_FORM_CUDACORE ? 2.5e13 : (I->jtype == PB_J_F32 ? 1.5e15 : 1.8e15);
     // small instances fill a fraction of the tensor tiles
@@ -112,6 +113,8 @@ void choose_form(const pb_instance* I, int R, int requested, int& form, int& wt)
                 form = requested == PB_FORM_RESIDENT ? PB_FORM_RESIDENT : PB_FORM_PLAIN;
             }
         }
+    } else if (I->topo == PB_TOPO_CSR) {
+        if (form == PB_FORM_AUTO) form = PB_FORM_PLAIN;
     } else {
         if (tuned) form = te.form;
         if (form == PB_FORM_AUTO) form = PB_FORM_TENSOR;
@@ -141,6 +144,8 @@ pb_status batch_start(int count, pb_instance* const* insts, const pb_schedule* s
             if (form == PB_FORM_RESIDENT && wt == 0) return fail(PB_EUNSUPPORTED, "lattice too large for the resident form");
             if (form != PB_FORM_RESIDENT && form != PB_FORM_PLAIN)
                 return fail(PB_EUNSUPPORTED, "form not available for EA instances");
+        } else if (I->topo == PB_TOPO_CSR) {
+            if (form != PB_FORM_PLAIN) return fail(PB_EUNSUPPORTED, "general sparse instances run in the plain form");
         } else if (form != PB_FORM_TENSOR && form != PB_FORM_CUDACORE) {
             return fail(PB_EUNSUPPORTED, "form not available for biclique instances");
         }
@@ -176,6 +181,8 @@ pb_status batch_start(int count, pb_instance* const* insts, const pb_schedule* s
         if (j.I->topo == PB_TOPO_EA3D) {
             ps = ea_prepare_run(r, j.I, &scheds[j.q], j.R, seeds[j.q], o, j.form, j.wt, st);
             if (ps == PB_OK && j.form == PB_FORM_RESIDENT) resident.push_back(r);
+        } else if (j.I->topo == PB_TOPO_CSR) {
+            ps = csr_setup(r, j.I, &scheds[j.q], j.R, seeds[j.q], o, st);
         } else {
             pb_anneal_opts oo = o ? *o : pb_anneal_opts{PB_FORM_AUTO, 0, NAN};
             oo.form = j.form;
@@ -252,7 +259,9 @@ pb_status batch_start(int count, pb_instance* const* insts, const pb_schedule* s
         if (stream_of) (*stream_of)[j->q] = k;
         pb_run* r = runs[j->q].get();
         r->stream = pool_stream(k);
-        ps = (j->I->topo == PB_TOPO_EA3D) ? ea_enqueue_plain(r, pool_stream(k)) : bq_launch(r, pool_stream(k));
+        ps = (j->I->topo == PB_TOPO_EA3D)  ? ea_enqueue_plain(r, pool_stream(k))
+             : (j->I->topo == PB_TOPO_CSR) ? csr_launch(r, pool_stream(k))
+                                            : bq_launch(r, pool_stream(k));
         if (ps != PB_OK) return ps;
     }
     // ---- join back into the caller's stream
@@ -303,6 +312,8 @@ pb_status pb_autotune(pb_instance* I, int32_t R, int32_t probe_sweeps, void* str
         const int wmax = ea_choose_wt(I, R, nF);
         for (int w = 1; w <= wmax && cand.size() < 7; w *= 2) cand.push_back({PB_FORM_RESIDENT, w});
         cand.push_back({PB_FORM_PLAIN, 0});
+    } else if (I->topo == PB_TOPO_CSR) {
+        cand.push_back({PB_FORM_PLAIN, 0});
     } else {
         cand.push_back({PB_FORM_TENSOR, 0});
         cand.push_back({PB_FORM_CUDACORE, 0});
@@ -335,6 +346,9 @@ pb_status pb_autotune(pb_instance* I, int32_t R, int32_t probe_sweeps, void* str
             } else if (ps == PB_OK) {
                 ps = ea_enqueue_plain(run.get(), st);
             }
+        } else if (I->topo == PB_TOPO_CSR) {
+            ps = csr_setup(run.get(), I, &sc, R, 1, &o, st);
+            if (ps == PB_OK) ps = csr_launch(run.get(), st);
         } else {
             ps = bq_setup(run.get(), I, &sc, R, 1, &o, st);
             if (ps == PB_OK) ps = bq_launch(run.get(), st);

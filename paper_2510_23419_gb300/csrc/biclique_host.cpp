@@ -200,35 +200,8 @@ static pb_status bq_prepare(pb_run* run, pb_instance* I, const pb_schedule* sc, 
         const int fmax = n + I->hmax;
         j.fmin = -fmax;
         j.nF = 2 * fmax + 1;
-        // Threshold rows (Eq. 2, FP64 on the host), one per beta level, stored as the
-        // window of the row outside which T is saturated: T is nondecreasing in F, so
-        // every entry below the window is 0 and every entry above it 2^32 - 1, and the
-        // window keeps one saturated entry on each side; a lookup clamps F into the
-        // window.  The window edges are found by bisection, so a level costs
-        // O(width + log nF) evaluations instead of nF.
         std::vector<uint32_t> tab;
-        run->bq_win.assign((size_t)nlev * 3, 0);
-        for (int l = 0; l < nlev; ++l) {
-            const double beta = betas.empty() ? 0.0 : betas[l];
-            auto T = [&](int f) { return threshold_u32(beta, (double)(f + j.fmin)); };
-            int a = 0, b = j.nF;  // first index with T > 0
-            while (a < b) {
-                const int m = (a + b) / 2;
-                if (T(m) > 0u) b = m; else a = m + 1;
-            }
-            const int lo = std::max(0, a - 1);
-            a = 0;
-            b = j.nF;  // first index with T = 2^32 - 1
-            while (a < b) {
-                const int m = (a + b) / 2;
-                if (T(m) == 0xFFFFFFFFu) b = m; else a = m + 1;
-            }
-            const int hi = std::max(lo, std::min(j.nF - 1, a));
-            run->bq_win[3 * l] = lo;
-            run->bq_win[3 * l + 1] = hi - lo + 1;
-            run->bq_win[3 * l + 2] = (int32_t)tab.size();
-            for (int f = lo; f <= hi; ++f) tab.push_back(T(f));
-        }
+        threshold_windows(betas, j.nF, j.fmin, tab, run->bq_win);
         int wmax = 0;
         for (int l = 0; l < nlev; ++l) wmax = std::max(wmax, run->bq_win[3 * l + 1]);
         j.tabmode = wmax <= kBqTcWindowMax ? 2 : (wmax * 4 <= 33 * 1024 ? 1 : 0);

@@ -54,13 +54,6 @@ struct BqJob {
     int32_t tabmode;        // tensor form: where the decisions read the windows (widest level decides)
 };
 
-// Threshold window of one beta level (+-1 couplings): the row T[F - F_min]
-// restricted to indices [lo, lo + width), stored at table + off; indices
-// outside the window take the value at its nearer edge.
-struct TabWindow {
-    int32_t off, lo, width;
-};
-
 constexpr int kBqTileRows = 64;   // CUDA-core field kernel: rows (spins of the updated side) per block
 constexpr int kBqTileReps = 64;   // replicas per block
 

@@ -1,0 +1,288 @@
+// csr.cu -- p-bit update on general sparse instances (arXiv 2510.23419: the
+// Ising graph of Eq. 1 with an arbitrary edge set; the update groups of
+// Sec. 1.2.2 are the classes of a proper colouring, k >= 2 of them, updated in
+// turn).  One launch per colour class and sweep (the plain form).
+//
+// A thread owns one spin i of the class and one spin word (4 replicas):
+// F_r = sum_j J_ij m_j(r) + h_i (Eq. 3) over i's compressed row, then the p-bit
+// decision (Eq. 2) with the Philox word of (class rank of i, s, word, colour).
+// Spins of one class have no edge between them, so the class is updated in
+// place.
+#include "csr_launch.h"
+#include "ea_kernels.cuh"
+
+namespace pb {
+
+namespace {
+
+__device__ __forceinline__ uint32_t byte_of(uint32_t w, int b) { return (w >> (8 * b)) & 0xFFu; }
+
+// sum_j J_ij (1 - 2 bit_j) for 4 replicas of a +-1 row: packed byte counters of
+// the set bits under J = +1 and J = -1, emptied every 255 neighbours.
+__device__ __forceinline__ void pm1_row(const CsrJob& job, const uint32_t* m, int i, int q, int (&G)[4])
+{
+    const int a0 = job.g.rowptr[i], a1 = job.g.rowptr[i + 1];
+    int sumJ = 0;
+    int d[4] = {0, 0, 0, 0};
+    uint32_t accp = 0, accn = 0;
+    int cnt = 0;
+    for (int a = a0; a < a1; ++a) {
+        const uint32_t w = m[(size_t)job.g.col[a] * job.Rw + q];
+        const int J = job.g.J8[a];
+        sumJ += J;
+        if (J > 0) accp += w; else accn += w;
+        if (++cnt == 255) {
+#pragma unroll
+            for (int b = 0; b < 4; ++b) d[b] += (int)byte_of(accp, b) - (int)byte_of(accn, b);
+            accp = accn = 0;
+            cnt = 0;
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < 4; ++b) G[b] = sumJ - 2 * (d[b] + (int)byte_of(accp, b) - (int)byte_of(accn, b));
+}
+
+template <typename T>
+__device__ __forceinline__ void f32_row(const CsrJob& job, const uint32_t* m, int i, int q, T (&G)[4])
+{
+    const int a0 = job.g.rowptr[i], a1 = job.g.rowptr[i + 1];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) G[b] = T(0);
+    for (int a = a0; a < a1; ++a) {
+        const uint32_t w = m[(size_t)job.g.col[a] * job.Rw + q];
+        const T J = (T)job.g.Jf[a];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) G[b] += byte_of(w, b) ? -J : J;
+    }
+}
+
+__global__ void __launch_bounds__(256) csr_init_kernel(CsrJob job)
+{
+    const long long total = (long long)job.g.N * job.Rw;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int p = (int)(idx / job.Rw), q = (int)(idx - (long long)p * job.Rw);
+        const int i = job.g.cls_v[p];
+        const int c = job.g.colour[i];
+        const uint32_t k = (uint32_t)(p - job.g.cls_off[c]);
+        const U4 r = philox10(k, 0u, (uint32_t)q, (kTagInit << 24) | (uint32_t)c, job.key0, job.key1);
+        const uint32_t ws[4] = {r.x, r.y, r.z, r.w};
+        uint32_t w = 0;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) w |= (ws[b] >= 0x80000000u ? 1u : 0u) << (8 * b);
+        job.spins[(size_t)i * job.Rw + q] = w;
+    }
+}
+
+template <int JT>
+__global__ void __launch_bounds__(256) csr_class_kernel(CsrJob job, int c, int s)
+{
+    const int off = job.g.cls_off[c], ncls = job.g.cls_off[c + 1] - off;
+    const int lev = s / job.step;
+    TabWindow win{0, 0, 1};
+    float cexp = 0.0f;
+    if (JT == PB_J_PM1_I8)
+        win = TabWindow{job.win[3 * lev + 2], job.win[3 * lev], job.win[3 * lev + 1]};
+    else
+        cexp = f32_cexp(job.betaf[lev]);
+    const long long total = (long long)ncls * job.Rw;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int t = (int)(idx / job.Rw), q = (int)(idx - (long long)t * job.Rw);
+        const int i = job.g.cls_v[off + t];
+        const U4 r = philox10((uint32_t)t, (uint32_t)s, (uint32_t)q, (kTagDecision << 24) | (uint32_t)c, job.key0,
+                              job.key1);
+        const uint32_t ws[4] = {r.x, r.y, r.z, r.w};
+        uint32_t w = 0;
+        if (JT == PB_J_PM1_I8) {
+            int G[4];
+            pm1_row(job, job.spins, i, q, G);
+            const int h = job.g.h8 ? job.g.h8[i] : 0;
+            const uint32_t* trow = job.table + win.off;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const int f = min(max(G[b] + h - job.fmin, win.lo), win.lo + win.width - 1) - win.lo;
+                w |= decide_bit(ws[b], trow[f]) << (8 * b);
+            }
+        } else {
+            float G[4];
+            f32_row(job, job.spins, i, q, G);
+            const float h = job.g.hf ? job.g.hf[i] : 0.0f;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) w |= decide_f32(ws[b], G[b] + h, cexp) << (8 * b);
+        }
+        job.spins[(size_t)i * job.Rw + q] = w;
+    }
+}
+
+// 2E partials per chunk of kCsrChunk vertices: -(sum_i m_i G_i) - 2 sum_i h_i m_i,
+// with G_i = sum_j J_ij m_j (every edge seen from both ends).  +-1: exact
+// integers; real couplings: FP32 rows (running energy) or FP64 rows (EXACT).
+template <int JT, bool EXACT>
+__global__ void __launch_bounds__(128) csr_energy_kernel(CsrJob job, const uint32_t* __restrict__ m)
+{
+    const int q = blockIdx.y * blockDim.x + threadIdx.x;
+    if (q >= job.Rw) return;
+    const int i0 = blockIdx.x * kCsrChunk, i1 = min(job.g.N, i0 + kCsrChunk);
+    double e[4] = {0.0, 0.0, 0.0, 0.0};
+    long long ei[4] = {0, 0, 0, 0};
+    for (int i = i0; i < i1; ++i) {
+        const uint32_t mw = m[(size_t)i * job.Rw + q];
+        if (JT == PB_J_PM1_I8) {
+            int G[4];
+            pm1_row(job, m, i, q, G);
+            const int h = job.g.h8 ? job.g.h8[i] : 0;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const int mi = byte_of(mw, b) ? -1 : 1;
+                ei[b] -= (long long)mi * (G[b] + 2 * h);
+            }
+        } else if (EXACT) {
+            double G[4];
+            f32_row(job, m, i, q, G);
+            const double h = job.g.hf ? (double)job.g.hf[i] : 0.0;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) e[b] -= (byte_of(mw, b) ? -1.0 : 1.0) * (G[b] + 2.0 * h);
+        } else {
+            float G[4];
+            f32_row(job, m, i, q, G);
+            const float h = job.g.hf ? job.g.hf[i] : 0.0f;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) e[b] -= (double)((byte_of(mw, b) ? -1.0f : 1.0f) * (G[b] + 2.0f * h));
+        }
+    }
+    double* out = job.part + (size_t)blockIdx.x * 4 * job.Rw + 4 * q;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) out[b] = JT == PB_J_PM1_I8 ? (double)ei[b] : e[b];
+}
+
+__device__ __forceinline__ double csr_energy_of(const CsrJob& job, int r)
+{
+    double t = 0.0;
+    for (int ch = 0; ch < job.nchunk; ++ch) t += job.part[(size_t)ch * 4 * job.Rw + r];
+    return 0.5 * t;
+}
+
+__global__ void __launch_bounds__(256) csr_sweep_end_kernel(CsrJob job, int s, int init)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= 4 * job.Rw) return;
+    const double E = csr_energy_of(job, r);
+    bool imp;
+    if (init) {
+        imp = true;
+        job.E_best[r] = E;
+        job.best_sweep[r] = -1;
+        job.hit_sweep[r] = -1;
+    } else {
+        imp = E < job.E_best[r];
+        if (imp) {
+            job.E_best[r] = E;
+            job.best_sweep[r] = s;
+        }
+        if (job.has_target && job.hit_sweep[r] < 0 && E <= job.target) job.hit_sweep[r] = s;
+    }
+    job.improved[r] = imp ? 1 : 0;
+}
+
+// best <- spins for the replicas flagged as improved (byte masks per word).
+__global__ void __launch_bounds__(256) csr_snapshot_kernel(CsrJob job)
+{
+    const long long total = (long long)job.g.N * job.Rw;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int q = (int)(idx % job.Rw);
+        const uint32_t f = *reinterpret_cast<const uint32_t*>(job.improved + 4 * q);  // 4 flag bytes
+        if (!f) continue;
+        const uint32_t mask = f * 0xFFu;  // 0x01 -> 0xFF per byte
+        job.best[idx] = (job.spins[idx] & mask) | (job.best[idx] & ~mask);
+    }
+}
+
+__global__ void __launch_bounds__(256) csr_states_kernel(CsrJob job, const uint32_t* __restrict__ m, int8_t* out)
+{
+    const long long total = (long long)job.R * job.g.N;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(idx / job.g.N), i = (int)(idx - (long long)r * job.g.N);
+        out[idx] = byte_of(m[(size_t)i * job.Rw + (r >> 2)], r & 3) ? (int8_t)-1 : (int8_t)1;
+    }
+}
+
+__global__ void __launch_bounds__(256) csr_energy_out_kernel(CsrJob job, double* out)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < job.R) out[r] = csr_energy_of(job, r);
+}
+
+__global__ void __launch_bounds__(256) csr_fields_kernel(CsrJob job, const int8_t* __restrict__ st, float* out)
+{
+    const long long total = (long long)job.R * job.g.N;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(idx / job.g.N), i = (int)(idx - (long long)r * job.g.N);
+        const int8_t* mr = st + (size_t)r * job.g.N;
+        float F = job.g.jtype == PB_J_PM1_I8 ? (job.g.h8 ? (float)job.g.h8[i] : 0.0f) : (job.g.hf ? job.g.hf[i] : 0.0f);
+        for (int a = job.g.rowptr[i]; a < job.g.rowptr[i + 1]; ++a) {
+            const float J = job.g.jtype == PB_J_PM1_I8 ? (float)job.g.J8[a] : job.g.Jf[a];
+            F = fmaf(J, (float)mr[job.g.col[a]], F);
+        }
+        out[idx] = F;
+    }
+}
+
+unsigned grid_for(long long total) { return (unsigned)std::max(1LL, std::min<long long>((total + 255) / 256, 152LL * 16)); }
+
+}  // namespace
+
+cudaError_t csr_launch_init(const CsrJob& job, cudaStream_t st)
+{
+    csr_init_kernel<<<grid_for((long long)job.g.N * job.Rw), 256, 0, st>>>(job);
+    return cudaGetLastError();
+}
+
+cudaError_t csr_launch_class(const CsrJob& job, int c, int s, cudaStream_t st)
+{
+    const long long total = (long long)job.Rw * job.g.N;  // an upper bound of the class size
+    if (job.g.jtype == PB_J_PM1_I8)
+        csr_class_kernel<PB_J_PM1_I8><<<grid_for(total / std::max(1, job.g.n_colours) + 1), 256, 0, st>>>(job, c, s);
+    else
+        csr_class_kernel<PB_J_F32><<<grid_for(total / std::max(1, job.g.n_colours) + 1), 256, 0, st>>>(job, c, s);
+    return cudaGetLastError();
+}
+
+cudaError_t csr_launch_energy(const CsrJob& job, const uint32_t* m, int exact, cudaStream_t st)
+{
+    const dim3 grid((unsigned)job.nchunk, (unsigned)((job.Rw + 127) / 128));
+    if (job.g.jtype == PB_J_PM1_I8)
+        csr_energy_kernel<PB_J_PM1_I8, true><<<grid, 128, 0, st>>>(job, m);
+    else if (exact)
+        csr_energy_kernel<PB_J_F32, true><<<grid, 128, 0, st>>>(job, m);
+    else
+        csr_energy_kernel<PB_J_F32, false><<<grid, 128, 0, st>>>(job, m);
+    return cudaGetLastError();
+}
+
+cudaError_t csr_launch_sweep_end(const CsrJob& job, int s, int init, cudaStream_t st)
+{
+    csr_sweep_end_kernel<<<(4 * job.Rw + 255) / 256, 256, 0, st>>>(job, s, init);
+    csr_snapshot_kernel<<<grid_for((long long)job.g.N * job.Rw), 256, 0, st>>>(job);
+    return cudaGetLastError();
+}
+
+cudaError_t csr_launch_readout(const CsrJob& job, const uint32_t* m, int8_t* out_pm, double* out_E, cudaStream_t st)
+{
+    csr_states_kernel<<<grid_for((long long)job.R * job.g.N), 256, 0, st>>>(job, m, out_pm);
+    cudaError_t e = csr_launch_energy(job, m, 1, st);
+    if (e != cudaSuccess) return e;
+    csr_energy_out_kernel<<<(job.R + 255) / 256, 256, 0, st>>>(job, out_E);
+    return cudaGetLastError();
+}
+
+cudaError_t csr_launch_fields(const CsrJob& job, const int8_t* states, float* out, cudaStream_t st)
+{
+    csr_fields_kernel<<<grid_for((long long)job.R * job.g.N), 256, 0, st>>>(job, states, out);
+    return cudaGetLastError();
+}
+
+}  // namespace pb

@@ -1,0 +1,313 @@
+// csr_host.cpp -- general sparse instances (arXiv 2510.23419, Eq. 1 on an
+// arbitrary edge set; update groups of Sec. 1.2.2 from a proper colouring):
+// instance build, greedy colouring, runs of the plain per-class form.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <memory>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "pb_handles.h"
+
+namespace pb {
+
+namespace {
+
+// Greedy colouring, vertices by decreasing degree (ties by index): each takes
+// the smallest colour that none of its coloured neighbours has.  Returns the
+// number of colours.
+int greedy_colouring(int32_t N, int64_t E, const int32_t* eu, const int32_t* ev, int32_t* colour)
+{
+    std::vector<int64_t> off((size_t)N + 1, 0);
+    for (int64_t e = 0; e < E; ++e) {
+        off[(size_t)eu[e] + 1]++;
+        off[(size_t)ev[e] + 1]++;
+    }
+    for (int32_t i = 0; i < N; ++i) off[(size_t)i + 1] += off[i];
+    std::vector<int32_t> adj((size_t)(2 * E));
+    std::vector<int64_t> fill(off.begin(), off.end() - 1);
+    for (int64_t e = 0; e < E; ++e) {
+        adj[(size_t)fill[eu[e]]++] = ev[e];
+        adj[(size_t)fill[ev[e]]++] = eu[e];
+    }
+    std::vector<int32_t> order((size_t)N);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int32_t a, int32_t b) { return off[a + 1] - off[a] > off[b + 1] - off[b]; });
+    std::fill(colour, colour + N, -1);
+    std::vector<int64_t> seen;  // seen[c] == i: colour c is taken by a neighbour of i
+    int k = 0;
+    for (int32_t i : order) {
+        for (int64_t a = off[i]; a < off[i + 1]; ++a) {
+            const int32_t c = colour[adj[(size_t)a]];
+            if (c >= 0) {
+                if ((size_t)c >= seen.size()) seen.resize((size_t)c + 1, -1);
+                seen[(size_t)c] = i;
+            }
+        }
+        int c = 0;
+        while ((size_t)c < seen.size() && seen[(size_t)c] == i) ++c;
+        colour[i] = c;
+        k = std::max(k, c + 1);
+    }
+    return k;
+}
+
+}  // namespace
+
+pb_status csr_build(pb_instance* I, int32_t N, int64_t E, const int32_t* eu, const int32_t* ev, int jtype,
+                    const void* J, const void* h, const int32_t* colour_in, cudaStream_t st)
+{
+    if (N < 1 || E < 0) return fail(PB_EINVAL, "graph needs N >= 1 and n_edges >= 0");
+    if (E > 0 && (!eu || !ev || !J)) return fail(PB_EINVAL, "edge arrays are null");
+    if (2 * E > 2000000000LL) return fail(PB_EINVAL, "too many edges");
+    const bool pm1 = jtype == PB_J_PM1_I8;
+    for (int64_t e = 0; e < E; ++e) {
+        if (eu[e] < 0 || eu[e] >= N || ev[e] < 0 || ev[e] >= N) return fail(PB_EINVAL, "edge end out of range");
+        if (eu[e] == ev[e]) return fail(PB_EINVAL, "self-loop edge");
+        if (pm1) {
+            const int v = static_cast<const int8_t*>(J)[e];
+            if (v != 1 && v != -1) return fail(PB_EINVAL, "PM1 couplings must be +1 or -1");
+        }
+    }
+    // colouring: given (validated) or greedy
+    std::vector<int32_t> colour((size_t)N);
+    int k = 0;
+    if (colour_in) {
+        for (int32_t i = 0; i < N; ++i) {
+            if (colour_in[i] < 0 || colour_in[i] > 254) return fail(PB_ECOLOUR, "colour out of range [0, 254]");
+            colour[i] = colour_in[i];
+            k = std::max(k, colour[i] + 1);
+        }
+        for (int64_t e = 0; e < E; ++e)
+            if (colour[eu[e]] == colour[ev[e]]) return fail(PB_ECOLOUR, "an edge joins two spins of the same colour");
+    } else {
+        k = greedy_colouring(N, E, eu, ev, colour.data());
+        if (k > 255) return fail(PB_ECOLOUR, "greedy colouring needs more than 255 colours");
+    }
+    // compressed rows, half-edges in edge order
+    std::vector<int32_t> rowptr((size_t)N + 1, 0);
+    for (int64_t e = 0; e < E; ++e) {
+        rowptr[(size_t)eu[e] + 1]++;
+        rowptr[(size_t)ev[e] + 1]++;
+    }
+    for (int32_t i = 0; i < N; ++i) rowptr[(size_t)i + 1] += rowptr[i];
+    std::vector<int32_t> col((size_t)(2 * E));
+    std::vector<int8_t> J8(pm1 ? (size_t)(2 * E) : 0);
+    std::vector<float> Jf(pm1 ? 0 : (size_t)(2 * E));
+    std::vector<int32_t> fill(rowptr.begin(), rowptr.end() - 1);
+    for (int64_t e = 0; e < E; ++e) {
+        const int32_t ends[2][2] = {{eu[e], ev[e]}, {ev[e], eu[e]}};
+        for (auto& uv : ends) {
+            const int32_t a = fill[uv[0]]++;
+            col[(size_t)a] = uv[1];
+            if (pm1) J8[(size_t)a] = static_cast<const int8_t*>(J)[e];
+            else Jf[(size_t)a] = static_cast<const float*>(J)[e];
+        }
+    }
+    int maxdeg = 0;
+    for (int32_t i = 0; i < N; ++i) maxdeg = std::max(maxdeg, rowptr[(size_t)i + 1] - rowptr[i]);
+    // classes in ascending index
+    std::vector<int32_t> cls_off((size_t)k + 1, 0);
+    for (int32_t i = 0; i < N; ++i) cls_off[(size_t)colour[i] + 1]++;
+    for (int c = 0; c < k; ++c) cls_off[(size_t)c + 1] += cls_off[c];
+    std::vector<int32_t> cls_v((size_t)N), cf(cls_off.begin(), cls_off.end() - 1);
+    for (int32_t i = 0; i < N; ++i) cls_v[(size_t)cf[colour[i]]++] = i;
+    int hmax = 0;
+    if (h && pm1) {
+        for (int32_t i = 0; i < N; ++i) hmax = std::max(hmax, std::abs((int)static_cast<const int8_t*>(h)[i]));
+        if (hmax > 64) return fail(PB_EINVAL, "PM1 fields must satisfy |h| <= 64");
+    }
+
+    I->topo = PB_TOPO_CSR;
+    I->jtype = jtype;
+    I->N = N;
+    I->n = N;
+    I->has_h = h ? 1 : 0;
+    I->hmax = hmax;
+    I->maxdeg = maxdeg;
+    I->n_colours = k;
+    DevBuf* B = I->csr_bufs;  // 0 rowptr, 1 col, 2 J, 3 h, 4 cls_off, 5 cls_v, 6 colour
+    auto up = [&](DevBuf& b, const void* src, size_t bytes) -> pb_status {
+        PB_ALLOC(b, bytes);
+        if (bytes) PB_CUDA_TRY(cudaMemcpyAsync(b.p, src, bytes, cudaMemcpyHostToDevice, st));
+        return PB_OK;
+    };
+    pb_status ps;
+    if ((ps = up(B[0], rowptr.data(), rowptr.size() * 4)) != PB_OK) return ps;
+    if ((ps = up(B[1], col.data(), col.size() * 4)) != PB_OK) return ps;
+    if ((ps = pm1 ? up(B[2], J8.data(), J8.size()) : up(B[2], Jf.data(), Jf.size() * 4)) != PB_OK) return ps;
+    if (h && (ps = up(B[3], h, (size_t)N * (pm1 ? 1 : 4))) != PB_OK) return ps;
+    if ((ps = up(B[4], cls_off.data(), cls_off.size() * 4)) != PB_OK) return ps;
+    if ((ps = up(B[5], cls_v.data(), cls_v.size() * 4)) != PB_OK) return ps;
+    if ((ps = up(B[6], colour.data(), colour.size() * 4)) != PB_OK) return ps;
+    PB_CUDA_TRY(cudaStreamSynchronize(st));
+    CsrDevice& g = I->csr;
+    g = CsrDevice{};
+    g.N = N;
+    g.jtype = jtype;
+    g.n_colours = k;
+    g.maxdeg = maxdeg;
+    g.has_h = I->has_h;
+    g.hmax = hmax;
+    g.rowptr = B[0].as<int32_t>();
+    g.col = B[1].as<int32_t>();
+    g.J8 = pm1 ? B[2].as<int8_t>() : nullptr;
+    g.Jf = pm1 ? nullptr : B[2].as<float>();
+    g.h8 = (h && pm1) ? B[3].as<int8_t>() : nullptr;
+    g.hf = (h && !pm1) ? B[3].as<float>() : nullptr;
+    g.cls_off = B[4].as<int32_t>();
+    g.cls_v = B[5].as<int32_t>();
+    g.colour = B[6].as<int32_t>();
+    return PB_OK;
+}
+
+pb_status csr_setup(pb_run* run, pb_instance* I, const pb_schedule* sc, int R, uint64_t seed,
+                    const pb_anneal_opts* opts, cudaStream_t st)
+{
+    const int form = opts ? opts->form : PB_FORM_AUTO;
+    if (form != PB_FORM_AUTO && form != PB_FORM_PLAIN)
+        return fail(PB_EUNSUPPORTED, "general sparse instances run in the plain form");
+    std::vector<double> betas;
+    int step = 1;
+    pb_status ps = schedule_levels(sc, betas, step);
+    if (ps != PB_OK) return ps;
+    run->inst = I;
+    run->form = PB_FORM_PLAIN;
+    run->R = R;
+    run->S = sc->n_sweeps;
+    run->N = I->N;
+    run->stream = st;
+    CsrJob& j = run->cjob;
+    j = CsrJob{};
+    j.g = I->csr;
+    j.key0 = (uint32_t)(seed & 0xFFFFFFFFu);
+    j.key1 = (uint32_t)(seed >> 32);
+    j.S = sc->n_sweeps;
+    j.step = step;
+    j.R = R;
+    j.Rw = (R + 3) / 4;
+    const int nlev = std::max<int>(1, (int)betas.size());
+    if (I->jtype == PB_J_PM1_I8) {
+        const int fmax = I->maxdeg + I->hmax;
+        j.fmin = -fmax;
+        j.nF = 2 * fmax + 1;
+        std::vector<uint32_t> tab;
+        threshold_windows(betas, j.nF, j.fmin, tab, run->bq_win);
+        PB_ALLOC(run->table, tab.size() * 4);
+        PB_CUDA_TRY(cudaMemcpyAsync(run->table.p, tab.data(), tab.size() * 4, cudaMemcpyHostToDevice, st));
+        PB_ALLOC(run->extra[7], run->bq_win.size() * 4);
+        PB_CUDA_TRY(cudaMemcpyAsync(run->extra[7].p, run->bq_win.data(), run->bq_win.size() * 4,
+                                    cudaMemcpyHostToDevice, st));
+        j.table = run->table.as<uint32_t>();
+        j.win = run->extra[7].as<int32_t>();
+    } else {
+        std::vector<float> bf((size_t)nlev, 0.0f);
+        for (size_t l = 0; l < betas.size(); ++l) bf[l] = (float)betas[l];
+        PB_ALLOC(run->betaf, bf.size() * 4);
+        PB_CUDA_TRY(cudaMemcpyAsync(run->betaf.p, bf.data(), bf.size() * 4, cudaMemcpyHostToDevice, st));
+        j.betaf = run->betaf.as<float>();
+    }
+    PB_CUDA_TRY(cudaStreamSynchronize(st));
+    if (opts && !std::isnan(opts->target_energy)) {
+        j.has_target = 1;
+        j.target = opts->target_energy;
+    }
+    const size_t words = (size_t)I->N * j.Rw;
+    j.nchunk = (int)((I->N + kCsrChunk - 1) / kCsrChunk);
+    PB_ALLOC(run->final_words, words * 4);
+    PB_ALLOC(run->best_words, words * 4);
+    PB_ALLOC(run->extra[0], (size_t)j.nchunk * 4 * j.Rw * 8);
+    PB_ALLOC(run->extra[1], (size_t)4 * j.Rw * 8);
+    PB_ALLOC(run->best_sweep, (size_t)4 * j.Rw * 4);
+    PB_ALLOC(run->hit_sweep, (size_t)4 * j.Rw * 4);
+    PB_ALLOC(run->extra[2], (size_t)4 * j.Rw + 16);
+    j.spins = run->final_words.as<uint32_t>();
+    j.best = run->best_words.as<uint32_t>();
+    j.part = run->extra[0].as<double>();
+    j.E_best = run->extra[1].as<double>();
+    j.best_sweep = run->best_sweep.as<int32_t>();
+    j.hit_sweep = run->hit_sweep.as<int32_t>();
+    j.improved = run->extra[2].as<uint8_t>();
+    PB_ALLOC(run->best_pm, (size_t)R * I->N);
+    PB_ALLOC(run->final_pm, (size_t)R * I->N);
+    PB_ALLOC(run->E_out, (size_t)2 * R * 8);
+    PB_CUDA_TRY(cudaEventCreate(&run->ev_start));
+    PB_CUDA_TRY(cudaEventCreate(&run->ev_stop));
+    PB_CUDA_TRY(cudaEventCreate(&run->ev_k0));
+    PB_CUDA_TRY(cudaEventCreate(&run->ev_k1));
+    return PB_OK;
+}
+
+// Plain form: one launch per colour class and sweep, then the energy of the
+// sweep and the running best (Sec. 1.2.2, Eq. 2, Eq. 3).
+pb_status csr_launch(pb_run* run, cudaStream_t st)
+{
+    const CsrJob& j = run->cjob;
+    PB_CUDA_TRY(cudaEventRecord(run->ev_start, st));
+    PB_CUDA_TRY(csr_launch_init(j, st));
+    PB_CUDA_TRY(csr_launch_energy(j, j.spins, 0, st));
+    PB_CUDA_TRY(csr_launch_sweep_end(j, -1, 1, st));
+    PB_CUDA_TRY(cudaEventRecord(run->ev_k0, st));
+    for (int s = 0; s < j.S; ++s) {
+        for (int c = 0; c < j.g.n_colours; ++c) PB_CUDA_TRY(csr_launch_class(j, c, s, st));
+        PB_CUDA_TRY(csr_launch_energy(j, j.spins, 0, st));
+        PB_CUDA_TRY(csr_launch_sweep_end(j, s, 0, st));
+    }
+    PB_CUDA_TRY(cudaEventRecord(run->ev_k1, st));
+    PB_CUDA_TRY(csr_launch_readout(j, j.spins, run->final_pm.as<int8_t>(), run->E_out.as<double>(), st));
+    PB_CUDA_TRY(csr_launch_readout(j, j.best, run->best_pm.as<int8_t>(), run->E_out.as<double>() + run->R, st));
+    PB_CUDA_TRY(cudaEventRecord(run->ev_stop, st));
+    return PB_OK;
+}
+
+pb_status csr_fields(pb_instance* I, const int8_t* d_states, int R, float* d_out, cudaStream_t st)
+{
+    CsrJob j{};
+    j.g = I->csr;
+    j.R = R;
+    j.Rw = (R + 3) / 4;
+    PB_CUDA_TRY(csr_launch_fields(j, d_states, d_out, st));
+    return PB_OK;
+}
+
+}  // namespace pb
+
+using namespace pb;
+
+extern "C" {
+
+int32_t pb_greedy_colouring(int32_t N, int64_t n_edges, const int32_t* eu, const int32_t* ev, int32_t* colour_out)
+{
+    if (N < 1 || n_edges < 0 || !colour_out || (n_edges > 0 && (!eu || !ev))) return -1;
+    for (int64_t e = 0; e < n_edges; ++e)
+        if (eu[e] < 0 || eu[e] >= N || ev[e] < 0 || ev[e] >= N || eu[e] == ev[e]) return -1;
+    return greedy_colouring(N, n_edges, eu, ev, colour_out);
+}
+
+pb_status pb_create_graph_instance(const pb_graph_desc* d, void* stream, pb_instance** out)
+{
+    if (!d || !out) return fail(PB_EINVAL, "null argument");
+    *out = nullptr;
+    if (d->jtype != PB_J_PM1_I8 && d->jtype != PB_J_F32) return fail(PB_EINVAL, "unknown jtype");
+    std::unique_ptr<pb_instance> I(new (std::nothrow) pb_instance());
+    if (!I) return fail(PB_ENOMEM, "host allocation failed");
+    pb_status ps = csr_build(I.get(), d->N, d->n_edges, d->eu, d->ev, d->jtype, d->J, d->h, d->colour,
+                             static_cast<cudaStream_t>(stream));
+    if (ps != PB_OK) return ps;
+    *out = I.release();
+    return PB_OK;
+}
+
+int32_t pb_instance_colours(const pb_instance* inst)
+{
+    if (!inst) return -1;
+    if (inst->topo == PB_TOPO_CSR) return inst->n_colours;
+    return 2;
+}
+
+}  // extern "C"

@@ -1,0 +1,63 @@
+// csr_launch.h -- host/device interface of the p-bit update on general sparse
+// instances (arXiv 2510.23419: the general graph of Eq. 1, update groups of
+// Sec. 1.2.2 from a proper colouring with k >= 2 colours).
+#pragma once
+
+#include "pb_common.h"
+
+namespace pb {
+
+// Device copy of a general instance: each undirected edge (u, v, J) stored
+// from both ends in compressed rows; colour classes listed in ascending index,
+// so a spin's position inside its class list is its class rank (the Philox
+// counter word 0).
+struct CsrDevice {
+    int32_t N, jtype, n_colours, maxdeg, has_h, hmax;
+    const int32_t* rowptr;   // [N + 1]
+    const int32_t* col;      // [2E] neighbour of each half-edge
+    const int8_t* J8;        // [2E] +-1 couplings (PM1)
+    const float* Jf;         // [2E] real couplings (F32)
+    const int8_t* h8;        // [N] or null (PM1)
+    const float* hf;         // [N] or null (F32)
+    const int32_t* cls_off;  // [n_colours + 1]
+    const int32_t* cls_v;    // [N] vertices of class c at cls_off[c] .. cls_off[c+1]-1, ascending
+    const int32_t* colour;   // [N]
+};
+
+// Spin words: 4 replicas per uint32, one byte each, byte = 0 <=> m = +1,
+// 1 <=> m = -1; state [N][Rw], Rw = ceil(R / 4), replica r in byte r % 4 of word r / 4.
+struct CsrJob {
+    CsrDevice g;
+    uint32_t key0, key1;
+    int32_t S, step, nF, fmin;
+    const uint32_t* table;   // PM1: threshold windows of all levels, concatenated
+    const int32_t* win;      // PM1: [levels][3] (lo, width, off)
+    const float* betaf;      // F32: [levels]
+    int32_t R, Rw;
+    uint32_t* spins;         // [N][Rw]
+    uint32_t* best;          // [N][Rw]
+    int32_t nchunk;          // vertex chunks of the energy partials
+    double* part;            // [nchunk][4 Rw] energy partials (PM1: 2E as exact integers)
+    double* E_best;          // [4 Rw]
+    int32_t* best_sweep;     // [4 Rw]
+    int32_t* hit_sweep;      // [4 Rw]
+    uint8_t* improved;       // [4 Rw] + 1 "any" flag at [4 Rw]
+    int32_t has_target;
+    double target;
+};
+
+constexpr int kCsrChunk = 64;  // vertices per energy chunk
+
+cudaError_t csr_launch_init(const CsrJob& job, cudaStream_t st);
+// Update of colour class c in sweep s (Eq. 2, Eq. 3).
+cudaError_t csr_launch_class(const CsrJob& job, int c, int s, cudaStream_t st);
+// Energy partials of the state `m` ([N][Rw] words); exact FP64 per term when exact != 0.
+cudaError_t csr_launch_energy(const CsrJob& job, const uint32_t* m, int exact, cudaStream_t st);
+// Running best after sweep s (init: the initial state), snapshot of improved replicas.
+cudaError_t csr_launch_sweep_end(const CsrJob& job, int s, int init, cudaStream_t st);
+// States [R][N] int8 +-1 and energies (from the partials of the same state) of `m`.
+cudaError_t csr_launch_readout(const CsrJob& job, const uint32_t* m, int8_t* out_pm, double* out_E, cudaStream_t st);
+// Fields F[r][i] = sum_j J_ij m_j + h_i of given +-1 states [R][N] (written as [R][N] float).
+cudaError_t csr_launch_fields(const CsrJob& job, const int8_t* states, float* out, cudaStream_t st);
+
+}  // namespace pb

@@ -109,6 +109,41 @@ uint32_t threshold_u32(double beta, double F)
     return (uint32_t)T;
 }
 
+// Threshold rows (Eq. 2, FP64 on the host), one per beta level, stored as the
+// window of the row outside which T is saturated: T is nondecreasing in F, so
+// every entry below the window is 0 and every entry above it 2^32 - 1, and the
+// window keeps one saturated entry on each side; a lookup clamps the index into
+// the window.  The window edges are found by bisection, so a level costs
+// O(width + log nF) evaluations instead of nF.  win gets (lo, width, off) per level.
+void threshold_windows(const std::vector<double>& betas, int nF, int fmin, std::vector<uint32_t>& tab,
+                       std::vector<int32_t>& win)
+{
+    const int nlev = std::max<int>(1, (int)betas.size());
+    tab.clear();
+    win.assign((size_t)nlev * 3, 0);
+    for (int l = 0; l < nlev; ++l) {
+        const double beta = betas.empty() ? 0.0 : betas[l];
+        auto T = [&](int f) { return threshold_u32(beta, (double)(f + fmin)); };
+        int a = 0, b = nF;  // first index with T > 0
+        while (a < b) {
+            const int m = (a + b) / 2;
+            if (T(m) > 0u) b = m; else a = m + 1;
+        }
+        const int lo = std::max(0, a - 1);
+        a = 0;
+        b = nF;  // first index with T = 2^32 - 1
+        while (a < b) {
+            const int m = (a + b) / 2;
+            if (T(m) == 0xFFFFFFFFu) b = m; else a = m + 1;
+        }
+        const int hi = std::max(lo, std::min(nF - 1, a));
+        win[3 * l] = lo;
+        win[3 * l + 1] = hi - lo + 1;
+        win[3 * l + 2] = (int32_t)tab.size();
+        for (int f = lo; f <= hi; ++f) tab.push_back(T(f));
+    }
+}
+
 }  // namespace pb
 
 namespace pb {
@@ -569,6 +604,10 @@ pb_status pb_anneal_ex(pb_instance* I, const pb_schedule* sc, int32_t R, uint64_
             ps = ea_enqueue_resident(v, st);
         }
         if (ps != PB_OK) return ps;
+    } else if (I->topo == PB_TOPO_CSR) {
+        pb_status ps = csr_setup(run.get(), I, sc, R, seed, opts, st);
+        if (ps == PB_OK) ps = csr_launch(run.get(), st);
+        if (ps != PB_OK) return ps;
     } else {
         int f = 0, wt = 0;
         choose_form(I, R, form, f, wt);
@@ -695,9 +734,12 @@ pb_status pb_fields_ex(pb_instance* I, const int8_t* states, int32_t R, int32_t 
     PB_ALLOC(dm, (size_t)n);
     PB_ALLOC(df, (size_t)n * 4);
     PB_CUDA_TRY(cudaMemcpyAsync(dm.p, states, (size_t)n, cudaMemcpyHostToDevice, st));
-    if (I->topo == PB_TOPO_EA3D)
+    if (I->topo == PB_TOPO_EA3D) {
         PB_CUDA_TRY(ea_launch_fields(I->ea, dm.as<int8_t>(), R, df.as<float>(), st));
-    else {
+    } else if (I->topo == PB_TOPO_CSR) {
+        pb_status ps = csr_fields(I, dm.as<int8_t>(), R, df.as<float>(), st);
+        if (ps != PB_OK) return ps;
+    } else {
         pb_status ps = bq_fields(I, dm.as<int8_t>(), R, form, df.as<float>(), st);
         if (ps != PB_OK) return ps;
     }

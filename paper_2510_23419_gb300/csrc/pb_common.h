@@ -54,6 +54,13 @@ PB_HD U4 philox10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k
     return U4{c0, c1, c2, c3};
 }
 
+// Threshold window of one beta level (+-1 couplings): the row T[F - F_min]
+// restricted to indices [lo, lo + width), stored at table + off; indices
+// outside the window take the value at its nearer edge.
+struct TabWindow {
+    int32_t off, lo, width;
+};
+
 // Stream tags (counter word 3, bits 24..31).
 constexpr uint32_t kTagDecision = 0u;
 constexpr uint32_t kTagInit = 1u;

@@ -8,6 +8,7 @@
 
 #include "biclique_launch.h"
 #include "biclique_tc.h"
+#include "csr_launch.h"
 #include "ea_launch.h"
 #include "pb_common.h"
 
@@ -70,6 +71,10 @@ struct pb_instance {
     // biclique
     pb::BqDevice bq{};
     pb::DevBuf bq_bufs[12];
+    // general sparse instance
+    int n_colours = 0;
+    pb::CsrDevice csr{};
+    pb::DevBuf csr_bufs[10];
 };
 
 namespace pb {
@@ -98,6 +103,8 @@ struct pb_run {
     cudaEvent_t ev_k0 = nullptr, ev_k1 = nullptr;  // around the annealing kernels
     // EA
     pb::EaJob job{};
+    // general sparse instance
+    pb::CsrJob cjob{};
     // biclique
     pb::BqJob bjob{};
     pb::BqTcMaps maps{};
@@ -122,6 +129,8 @@ int sm_count();
 pb_status schedule_levels(const pb_schedule* sc, std::vector<double>& betas, int& step);
 uint32_t threshold_u32(double beta, double F);
 pb_status bq_build(pb_instance* I, const pb_instance_desc* d, cudaStream_t st);
+void threshold_windows(const std::vector<double>& betas, int nF, int fmin, std::vector<uint32_t>& tab,
+                       std::vector<int32_t>& win);
 pb_status bq_anneal(pb_run* run, pb_instance* I, const pb_schedule* sc, int R, uint64_t seed,
                     const pb_anneal_opts* opts, cudaStream_t st);
 pb_status bq_fields(pb_instance* I, const int8_t* d_states, int R, int form, float* d_out, cudaStream_t st);
@@ -136,6 +145,12 @@ int ea_choose_wt(const pb_instance* I, int R, int nF);
 pb_status bq_setup(pb_run* run, pb_instance* I, const pb_schedule* sc, int R, uint64_t seed,
                    const pb_anneal_opts* opts, cudaStream_t st);
 pb_status bq_launch(pb_run* run, cudaStream_t st);
+pb_status csr_build(pb_instance* I, int32_t N, int64_t n_edges, const int32_t* eu, const int32_t* ev, int jtype,
+                    const void* J, const void* h, const int32_t* colour, cudaStream_t st);
+pb_status csr_setup(pb_run* run, pb_instance* I, const pb_schedule* sc, int R, uint64_t seed,
+                    const pb_anneal_opts* opts, cudaStream_t st);
+pb_status csr_launch(pb_run* run, cudaStream_t st);
+pb_status csr_fields(pb_instance* I, const int8_t* d_states, int R, float* d_out, cudaStream_t st);
 pb_status wait_run(pb_run* run, int32_t timeout_ms);
 // Form (and EA tile width) for a job: the caller's choice, else the autotuner's
 // table entry for the job's shape, else the built-in rule.

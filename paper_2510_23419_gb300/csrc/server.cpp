@@ -51,6 +51,11 @@ int64_t footprint_bytes(const pb_instance* I, const pb_schedule* sc, int R, cons
         const int64_t nF = 2 * (6 + I->hmax) + 1;
         return 2 * tiles * N * WT * 4 + 3 * Rpad * 4 + nlev * nF * 4 + out + 4096;
     }
+    if (I->topo == PB_TOPO_CSR) {
+        const int64_t Rw = (R + 3) / 4;
+        const int64_t nF = 2 * (I->maxdeg + I->hmax) + 1;
+        return 2 * N * Rw * 4 + (N + kCsrChunk - 1) / kCsrChunk * 4 * Rw * 8 + 4 * Rw * 20 + nlev * nF * 4 + out + 4096;
+    }
     const int64_t n = I->n;
     const bool tensor = form != PB_FORM_CUDACORE;
     const int64_t tile = tensor ? kBqTcReps : kBqTileReps;

@@ -17,7 +17,7 @@ import numpy as np
 from . import _build
 
 PB_OK, PB_EINVAL, PB_ECOLOUR, PB_ENOMEM, PB_EDEVICE, PB_ETIMEOUT, PB_EBUSY, PB_EUNSUPPORTED = range(8)
-PB_TOPO_EA3D, PB_TOPO_BICLIQUE = 0, 1
+PB_TOPO_EA3D, PB_TOPO_BICLIQUE, PB_TOPO_CSR = 0, 1, 2
 PB_J_PM1_I8, PB_J_F32 = 0, 1
 PB_DIST_PM1, PB_DIST_GAUSS, PB_DIST_UNIF = 0, 1, 2
 PB_SCHED_LINEAR, PB_SCHED_GEOMETRIC, PB_SCHED_EXPLICIT = 0, 1, 2
@@ -36,6 +36,11 @@ class PbError(RuntimeError):
 class pb_instance_desc(ctypes.Structure):
     _fields_ = [("topo", ctypes.c_int32), ("L", ctypes.c_int32), ("n", ctypes.c_int32), ("jtype", ctypes.c_int32),
                 ("J", ctypes.c_void_p), ("h", ctypes.c_void_p), ("colour", ctypes.c_void_p)]
+
+
+class pb_graph_desc(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int32), ("jtype", ctypes.c_int32), ("n_edges", ctypes.c_int64), ("eu", ctypes.c_void_p),
+                ("ev", ctypes.c_void_p), ("J", ctypes.c_void_p), ("h", ctypes.c_void_p), ("colour", ctypes.c_void_p)]
 
 
 class pb_schedule(ctypes.Structure):
@@ -107,6 +112,9 @@ def load():
         "pb_fields": ([P, P, I32, P, I64, P], st),
         "pb_fields_ex": ([P, P, I32, I32, P, I64, P], st),
         "pb_anneal_ea_noalloc": ([I32, P, P, I32, U64, P, P, P, P, P, P], st),
+        "pb_create_graph_instance": ([P, P, P], st),
+        "pb_greedy_colouring": ([I32, I64, P, P, P], I32),
+        "pb_instance_colours": ([P], I32),
         "pb_autotune": ([P, I32, I32, P, P], st),
         "pb_autotune_clear": ([], None),
         "pb_run_footprint": ([P, P, I32, P], I64),
@@ -185,6 +193,37 @@ def pb_create_instance(topo: int, J: np.ndarray, h: np.ndarray | None = None, co
     out = ctypes.c_void_p()
     _check(load().pb_create_instance(ctypes.byref(d), _stream(stream), ctypes.byref(out)))
     return out
+
+
+def pb_create_graph_instance(N: int, eu: np.ndarray, ev: np.ndarray, J: np.ndarray, h: np.ndarray | None = None,
+                             colour: np.ndarray | None = None, stream=None) -> ctypes.c_void_p:
+    """General sparse instance: edges (eu[e], ev[e]) with couplings J[e] (int8 +-1 or float32)."""
+    pm1 = J.dtype == np.int8
+    eu = np.ascontiguousarray(eu, dtype=np.int32)
+    ev = np.ascontiguousarray(ev, dtype=np.int32)
+    J = np.ascontiguousarray(J)
+    hh = None if h is None else np.ascontiguousarray(h, dtype=np.int8 if pm1 else np.float32)
+    cc = None if colour is None else np.ascontiguousarray(colour, dtype=np.int32)
+    d = pb_graph_desc(N=N, jtype=PB_J_PM1_I8 if pm1 else PB_J_F32, n_edges=eu.size, eu=_ptr(eu), ev=_ptr(ev),
+                      J=_ptr(J), h=_ptr(hh), colour=_ptr(cc))
+    out = ctypes.c_void_p()
+    _check(load().pb_create_graph_instance(ctypes.byref(d), _stream(stream), ctypes.byref(out)))
+    return out
+
+
+def pb_greedy_colouring(N: int, eu: np.ndarray, ev: np.ndarray):
+    """(colour[N], number of colours); host only."""
+    eu = np.ascontiguousarray(eu, dtype=np.int32)
+    ev = np.ascontiguousarray(ev, dtype=np.int32)
+    col = np.empty(N, np.int32)
+    k = int(load().pb_greedy_colouring(N, eu.size, _ptr(eu), _ptr(ev), _ptr(col)))
+    if k < 0:
+        raise PbError(PB_EINVAL, "invalid graph")
+    return col, k
+
+
+def pb_instance_colours(inst) -> int:
+    return int(load().pb_instance_colours(inst))
 
 
 def pb_instance_destroy(inst):

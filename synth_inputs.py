@@ -42,3 +42,54 @@ def real_fields(N: int, scale: float, seed: int) -> np.ndarray:
 
 def states(R: int, N: int, seed: int) -> np.ndarray:
     return np.random.default_rng(seed).choice(np.array([-1, 1], np.int8), size=(R, N))
+
+
+# ---------------------------------------------------------------- graphs
+# Edge lists (eu, ev) of the sparse test and bench topologies; each undirected
+# edge once.  Structure only: no coupling values, no colouring.
+
+def graph_periodic_cube(L: int):
+    """Periodic L^3 lattice, 6 neighbours; odd L is not bipartite (3 colours)."""
+    idx = np.arange(L ** 3).reshape(L, L, L)  # [z][y][x]
+    eu, ev = [], []
+    for ax in (2, 1, 0):
+        eu.append(idx.reshape(-1))
+        ev.append(np.roll(idx, -1, axis=ax).reshape(-1))
+    return np.concatenate(eu).astype(np.int32), np.concatenate(ev).astype(np.int32)
+
+
+def graph_king(Lx: int, Ly: int):
+    """Open 2D king's graph (8 neighbours), chromatic number 4."""
+    eu, ev = [], []
+    for y in range(Ly):
+        for x in range(Lx):
+            i = y * Lx + x
+            for dx, dy in ((1, 0), (0, 1), (1, 1), (-1, 1)):
+                X, Y = x + dx, y + dy
+                if 0 <= X < Lx and 0 <= Y < Ly:
+                    eu.append(i)
+                    ev.append(Y * Lx + X)
+    return np.array(eu, np.int32), np.array(ev, np.int32)
+
+
+def graph_random(N: int, n_edges: int, seed: int):
+    """Random simple graph: n_edges distinct pairs, no self-loops."""
+    rng = np.random.default_rng(seed)
+    seen, eu, ev = set(), [], []
+    while len(eu) < n_edges:
+        u, v = (int(x) for x in rng.integers(0, N, size=2))
+        if u == v or (min(u, v), max(u, v)) in seen:
+            continue
+        seen.add((min(u, v), max(u, v)))
+        eu.append(u)
+        ev.append(v)
+    return np.array(eu, np.int32), np.array(ev, np.int32)
+
+
+def edge_couplings(n_edges: int, law: str, seed: int) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    if law == "pm1":
+        return np.where(rng.random(n_edges) < 0.5, 1, -1).astype(np.int8)
+    if law == "gauss":
+        return rng.normal(size=n_edges).astype(np.float32)
+    return rng.uniform(-1.0, 1.0, size=n_edges).astype(np.float32)

@@ -78,3 +78,44 @@ def test_single_pbit_eq2(orc, beta, h):
     phat = (out["final_state"][:, 0] > 0).mean()
     p = 0.5 + 0.5 * np.tanh(beta * h)
     assert abs(phat - p) < 4.5 * np.sqrt(p * (1 - p) / R)
+
+
+@pytest.mark.parametrize("graph", ["odd_cycle_chords_3col", "king_3x3_4col"])
+def test_full_state_law_k_colours(orc, graph):
+    """More than two update groups (Sec. 1.2.2 with a k-colouring): classes updated
+    in colour order still sample the Boltzmann law."""
+    rng = np.random.default_rng(202)
+    beta, R, burn = 0.7, 40000, 60
+    if graph.startswith("odd"):
+        N = 9
+        eu = list(range(9)) + [0, 2, 4]
+        ev = [(i + 1) % 9 for i in range(9)] + [3, 5, 7]
+        col = np.array([0, 1, 0, 1, 0, 1, 0, 1, 2], np.int32)  # 9-cycle needs a third colour
+    else:
+        N = 9
+        eu, ev = [], []
+        for y in range(3):
+            for x in range(3):
+                for dx, dy in ((1, 0), (0, 1), (1, 1), (-1, 1)):
+                    X, Y = x + dx, y + dy
+                    if 0 <= X < 3 and 0 <= Y < 3:
+                        eu.append(y * 3 + x)
+                        ev.append(Y * 3 + X)
+        col = np.array([(x % 2) + 2 * (y % 2) for y in range(3) for x in range(3)], np.int32)
+    eu, ev = np.array(eu, np.int32), np.array(ev, np.int32)
+    assert orc.count_monochrome(eu, ev, col) == 0 and col.max() + 1 > 2
+    J = rng.normal(size=eu.size)
+    h = 0.5 * rng.normal(size=N)
+    E = orc.brute_force(N, eu, ev, J, h)
+    p = np.exp(-beta * (E - E.min())); p /= p.sum()
+    out = orc.anneal(eu, ev, J, h, col, np.full(burn, beta), R, seed=91)
+    idx = _state_index(out["final_state"])
+    counts = np.bincount(idx, minlength=1 << N).astype(float)
+    assert _chi2_p(counts, p) > 1e-4
+    assert np.allclose(out["final_E"], E[idx])
+
+
+def test_invalid_colouring_rejected(orc):
+    eu, ev = np.array([0, 1], np.int32), np.array([1, 2], np.int32)
+    with pytest.raises(ValueError):
+        orc.anneal(eu, ev, np.ones(2), None, np.array([0, 0, 1], np.int32), np.full(3, 0.5), 2, seed=1)
