@@ -203,6 +203,35 @@ pb_status pb_anneal_batch(int32_t count, pb_instance* const* insts, const pb_sch
                           const int32_t* replicas, const uint64_t* seeds, const pb_anneal_opts* opts,
                           void* stream, pb_run** outs);
 
+/* Benchmarking protocol (Sec. 4.1.3, Algorithm 1): the smallest iteration
+ * budget i in i_start, i_start + i_step, ... (<= i_max) at which `trials`
+ * independent anneals, each of i iterations (one iteration = one colour-class
+ * step, so ceil(i / k) sweeps for k classes) with beta linear from beta_i to
+ * beta_f, have at most round(trials (1 - p_succ)) fails, a fail being a best
+ * energy above theta = p * ground (ground < 0).  The trials of budget i are the
+ * replicas of one anneal seeded seed + i; `budgets_per_launch` budgets (0 = 8)
+ * run as one pb_anneal_batch.  Returns the same i as the paper's sequential loop
+ * with early exit for the same trial outcomes; i_min = -1 if none passes.
+ * Synchronous. */
+typedef struct pb_imin_opts {
+    double ground;
+    double p;
+    double p_succ;
+    int32_t i_start, i_step, i_max;  /* i_max = 0: i_start + 1000 i_step */
+    int32_t trials;
+    double beta_i, beta_f;
+    int32_t budgets_per_launch;
+    int32_t form;                    /* pb_form of the anneals */
+    uint64_t seed;
+} pb_imin_opts;
+typedef struct pb_imin_result {
+    int32_t i_min;          /* -1: no budget passed */
+    int32_t fails;          /* fails at i_min */
+    int32_t budgets_tried;  /* budgets whose verdict was read, in order */
+    int32_t launches;       /* batched launches */
+} pb_imin_result;
+pb_status pb_find_imin(pb_instance* inst, const pb_imin_opts* opts, void* stream, pb_imin_result* out);
+
 /* Autotuner.  Times each candidate launch choice for `inst` with `replicas`
  * replicas on a short probe anneal of `probe_sweeps` sweeps (linear beta
  * 0.1 -> 3.0) on `stream`: EA resident form with every valid tile width (replica

@@ -250,3 +250,32 @@ def anneal_ea(L: int, J, h, betas, R: int, seed: int, **kw) -> dict:
 def anneal_biclique(n: int, J, h, betas, R: int, seed: int, **kw) -> dict:
     eu, ev, col = biclique_graph(n)
     return anneal(eu, ev, np.asarray(J, np.float64).reshape(-1), h, col, betas, R, seed, 2, **kw)
+
+
+# ------------------------------------------------ benchmarking protocol
+def find_imin(eu, ev, J, h, colour, ground: float, p: float, p_succ: float, i_start: int, i_step: int,
+              trials: int, beta_i: float, beta_f: float, i_max: int, seed: int, n_colours: int | None = None):
+    """Algorithm 1 (Sec. 4.1.3) as printed: budgets i = i_start, i_start + i_step, ...; at each, run the
+    trials one after another (trial j = replica j of seed + i), count fails (best energy > p G) and stop
+    the budget early once the fails exceed m_max = round(t (1 - p_succ)) (half up); return the first budget that
+    passes (None if none up to i_max).  One iteration = one colour-class step: ceil(i / k) sweeps with
+    a linear schedule (both ends included)."""
+    colour = np.ascontiguousarray(colour, np.int32)
+    k = int(colour.max()) + 1 if n_colours is None else n_colours
+    theta = p * ground
+    m_max = int(np.floor(trials * (1.0 - p_succ) + 0.5))  # round half up
+    i = i_start
+    while i <= i_max:
+        S = (i + k - 1) // k
+        betas = schedule(SCHED_LINEAR, beta_i, beta_f, S)
+        m = 0
+        for j in range(trials):
+            v = anneal(eu, ev, J, h, colour, betas, 1, seed + i, n_colours=k, r_first=j)["best_E"][0]
+            if v > theta:
+                m += 1
+                if m > m_max:
+                    break
+        if m <= m_max:
+            return i
+        i += i_step
+    return None

@@ -43,6 +43,18 @@ class pb_graph_desc(ctypes.Structure):
                 ("ev", ctypes.c_void_p), ("J", ctypes.c_void_p), ("h", ctypes.c_void_p), ("colour", ctypes.c_void_p)]
 
 
+class pb_imin_opts(ctypes.Structure):
+    _fields_ = [("ground", ctypes.c_double), ("p", ctypes.c_double), ("p_succ", ctypes.c_double),
+                ("i_start", ctypes.c_int32), ("i_step", ctypes.c_int32), ("i_max", ctypes.c_int32),
+                ("trials", ctypes.c_int32), ("beta_i", ctypes.c_double), ("beta_f", ctypes.c_double),
+                ("budgets_per_launch", ctypes.c_int32), ("form", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+
+
+class pb_imin_result(ctypes.Structure):
+    _fields_ = [("i_min", ctypes.c_int32), ("fails", ctypes.c_int32), ("budgets_tried", ctypes.c_int32),
+                ("launches", ctypes.c_int32)]
+
+
 class pb_schedule(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("n_sweeps", ctypes.c_int32), ("step_duration", ctypes.c_int32),
                 ("reserved", ctypes.c_int32), ("beta0", ctypes.c_double), ("beta1", ctypes.c_double),
@@ -115,6 +127,7 @@ def load():
         "pb_create_graph_instance": ([P, P, P], st),
         "pb_greedy_colouring": ([I32, I64, P, P, P], I32),
         "pb_instance_colours": ([P], I32),
+        "pb_find_imin": ([P, P, P, P], st),
         "pb_autotune": ([P, I32, I32, P, P], st),
         "pb_autotune_clear": ([], None),
         "pb_run_footprint": ([P, P, I32, P], I64),
@@ -350,6 +363,17 @@ def pb_anneal_ea_noalloc(L: int, J_dev: int, sched: pb_schedule, replicas: int, 
                                        ctypes.c_void_p(best_E_dev), ctypes.c_void_p(best_sweep_dev),
                                        ctypes.c_void_p(best_states_dev), ctypes.c_void_p(final_E_dev),
                                        ctypes.c_void_p(final_states_dev), _stream(stream)))
+
+
+# ------------------------------------------------------- Algorithm 1 driver
+def pb_find_imin(inst, ground: float, p: float, p_succ: float, i_start: int, i_step: int, trials: int,
+                 beta_i: float = 0.35, beta_f: float = 3.5, i_max: int = 0, budgets_per_launch: int = 0,
+                 form: int = PB_FORM_AUTO, seed: int = 0, stream=None) -> pb_imin_result:
+    o = pb_imin_opts(ground=ground, p=p, p_succ=p_succ, i_start=i_start, i_step=i_step, i_max=i_max, trials=trials,
+                     beta_i=beta_i, beta_f=beta_f, budgets_per_launch=budgets_per_launch, form=form, seed=seed)
+    r = pb_imin_result()
+    _check(load().pb_find_imin(inst, ctypes.byref(o), _stream(stream), ctypes.byref(r)))
+    return r
 
 
 # ------------------------------------------------------- autotuner, server
