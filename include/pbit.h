@@ -203,6 +203,29 @@ pb_status pb_anneal_batch(int32_t count, pb_instance* const* insts, const pb_sch
                           const int32_t* replicas, const uint64_t* seeds, const pb_anneal_opts* opts,
                           void* stream, pb_run** outs);
 
+/* Sparsified biclique (host only; Sec. 5.3 outlook, construction of this
+ * library): vertex v of K_{n,n} (left i = v, right j = v - n) becomes a path of
+ * copies joined by ferromagnetic copy edges of strength copy_strength (for
+ * PB_J_PM1_I8 as that many unit edges); biclique edge (i, j) of parity
+ * (i + j) mod 2 joins a copy of i and a copy of j of that slot, each copy
+ * carrying at most per_copy (1..4) edges, so no copy has more than
+ * per_copy + 2 <= 6 neighbours.  colour[] is a proper 2-colouring (left copy:
+ * slot, right copy: 1 - slot) and copy_of[] maps each copy to v.  J is the
+ * biclique's [n][n] row-major coupling matrix.  With null output arrays only
+ * *N_out is set and the number of edges returned (size query); otherwise fills
+ * eu, ev, J_out (int8 or float), colour, copy_of and returns the number of
+ * edges, or -1 on invalid arguments or too small capacities.  When all copies
+ * of every vertex agree with a biclique state m, the copy graph's energy is
+ * E(m) - copy_strength * (N_out - 2n). */
+int64_t pb_sparsify_biclique(int32_t n, int32_t jtype, const void* J, int32_t per_copy, int32_t copy_strength,
+                             int32_t* N_out, int32_t* eu, int32_t* ev, void* J_out, int32_t* colour,
+                             int32_t* copy_of, int64_t edge_capacity, int32_t vertex_capacity);
+/* Projection of copy-graph states [R][N_sparse] onto the original vertices
+ * [R][n_orig]: the majority of each vertex's copies (a tie takes copy 0).
+ * Host only; returns 0, or -1 on invalid arguments. */
+int32_t pb_sparse_project(int32_t N_sparse, const int32_t* copy_of, int32_t n_orig, int32_t R, const int8_t* states,
+                          int8_t* out);
+
 /* Benchmarking protocol (Sec. 4.1.3, Algorithm 1): the smallest iteration
  * budget i in i_start, i_start + i_step, ... (<= i_max) at which `trials`
  * independent anneals, each of i iterations (one iteration = one colour-class

@@ -128,6 +128,8 @@ def load():
         "pb_greedy_colouring": ([I32, I64, P, P, P], I32),
         "pb_instance_colours": ([P], I32),
         "pb_find_imin": ([P, P, P, P], st),
+        "pb_sparsify_biclique": ([I32, I32, P, I32, I32, P, P, P, P, P, P, I64, I32], I64),
+        "pb_sparse_project": ([I32, P, I32, I32, P, P], I32),
         "pb_autotune": ([P, I32, I32, P, P], st),
         "pb_autotune_clear": ([], None),
         "pb_run_footprint": ([P, P, I32, P], I64),
@@ -363,6 +365,41 @@ def pb_anneal_ea_noalloc(L: int, J_dev: int, sched: pb_schedule, replicas: int, 
                                        ctypes.c_void_p(best_E_dev), ctypes.c_void_p(best_sweep_dev),
                                        ctypes.c_void_p(best_states_dev), ctypes.c_void_p(final_E_dev),
                                        ctypes.c_void_p(final_states_dev), _stream(stream)))
+
+
+# ------------------------------------------------------- sparsified biclique
+def pb_sparsify_biclique(J: np.ndarray, per_copy: int = 4, copy_strength: int = 2):
+    """Copy graph of the biclique with couplings J [n][n] (int8 or float32):
+    dict(N, eu, ev, J, colour, copy_of)."""
+    J = np.ascontiguousarray(J)
+    n = J.shape[0]
+    jt = PB_J_PM1_I8 if J.dtype == np.int8 else PB_J_F32
+    N = ctypes.c_int32()
+    lib = load()
+    E = int(lib.pb_sparsify_biclique(n, jt, _ptr(J), per_copy, copy_strength, ctypes.byref(N), None, None, None, None,
+                                     None, 0, 0))
+    if E < 0:
+        raise PbError(PB_EINVAL, "invalid sparsification arguments")
+    eu = np.empty(E, np.int32)
+    ev = np.empty(E, np.int32)
+    Jo = np.empty(E, np.int8 if jt == PB_J_PM1_I8 else np.float32)
+    col = np.empty(N.value, np.int32)
+    cof = np.empty(N.value, np.int32)
+    got = int(lib.pb_sparsify_biclique(n, jt, _ptr(J), per_copy, copy_strength, ctypes.byref(N), _ptr(eu), _ptr(ev),
+                                       _ptr(Jo), _ptr(col), _ptr(cof), E, N.value))
+    if got != E:
+        raise PbError(PB_EINVAL, "sparsification failed")
+    return dict(N=N.value, eu=eu, ev=ev, J=Jo, colour=col, copy_of=cof)
+
+
+def pb_sparse_project(copy_of: np.ndarray, n_orig: int, states: np.ndarray) -> np.ndarray:
+    states = np.ascontiguousarray(states, dtype=np.int8)
+    R, Ns = states.shape
+    out = np.empty((R, n_orig), np.int8)
+    cof = np.ascontiguousarray(copy_of, dtype=np.int32)
+    if load().pb_sparse_project(Ns, _ptr(cof), n_orig, R, _ptr(states), _ptr(out)) != 0:
+        raise PbError(PB_EINVAL, "invalid projection arguments")
+    return out
 
 
 # ------------------------------------------------------- Algorithm 1 driver

@@ -152,3 +152,24 @@ def test_csr_in_batch_equals_alone(pb):
     finally:
         pb.pb_instance_destroy(inst)
         pb.pb_instance_destroy(binst)
+
+
+@pytest.mark.parametrize("n,cs", [(24, 2), (17, 3)])
+def test_sparsified_biclique_bit_exact(pb, orc, n, cs):
+    """The copy graph of a +-J biclique (degree <= 6, two update groups) on the CSR
+    path, with the construction's own colouring, against the oracle."""
+    J = pb.pb_generate_biclique(n, pb.PB_DIST_PM1, 50 + n)
+    sp = pb.pb_sparsify_biclique(J, 4, cs)
+    R, S = 20, 30
+    sc = pb.make_schedule(pb.PB_SCHED_LINEAR, S, 0.35, 3.5)
+    g, k = _run(pb, sp["N"], sp["eu"], sp["ev"], sp["J"], None, sp["colour"], sc, R, 11)
+    assert k == 2
+    o = orc.anneal(sp["eu"], sp["ev"], sp["J"].astype(np.float64), None, sp["colour"],
+                   orc.schedule(orc.SCHED_LINEAR, 0.35, 3.5, S), R, 11, n_colours=2)
+    for key in ("final_state", "best_state", "final_E", "best_E", "best_sweep"):
+        assert np.array_equal(g[key], o[key]), key
+    # projected best states are biclique states; their energies from the oracle
+    proj = pb.pb_sparse_project(sp["copy_of"], 2 * n, g["best_state"])
+    beu, bev, _ = orc.biclique_graph(n)
+    e = [orc.energy(beu, bev, J.astype(np.float64).reshape(-1), None, proj[r]) for r in range(R)]
+    assert min(e) >= -n * n
