@@ -71,7 +71,7 @@ def test_pm1_bit_exact(pb, orc, case):
     if greedy:
         col, k = pb.pb_greedy_colouring(N, eu, ev)
     else:
-        # a different proper colouring: classes by index mod 5 then repaired greedily
+        # a different proper colouring: the greedy classes in reverse order
         col, k = pb.pb_greedy_colouring(N, eu, ev)
         col = (k - 1 - col).astype(np.int32)  # reversed class order
     g, kg = _run(pb, N, eu, ev, J, h, None if greedy else col, pb.make_schedule(kind, S, b0, b1), R, seed)
