@@ -80,6 +80,8 @@ def _load():
             lib.orc_anneal.argtypes = [i32, i64, P, P, P, P, P, i32, P, i32, i32, i32, u64,
                                        P, P, P, P, P, P, P]
             lib.orc_anneal.restype = ctypes.c_int
+            lib.orc_pt.argtypes = [i32, i64, P, P, P, P, P, i32, P, i32, i32, i32, u64, P, P, P, P, P, P, P]
+            lib.orc_pt.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -279,3 +281,32 @@ def find_imin(eu, ev, J, h, colour, ground: float, p: float, p_succ: float, i_st
             return i
         i += i_step
     return None
+
+
+# ------------------------------------------------------- parallel tempering
+def anneal_pt(eu, ev, J, h, colour, ladder, S: int, R: int, seed: int, n_colours: int | None = None) -> dict:
+    """Parallel tempering (see the C file): per slot g = k R + r results, the final temperature index of
+    every slot and the accepted exchanges per temperature pair."""
+    colour = np.ascontiguousarray(colour, np.int32)
+    N = colour.size
+    eu = np.ascontiguousarray(eu, np.int32)
+    ev = np.ascontiguousarray(ev, np.int32)
+    J = np.ascontiguousarray(J, np.float64).reshape(-1)
+    hh = _h(h, N)
+    ladder = np.ascontiguousarray(ladder, np.float64)
+    M = ladder.size
+    if n_colours is None:
+        n_colours = int(colour.max()) + 1
+    G = M * R
+    out = dict(final_E=np.empty(G), best_E=np.empty(G), best_sweep=np.empty(G, np.int32),
+               final_state=np.empty((G, N), np.int8), best_state=np.empty((G, N), np.int8),
+               slot_temp=np.empty(G, np.int32), n_accept=np.zeros(max(M - 1, 1), np.int64))
+    rc = _load().orc_pt(N, eu.size, _p(eu), _p(ev), _p(J), _p(hh), _p(colour), n_colours, _p(ladder), M, S, R, seed,
+                        _p(out["final_E"]), _p(out["best_E"]), _p(out["best_sweep"]), _p(out["final_state"]),
+                        _p(out["best_state"]), _p(out["slot_temp"]), _p(out["n_accept"]))
+    if rc == -2:
+        raise ValueError("colouring has an edge inside a colour class")
+    if rc != 0:
+        raise ValueError(f"oracle parallel tempering failed ({rc})")
+    out["n_accept"] = out["n_accept"][: M - 1]
+    return out

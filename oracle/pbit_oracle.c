@@ -373,3 +373,131 @@ int orc_anneal(int32_t N, int64_t n_edges, const int32_t* eu, const int32_t* ev,
     free(deg); free(adj); free(adjJ); free(fill); free(rank); free(m);
     return 0;
 }
+
+/* ------------------------------------------------------------------------
+ * Parallel tempering (replica exchange; Hukushima & Nemoto, J. Phys. Soc. Jpn.
+ * 65, 1604 (1996)), named by the paper as a better PC solving method
+ * (Sec. 6.1).  Written from the standard definition:
+ *   - M inverse temperatures ladder[0] < ... < ladder[M-1] and R independent
+ *     chains; chain r has M slots g = k R + r (k = 0..M-1), slot g starts at
+ *     temperature k with its own initial state (tag 1, replica index g).
+ *   - Sweep s: every slot updates every colour class in order with the beta of
+ *     its current temperature (decision words tag 0, replica index g).
+ *   - After the sweep, energies are taken (and each slot's running best kept as
+ *     in orc_anneal); then, for every chain r and every temperature pair
+ *     (t, t+1) with t = s mod 2, t + 2, ..., the slots a (temperature t) and b
+ *     (temperature t+1) exchange temperatures with probability
+ *     min(1, exp((beta_{t+1} - beta_t) (E_b - E_a))): accepted iff that
+ *     exponent x >= 0 or w < floor(exp(x) 2^32), w the word of counter
+ *     (t, s, r >> 2, 3 << 24), index r & 3.
+ * Outputs are per slot (arrays of M R) plus the final temperature of every
+ * slot and the accepted exchanges per pair.
+ * ------------------------------------------------------------------------ */
+#define ORC_TAG_EXCHANGE 3u
+
+int orc_pt(int32_t N, int64_t n_edges, const int32_t* eu, const int32_t* ev, const double* J, const double* h,
+           const int32_t* colour, int32_t n_colours, const double* ladder, int32_t M, int32_t S, int32_t R,
+           uint64_t seed, double* final_E, double* best_E, int32_t* best_sweep, int8_t* final_state,
+           int8_t* best_state, int32_t* slot_temp, int64_t* n_accept)
+{
+    if (N < 1 || M < 1 || R < 1 || S < 0 || n_colours < 1 || n_colours > 255) return -1;
+    for (int32_t k = 0; k + 1 < M; ++k)
+        if (!(ladder[k] < ladder[k + 1])) return -1;
+    for (int32_t i = 0; i < N; ++i)
+        if (colour[i] < 0 || colour[i] >= n_colours) return -1;
+    if (orc_count_monochrome(n_edges, eu, ev, colour) != 0) return -2;
+
+    const int32_t G = M * R;
+    int64_t* deg = (int64_t*)calloc((size_t)N + 1, sizeof(int64_t));
+    int32_t* adj = (int32_t*)malloc((size_t)(2 * n_edges + 1) * sizeof(int32_t));
+    double* adjJ = (double*)malloc((size_t)(2 * n_edges + 1) * sizeof(double));
+    int64_t* fill = (int64_t*)calloc((size_t)N, sizeof(int64_t));
+    uint32_t* rank = (uint32_t*)malloc((size_t)N * sizeof(uint32_t));
+    int8_t* m = (int8_t*)malloc((size_t)G * N);
+    double* E = (double*)malloc((size_t)G * sizeof(double));
+    int32_t* temp = (int32_t*)malloc((size_t)G * sizeof(int32_t));
+    int32_t* slot_of = (int32_t*)malloc((size_t)G * sizeof(int32_t)); /* [t][r] -> slot */
+    if (!deg || !adj || !adjJ || !fill || !rank || !m || !E || !temp || !slot_of) {
+        free(deg); free(adj); free(adjJ); free(fill); free(rank); free(m); free(E); free(temp); free(slot_of);
+        return -3;
+    }
+    for (int64_t e = 0; e < n_edges; ++e) {
+        deg[eu[e] + 1]++;
+        deg[ev[e] + 1]++;
+    }
+    for (int32_t i = 0; i < N; ++i) deg[i + 1] += deg[i];
+    for (int64_t e = 0; e < n_edges; ++e) {
+        int32_t u = eu[e], v = ev[e];
+        adj[deg[u] + fill[u]] = v; adjJ[deg[u] + fill[u]] = J[e]; fill[u]++;
+        adj[deg[v] + fill[v]] = u; adjJ[deg[v] + fill[v]] = J[e]; fill[v]++;
+    }
+    for (int32_t c = 0; c < n_colours; ++c) {
+        uint32_t k = 0;
+        for (int32_t i = 0; i < N; ++i)
+            if (colour[i] == c) rank[i] = k++;
+    }
+    if (n_accept)
+        for (int32_t t = 0; t + 1 < M; ++t) n_accept[t] = 0;
+
+    /* initial states, energies, bests */
+    for (int32_t g = 0; g < G; ++g) {
+        int8_t* mg = m + (int64_t)g * N;
+        for (int32_t i = 0; i < N; ++i) {
+            uint32_t w = orc_rand_word(seed, rank[i], 0u, (uint32_t)(g >> 2), (ORC_TAG_INIT << 24) | (uint32_t)colour[i],
+                                       g & 3);
+            mg[i] = (w < 0x80000000u) ? 1 : -1;
+        }
+        E[g] = orc_energy(N, n_edges, eu, ev, J, h, mg);
+        temp[g] = g / R;
+        slot_of[g] = g; /* temperature g / R of chain g % R sits in slot g */
+        best_E[g] = E[g];
+        best_sweep[g] = -1;
+        if (best_state) memcpy(best_state + (int64_t)g * N, mg, (size_t)N);
+    }
+    for (int32_t s = 0; s < S; ++s) {
+        for (int32_t g = 0; g < G; ++g) {
+            int8_t* mg = m + (int64_t)g * N;
+            const double beta = ladder[temp[g]];
+            for (int32_t c = 0; c < n_colours; ++c) {
+                for (int32_t i = 0; i < N; ++i) {
+                    if (colour[i] != c) continue;
+                    double F = h ? h[i] : 0.0;
+                    for (int64_t a = deg[i]; a < deg[i + 1]; ++a) F += adjJ[a] * (double)mg[adj[a]];
+                    uint32_t w = orc_rand_word(seed, rank[i], (uint32_t)s, (uint32_t)(g >> 2),
+                                               (ORC_TAG_DECISION << 24) | (uint32_t)c, g & 3);
+                    mg[i] = (w < orc_threshold(beta, F)) ? 1 : -1;
+                }
+            }
+            E[g] = orc_energy(N, n_edges, eu, ev, J, h, mg);
+            if (E[g] < best_E[g]) {
+                best_E[g] = E[g];
+                best_sweep[g] = s;
+                if (best_state) memcpy(best_state + (int64_t)g * N, mg, (size_t)N);
+            }
+        }
+        for (int32_t r = 0; r < R; ++r) {
+            for (int32_t t = s & 1; t + 1 < M; t += 2) {
+                const int32_t a = slot_of[t * R + r], b = slot_of[(t + 1) * R + r];
+                const double x = (ladder[t + 1] - ladder[t]) * (E[b] - E[a]);
+                const uint32_t w = orc_rand_word(seed, (uint32_t)t, (uint32_t)s, (uint32_t)(r >> 2), ORC_TAG_EXCHANGE << 24,
+                                                 r & 3);
+                int accept = x >= 0.0;
+                if (!accept) accept = (double)w < floor(exp(x) * ORC_TWO_POW_32);
+                if (accept) {
+                    temp[a] = t + 1;
+                    temp[b] = t;
+                    slot_of[t * R + r] = b;
+                    slot_of[(t + 1) * R + r] = a;
+                    if (n_accept) n_accept[t]++;
+                }
+            }
+        }
+    }
+    for (int32_t g = 0; g < G; ++g) {
+        if (final_E) final_E[g] = E[g];
+        if (final_state) memcpy(final_state + (int64_t)g * N, m + (int64_t)g * N, (size_t)N);
+        if (slot_temp) slot_temp[g] = temp[g];
+    }
+    free(deg); free(adj); free(adjJ); free(fill); free(rank); free(m); free(E); free(temp); free(slot_of);
+    return 0;
+}
