@@ -177,6 +177,24 @@ int32_t pb_greedy_colouring(int32_t N, int64_t n_edges, const int32_t* eu, const
 /* Number of colour classes of an instance (2 for EA and biclique), or -1. */
 int32_t pb_instance_colours(const pb_instance* inst);
 
+/* Parallel tempering (replica exchange, Hukushima & Nemoto 1996; Sec. 6.1 names
+ * it as a PC solving method) on a general sparse instance: M inverse
+ * temperatures ladder[0] < ... < ladder[M-1] and `chains` independent chains
+ * give M * chains slots; slot g = k * chains + r starts at temperature k with
+ * its own random stream (replica index g).  Every sweep each slot updates all
+ * colour classes at its temperature's beta; then, in every chain, the slots
+ * holding temperatures t and t + 1 (t = sweep mod 2, t + 2, ...) exchange
+ * temperatures with probability min(1, exp((beta_{t+1} - beta_t)(E_b - E_a))),
+ * decided by the Philox word of counter (t, sweep, r >> 2, 3 << 24), index
+ * r & 3, against floor(exp(.) 2^32) (FP64 table for +-1 instances: bit-exact).
+ * The run's replicas are the slots: pb_energy / pb_best_states etc. return
+ * M * chains entries; pb_pt_state gives each slot's final temperature and the
+ * accepted exchanges per pair.  Errors: PB_EUNSUPPORTED (not a graph instance),
+ * PB_EINVAL (ladder not increasing, M > 255, spacing below ~5e-6 for +-1). */
+pb_status pb_anneal_pt(pb_instance* inst, const double* ladder, int32_t M, int32_t n_sweeps, int32_t chains,
+                       uint64_t seed, void* stream, pb_run** out);
+pb_status pb_pt_state(pb_run* run, int32_t* slot_temp, int64_t* n_accept);
+
 /* Start an anneal of `replicas` independent replicas (Sec. 1.3.1) on `stream`.
  * Asynchronous: returns once the work is queued.  `opts` may be NULL (AUTO form,
  * no target).  The instance must outlive the run.  Errors: PB_EINVAL (schedule,

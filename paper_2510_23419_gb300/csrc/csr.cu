@@ -78,13 +78,16 @@ template <int JT>
 __global__ void __launch_bounds__(256) csr_class_kernel(CsrJob job, int c, int s)
 {
     const int off = job.g.cls_off[c], ncls = job.g.cls_off[c + 1] - off;
-    const int lev = s / job.step;
+    // annealing: one level for all replicas; tempering: each replica's own temperature
     TabWindow win{0, 0, 1};
     float cexp = 0.0f;
-    if (JT == PB_J_PM1_I8)
-        win = TabWindow{job.win[3 * lev + 2], job.win[3 * lev], job.win[3 * lev + 1]};
-    else
-        cexp = f32_cexp(job.betaf[lev]);
+    if (!job.temp) {
+        const int lev = s / job.step;
+        if (JT == PB_J_PM1_I8)
+            win = TabWindow{job.win[3 * lev + 2], job.win[3 * lev], job.win[3 * lev + 1]};
+        else
+            cexp = f32_cexp(job.betaf[lev]);
+    }
     const long long total = (long long)ncls * job.Rw;
     for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (long long)gridDim.x * blockDim.x) {
@@ -98,18 +101,25 @@ __global__ void __launch_bounds__(256) csr_class_kernel(CsrJob job, int c, int s
             int G[4];
             pm1_row(job, job.spins, i, q, G);
             const int h = job.g.h8 ? job.g.h8[i] : 0;
-            const uint32_t* trow = job.table + win.off;
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
-                const int f = min(max(G[b] + h - job.fmin, win.lo), win.lo + win.width - 1) - win.lo;
-                w |= decide_bit(ws[b], trow[f]) << (8 * b);
+                TabWindow wb = win;
+                if (job.temp) {
+                    const int l = job.temp[4 * q + b];
+                    wb = TabWindow{job.win[3 * l + 2], job.win[3 * l], job.win[3 * l + 1]};
+                }
+                const int f = min(max(G[b] + h - job.fmin, wb.lo), wb.lo + wb.width - 1) - wb.lo;
+                w |= decide_bit(ws[b], job.table[wb.off + f]) << (8 * b);
             }
         } else {
             float G[4];
             f32_row(job, job.spins, i, q, G);
             const float h = job.g.hf ? job.g.hf[i] : 0.0f;
 #pragma unroll
-            for (int b = 0; b < 4; ++b) w |= decide_f32(ws[b], G[b] + h, cexp) << (8 * b);
+            for (int b = 0; b < 4; ++b) {
+                const float cb = job.temp ? f32_cexp(job.betaf[job.temp[4 * q + b]]) : cexp;
+                w |= decide_f32(ws[b], G[b] + h, cb) << (8 * b);
+            }
         }
         job.spins[(size_t)i * job.Rw + q] = w;
     }
@@ -168,6 +178,7 @@ __global__ void __launch_bounds__(256) csr_sweep_end_kernel(CsrJob job, int s, i
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= 4 * job.Rw) return;
     const double E = csr_energy_of(job, r);
+    if (job.E_cur) job.E_cur[r] = E;
     bool imp;
     if (init) {
         imp = true;
@@ -196,6 +207,44 @@ __global__ void __launch_bounds__(256) csr_snapshot_kernel(CsrJob job)
         if (!f) continue;
         const uint32_t mask = f * 0xFFu;  // 0x01 -> 0xFF per byte
         job.best[idx] = (job.spins[idx] & mask) | (job.best[idx] & ~mask);
+    }
+}
+
+// Replica exchange after sweep s (tempering): one thread per chain, pairs of
+// the sweep's parity in increasing order; accepted with probability
+// min(1, exp((beta_{t+1} - beta_t)(E_b - E_a))) by the word of counter
+// (t, s, r >> 2, 3 << 24), index r & 3.
+__global__ void __launch_bounds__(128) csr_exchange_kernel(CsrJob job, int s)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= job.C) return;
+    for (int t = s & 1; t + 1 < job.M; t += 2) {
+        const int a = job.slot_of[t * job.C + r], b = job.slot_of[(t + 1) * job.C + r];
+        const double dE = job.E_cur[b] - job.E_cur[a];
+        const U4 rw = philox10((uint32_t)t, (uint32_t)s, (uint32_t)(r >> 2), 3u << 24, job.key0, job.key1);
+        const uint32_t ws[4] = {rw.x, rw.y, rw.z, rw.w};
+        const uint32_t w = ws[r & 3];
+        bool accept;
+        if (job.g.jtype == PB_J_PM1_I8) {
+            // integer energies: the host's FP64 table of floor(exp(dbeta (-d)) 2^32), d = 1, 2, ...
+            if (dE >= 0.0) {
+                accept = true;
+            } else {
+                const long long d = (long long)(-dE);
+                const int len = job.xwin[2 * t], off = job.xwin[2 * t + 1];
+                accept = d <= len && w < job.xtab[off + (int)(d - 1)];
+            }
+        } else {
+            const double x = (job.ladder[t + 1] - job.ladder[t]) * dE;
+            accept = x >= 0.0 || (double)w < floor(exp(x) * 4294967296.0);
+        }
+        if (accept) {
+            job.temp[a] = (uint8_t)(t + 1);
+            job.temp[b] = (uint8_t)t;
+            job.slot_of[t * job.C + r] = b;
+            job.slot_of[(t + 1) * job.C + r] = a;
+            atomicAdd(job.n_accept + t, 1ull);
+        }
     }
 }
 
@@ -267,6 +316,12 @@ cudaError_t csr_launch_sweep_end(const CsrJob& job, int s, int init, cudaStream_
 {
     csr_sweep_end_kernel<<<(4 * job.Rw + 255) / 256, 256, 0, st>>>(job, s, init);
     csr_snapshot_kernel<<<grid_for((long long)job.g.N * job.Rw), 256, 0, st>>>(job);
+    return cudaGetLastError();
+}
+
+cudaError_t csr_launch_exchange(const CsrJob& job, int s, cudaStream_t st)
+{
+    csr_exchange_kernel<<<(job.C + 127) / 128, 128, 0, st>>>(job, s);
     return cudaGetLastError();
 }
 

@@ -166,20 +166,15 @@ pb_status csr_build(pb_instance* I, int32_t N, int64_t E, const int32_t* eu, con
     return PB_OK;
 }
 
-pb_status csr_setup(pb_run* run, pb_instance* I, const pb_schedule* sc, int R, uint64_t seed,
-                    const pb_anneal_opts* opts, cudaStream_t st)
+// Buffers and tables of a run of R replicas over the levels `betas` (schedule
+// levels for annealing, the temperature ladder for tempering).
+static pb_status csr_prepare(pb_run* run, pb_instance* I, const std::vector<double>& betas, int step, int S, int R,
+                             uint64_t seed, const pb_anneal_opts* opts, cudaStream_t st)
 {
-    const int form = opts ? opts->form : PB_FORM_AUTO;
-    if (form != PB_FORM_AUTO && form != PB_FORM_PLAIN)
-        return fail(PB_EUNSUPPORTED, "general sparse instances run in the plain form");
-    std::vector<double> betas;
-    int step = 1;
-    pb_status ps = schedule_levels(sc, betas, step);
-    if (ps != PB_OK) return ps;
     run->inst = I;
     run->form = PB_FORM_PLAIN;
     run->R = R;
-    run->S = sc->n_sweeps;
+    run->S = S;
     run->N = I->N;
     run->stream = st;
     CsrJob& j = run->cjob;
@@ -187,7 +182,7 @@ pb_status csr_setup(pb_run* run, pb_instance* I, const pb_schedule* sc, int R, u
     j.g = I->csr;
     j.key0 = (uint32_t)(seed & 0xFFFFFFFFu);
     j.key1 = (uint32_t)(seed >> 32);
-    j.S = sc->n_sweeps;
+    j.S = S;
     j.step = step;
     j.R = R;
     j.Rw = (R + 3) / 4;
@@ -226,6 +221,8 @@ pb_status csr_setup(pb_run* run, pb_instance* I, const pb_schedule* sc, int R, u
     PB_ALLOC(run->best_sweep, (size_t)4 * j.Rw * 4);
     PB_ALLOC(run->hit_sweep, (size_t)4 * j.Rw * 4);
     PB_ALLOC(run->extra[2], (size_t)4 * j.Rw + 16);
+    PB_ALLOC(run->extra[3], (size_t)4 * j.Rw * 8);
+    j.E_cur = run->extra[3].as<double>();
     j.spins = run->final_words.as<uint32_t>();
     j.best = run->best_words.as<uint32_t>();
     j.part = run->extra[0].as<double>();
@@ -243,6 +240,77 @@ pb_status csr_setup(pb_run* run, pb_instance* I, const pb_schedule* sc, int R, u
     return PB_OK;
 }
 
+pb_status csr_setup(pb_run* run, pb_instance* I, const pb_schedule* sc, int R, uint64_t seed,
+                    const pb_anneal_opts* opts, cudaStream_t st)
+{
+    const int form = opts ? opts->form : PB_FORM_AUTO;
+    if (form != PB_FORM_AUTO && form != PB_FORM_PLAIN)
+        return fail(PB_EUNSUPPORTED, "general sparse instances run in the plain form");
+    std::vector<double> betas;
+    int step = 1;
+    pb_status ps = schedule_levels(sc, betas, step);
+    if (ps != PB_OK) return ps;
+    return csr_prepare(run, I, betas, step, sc->n_sweeps, R, seed, opts, st);
+}
+
+// Parallel tempering: M temperatures x C chains = M C slots; slot g = k C + r
+// starts at temperature k.  +-1 exchange thresholds floor(exp(dbeta (-d)) 2^32)
+// for d = 1, 2, ... until they reach 0, in FP64 on the host (the expression the
+// oracle evaluates).
+static pb_status csr_setup_pt(pb_run* run, pb_instance* I, const double* ladder, int M, int S, int C, uint64_t seed,
+                              cudaStream_t st)
+{
+    std::vector<double> lad(ladder, ladder + M);
+    pb_status ps = csr_prepare(run, I, lad, 1, S, M * C, seed, nullptr, st);
+    if (ps != PB_OK) return ps;
+    CsrJob& j = run->cjob;
+    j.M = M;
+    j.C = C;
+    std::vector<uint8_t> temp((size_t)4 * j.Rw, 0);
+    std::vector<int32_t> slot_of((size_t)M * C);
+    for (int g = 0; g < M * C; ++g) {
+        temp[(size_t)g] = (uint8_t)(g / C);
+        slot_of[(size_t)g] = g;
+    }
+    DevBuf* P = run->pt;  // 0 temp, 1 slot_of, 2 ladder, 3 xtab, 4 xwin, 5 n_accept
+    PB_ALLOC(P[0], temp.size());
+    PB_CUDA_TRY(cudaMemcpyAsync(P[0].p, temp.data(), temp.size(), cudaMemcpyHostToDevice, st));
+    PB_ALLOC(P[1], slot_of.size() * 4);
+    PB_CUDA_TRY(cudaMemcpyAsync(P[1].p, slot_of.data(), slot_of.size() * 4, cudaMemcpyHostToDevice, st));
+    PB_ALLOC(P[2], (size_t)M * 8);
+    PB_CUDA_TRY(cudaMemcpyAsync(P[2].p, ladder, (size_t)M * 8, cudaMemcpyHostToDevice, st));
+    std::vector<uint32_t> xtab;
+    std::vector<int32_t> xwin((size_t)2 * std::max(1, M - 1), 0);
+    if (I->jtype == PB_J_PM1_I8) {
+        for (int t = 0; t + 1 < M; ++t) {
+            const double db = ladder[t + 1] - ladder[t];
+            xwin[(size_t)2 * t + 1] = (int32_t)xtab.size();
+            for (long long d = 1;; ++d) {
+                const double A = std::floor(std::exp(db * (double)(-d)) * 4294967296.0);
+                if (A <= 0.0) break;
+                if (d > (1LL << 22))
+                    return fail(PB_EINVAL, "temperature spacing too small for the exchange table (> 2^22 entries)");
+                xtab.push_back((uint32_t)A);
+                xwin[(size_t)2 * t] = (int32_t)d;
+            }
+        }
+    }
+    PB_ALLOC(P[3], std::max<size_t>(1, xtab.size()) * 4);
+    if (!xtab.empty()) PB_CUDA_TRY(cudaMemcpyAsync(P[3].p, xtab.data(), xtab.size() * 4, cudaMemcpyHostToDevice, st));
+    PB_ALLOC(P[4], xwin.size() * 4);
+    PB_CUDA_TRY(cudaMemcpyAsync(P[4].p, xwin.data(), xwin.size() * 4, cudaMemcpyHostToDevice, st));
+    PB_ALLOC(P[5], (size_t)std::max(1, M - 1) * 8);
+    PB_CUDA_TRY(cudaMemsetAsync(P[5].p, 0, (size_t)std::max(1, M - 1) * 8, st));
+    PB_CUDA_TRY(cudaStreamSynchronize(st));
+    j.temp = P[0].as<uint8_t>();
+    j.slot_of = P[1].as<int32_t>();
+    j.ladder = P[2].as<double>();
+    j.xtab = P[3].as<uint32_t>();
+    j.xwin = P[4].as<int32_t>();
+    j.n_accept = P[5].as<unsigned long long>();
+    return PB_OK;
+}
+
 // Plain form: one launch per colour class and sweep, then the energy of the
 // sweep and the running best (Sec. 1.2.2, Eq. 2, Eq. 3).
 pb_status csr_launch(pb_run* run, cudaStream_t st)
@@ -257,6 +325,7 @@ pb_status csr_launch(pb_run* run, cudaStream_t st)
         for (int c = 0; c < j.g.n_colours; ++c) PB_CUDA_TRY(csr_launch_class(j, c, s, st));
         PB_CUDA_TRY(csr_launch_energy(j, j.spins, 0, st));
         PB_CUDA_TRY(csr_launch_sweep_end(j, s, 0, st));
+        if (j.temp) PB_CUDA_TRY(csr_launch_exchange(j, s, st));
     }
     PB_CUDA_TRY(cudaEventRecord(run->ev_k1, st));
     PB_CUDA_TRY(csr_launch_readout(j, j.spins, run->final_pm.as<int8_t>(), run->E_out.as<double>(), st));
@@ -300,6 +369,44 @@ pb_status pb_create_graph_instance(const pb_graph_desc* d, void* stream, pb_inst
                              static_cast<cudaStream_t>(stream));
     if (ps != PB_OK) return ps;
     *out = I.release();
+    return PB_OK;
+}
+
+pb_status pb_anneal_pt(pb_instance* I, const double* ladder, int32_t M, int32_t n_sweeps, int32_t chains,
+                       uint64_t seed, void* stream, pb_run** out)
+{
+    if (!I || !ladder || !out) return fail(PB_EINVAL, "null argument");
+    *out = nullptr;
+    if (I->topo != PB_TOPO_CSR)
+        return fail(PB_EUNSUPPORTED, "parallel tempering runs on general sparse instances (pb_create_graph_instance)");
+    if (M < 1 || M > 255 || chains < 1 || n_sweeps < 0) return fail(PB_EINVAL, "need 1 <= M <= 255, chains >= 1");
+    for (int t = 0; t + 1 < M; ++t)
+        if (!(ladder[t] < ladder[t + 1])) return fail(PB_EINVAL, "the ladder must increase");
+    if ((int64_t)M * chains > (1LL << 30)) return fail(PB_EINVAL, "too many slots");
+    std::unique_ptr<pb_run> run(new (std::nothrow) pb_run());
+    if (!run) return fail(PB_ENOMEM, "host allocation failed");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    pb_status ps = csr_setup_pt(run.get(), I, ladder, M, n_sweeps, chains, seed, st);
+    if (ps == PB_OK) ps = csr_launch(run.get(), st);
+    if (ps != PB_OK) return ps;
+    *out = run.release();
+    return PB_OK;
+}
+
+pb_status pb_pt_state(pb_run* run, int32_t* slot_temp, int64_t* n_accept)
+{
+    if (!run) return fail(PB_EINVAL, "null argument");
+    if (!run->cjob.temp) return fail(PB_EINVAL, "not a parallel-tempering run");
+    pb_status ps = wait_run(run, -1);
+    if (ps != PB_OK) return ps;
+    const CsrJob& j = run->cjob;
+    if (slot_temp) {
+        std::vector<uint8_t> t((size_t)j.M * j.C);
+        PB_CUDA_TRY(cudaMemcpy(t.data(), j.temp, t.size(), cudaMemcpyDeviceToHost));
+        for (size_t g = 0; g < t.size(); ++g) slot_temp[g] = t[g];
+    }
+    if (n_accept && j.M > 1)
+        PB_CUDA_TRY(cudaMemcpy(n_accept, j.n_accept, (size_t)(j.M - 1) * 8, cudaMemcpyDeviceToHost));
     return PB_OK;
 }
 

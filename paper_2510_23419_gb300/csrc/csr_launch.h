@@ -44,6 +44,15 @@ struct CsrJob {
     uint8_t* improved;       // [4 Rw] + 1 "any" flag at [4 Rw]
     int32_t has_target;
     double target;
+    double* E_cur;             // [4 Rw] energy after the last sweep
+    // parallel tempering (null temp: annealing with the schedule)
+    uint8_t* temp;             // [4 Rw] temperature index of every slot (= replica)
+    int32_t* slot_of;          // [M][C] slot holding temperature t of chain r
+    int32_t M, C;              // temperatures, chains; slot g = k C + r starts at temperature k
+    const double* ladder;      // [M] inverse temperatures (real couplings)
+    const uint32_t* xtab;      // +-1: exchange thresholds floor(exp(dbeta_t * (-d)) 2^32), d = 1, 2, ...
+    const int32_t* xwin;       // +-1: [M-1][2] (length, offset) of pair t's thresholds in xtab
+    unsigned long long* n_accept;  // [M-1] accepted exchanges per pair
 };
 
 constexpr int kCsrChunk = 64;  // vertices per energy chunk
@@ -53,6 +62,9 @@ cudaError_t csr_launch_init(const CsrJob& job, cudaStream_t st);
 cudaError_t csr_launch_class(const CsrJob& job, int c, int s, cudaStream_t st);
 // Energy partials of the state `m` ([N][Rw] words); exact FP64 per term when exact != 0.
 cudaError_t csr_launch_energy(const CsrJob& job, const uint32_t* m, int exact, cudaStream_t st);
+// Parallel tempering: exchange of temperatures between adjacent pairs of every
+// chain after sweep s (pairs t = s mod 2, t + 2, ...).
+cudaError_t csr_launch_exchange(const CsrJob& job, int s, cudaStream_t st);
 // Running best after sweep s (init: the initial state), snapshot of improved replicas.
 cudaError_t csr_launch_sweep_end(const CsrJob& job, int s, int init, cudaStream_t st);
 // States [R][N] int8 +-1 and energies (from the partials of the same state) of `m`.

@@ -128,6 +128,8 @@ def load():
         "pb_greedy_colouring": ([I32, I64, P, P, P], I32),
         "pb_instance_colours": ([P], I32),
         "pb_find_imin": ([P, P, P, P], st),
+        "pb_anneal_pt": ([P, P, I32, I32, I32, U64, P, P], st),
+        "pb_pt_state": ([P, P, P], st),
         "pb_sparsify_biclique": ([I32, I32, P, I32, I32, P, P, P, P, P, P, I64, I32], I64),
         "pb_sparse_project": ([I32, P, I32, I32, P, P], I32),
         "pb_autotune": ([P, I32, I32, P, P], st),
@@ -365,6 +367,22 @@ def pb_anneal_ea_noalloc(L: int, J_dev: int, sched: pb_schedule, replicas: int, 
                                        ctypes.c_void_p(best_E_dev), ctypes.c_void_p(best_sweep_dev),
                                        ctypes.c_void_p(best_states_dev), ctypes.c_void_p(final_E_dev),
                                        ctypes.c_void_p(final_states_dev), _stream(stream)))
+
+
+# ------------------------------------------------------- parallel tempering
+def pb_anneal_pt(inst, ladder, n_sweeps: int, chains: int, seed: int, stream=None) -> ctypes.c_void_p:
+    lad = np.ascontiguousarray(ladder, dtype=np.float64)
+    out = ctypes.c_void_p()
+    _check(load().pb_anneal_pt(inst, _ptr(lad), lad.size, n_sweeps, chains, seed, _stream(stream), ctypes.byref(out)))
+    return out
+
+
+def pb_pt_state(run, M: int, chains: int):
+    """(final temperature index of every slot [M * chains], accepted exchanges per pair [M - 1])."""
+    t = np.empty(M * chains, np.int32)
+    a = np.zeros(max(M - 1, 1), np.int64)
+    _check(load().pb_pt_state(run, _ptr(t), _ptr(a)))
+    return t, a[: M - 1]
 
 
 # ------------------------------------------------------- sparsified biclique
