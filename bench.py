@@ -396,6 +396,101 @@ def served_block(pb, stream, n_req: int):
             "rounds": st.rounds, "peak_inflight_bytes": st.peak_inflight_bytes, "failed": st.failed}
 
 
+# ------------------------------------------------------ next rows (f1-f4)
+def extensions_block(pb, stream, peaks):
+    """General-graph annealing (odd periodic cube, 3+ colours), parallel tempering on the
+    same graph, the sparsified biclique against the dense tensor form at equal sweeps, and
+    the Algorithm 1 driver; each timed with CUDA events on the stream it runs on."""
+    import torch
+    import synth_inputs as syn
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1), r
+
+    out = {}
+    # f1: odd periodic cube L = 25 (not bipartite), +-J, 1024 replicas, 200 sweeps
+    L, R, S = 25, 1024, 200
+    eu, ev = syn.graph_periodic_cube(L)
+    N = L ** 3
+    J = syn.edge_couplings(eu.size, "pm1", 71)
+    inst = pb.pb_create_graph_instance(N, eu, ev, J, stream=stream)
+    k = pb.pb_instance_colours(inst)
+    sc = pb.make_schedule(pb.PB_SCHED_LINEAR, S, 0.1, 3.0)
+    pb.pb_run_destroy(pb.pb_anneal(inst, pb.make_schedule(pb.PB_SCHED_LINEAR, 2, 0.1, 3.0), R, 1, stream=stream))
+    ms, run = timed(lambda: pb.pb_anneal(inst, sc, R, 5, stream=stream))
+    kms = pb.pb_run_kernel_ms(run)
+    best = float(pb.pb_energy(run, R)[1].min())
+    pb.pb_run_destroy(run)
+    upd = N * R * S
+    deg = 6
+    out["csr_k_colour"] = {
+        "workload": f"periodic cube L={L} (odd: {k} greedy colours), +-J, {R} replicas, {S} sweeps linear 0.1->3.0",
+        "ms": ms, "kernel_ms": kms, "updates_per_s": upd / (kms / 1e3), "best_E_per_spin": best / N,
+        "roofline": {"bound": "hbm", "bytes_per_update": deg + 1,
+                     "achieved_gbs": upd * (deg + 1) / (kms / 1e3) / 1e9, "peak_gbs": hbm,
+                     "frac": upd * (deg + 1) / (kms / 1e3) / 1e9 / hbm, "peak_source": "measured"}}
+    # f3: tempering on the same graph: 16 temperatures x 64 chains, 200 sweeps
+    M, C = 16, 64
+    ladder = np.linspace(0.1, 3.0, M)
+    ms, run = timed(lambda: pb.pb_anneal_pt(inst, ladder, S, C, 9, stream=stream))
+    kms = pb.pb_run_kernel_ms(run)
+    G = M * C
+    be = pb.pb_energy(run, G)[1]
+    temp, acc = pb.pb_pt_state(run, M, C)
+    pb.pb_run_destroy(run)
+    out["parallel_tempering"] = {
+        "workload": f"same cube, ladder linear 0.1..3.0 with {M} rungs, {C} chains, {S} sweeps",
+        "ms": ms, "kernel_ms": kms, "updates_per_s": N * G * S / (kms / 1e3), "best_E_per_spin": float(be.min()) / N,
+        "exchange_acceptance": [float(a) / (C * (S // 2)) for a in acc]}
+    pb.pb_instance_destroy(inst)
+    # f4: sparsified biclique n = 512 on the general-graph path vs the dense tensor form
+    n, R, S = 512, 256, 300
+    Jb = pb.pb_generate_biclique(n, pb.PB_DIST_PM1, 72)
+    sp = pb.pb_sparsify_biclique(Jb, 4, 2)
+    sinst = pb.pb_create_graph_instance(sp["N"], sp["eu"], sp["ev"], sp["J"], None, sp["colour"], stream=stream)
+    dinst = pb.pb_create_instance(pb.PB_TOPO_BICLIQUE, Jb, None, n=n, stream=stream)
+    sc = pb.make_schedule(pb.PB_SCHED_LINEAR, S, 0.35, 3.5)
+    ms_s, run = timed(lambda: pb.pb_anneal(sinst, sc, R, 3, stream=stream))
+    proj = pb.pb_sparse_project(sp["copy_of"], 2 * n, pb.pb_best_states(run, R, sp["N"]))
+    pb.pb_run_destroy(run)
+    ms_d, run = timed(lambda: pb.pb_anneal(dinst, sc, R, 3, stream=stream))
+    dense_best = float(pb.pb_energy(run, R)[1].min())
+    pb.pb_run_destroy(run)
+    F = pb.pb_fields(dinst, proj, stream=stream)  # biclique energies of the projected states: -(sum m F)/2
+    e_proj = -0.5 * (proj.astype(np.float64) * F.astype(np.float64)).sum(axis=1)
+    pb.pb_instance_destroy(sinst)
+    pb.pb_instance_destroy(dinst)
+    out["sparsified_biclique"] = {
+        "workload": f"biclique n={n} +-J, copy graph (<= 6 neighbours, copy strength 2, {sp['N']} spins), "
+                    f"{R} replicas, {S} sweeps linear 0.35->3.5",
+        "sparse_ms": ms_s, "dense_tensor_ms": ms_d,
+        "best_E_per_spin_sparse_projected": float(e_proj.min()) / (2 * n),
+        "best_E_per_spin_dense": dense_best / (2 * n)}
+    # f2: Algorithm 1 on an EA L = 8 +-J cube
+    J8 = pb.pb_generate_ea(8, pb.PB_DIST_PM1, 73)
+    einst = pb.pb_create_instance(pb.PB_TOPO_EA3D, J8, None, L=8, stream=stream)
+    run = pb.pb_anneal(einst, pb.make_schedule(pb.PB_SCHED_LINEAR, 2000, 0.35, 3.5), 256, 4, stream=stream)
+    G0 = float(pb.pb_energy(run, 256)[1].min())
+    pb.pb_run_destroy(run)
+    t0 = time.perf_counter()
+    r = pb.pb_find_imin(einst, G0, 0.97, 0.9, i_start=10, i_step=20, trials=128, i_max=4000, budgets_per_launch=8,
+                        seed=77, stream=stream)
+    dt = time.perf_counter() - t0
+    pb.pb_instance_destroy(einst)
+    out["algorithm1"] = {"workload": "EA L=8 +-J, G = best of 256 replicas x 2000 sweeps, p = 0.97, p_succ = 0.9, "
+                                     "128 trials, budgets 10, 30, ... (8 per launch)",
+                         "i_min": r.i_min, "fails": r.fails, "budgets_tried": r.budgets_tried,
+                         "launches": r.launches, "seconds": dt}
+    return out
+
+
 # ------------------------------------------------- small profiling cases
 CASES = {
     # name: (topology, L or n, law, replicas, sweeps, form)
@@ -408,6 +503,7 @@ CASES = {
     "bq-n1024-R1024-pm1-tensor": ("bq", 1024, "pm1", 1024, 4, "tensor"),
     "bq-n4096-R4096-pm1-tensor-s200": ("bq", 4096, "pm1", 4096, 200, "tensor"),
     "bq-n4096-R4096-gauss-tensor-s100": ("bq", 4096, "gauss", 4096, 100, "tensor"),
+    "csr-cube25-R1024-pm1": ("csr", 25, "pm1", 1024, 50, "plain"),
 }
 
 
@@ -424,6 +520,10 @@ def run_case(name):
     if topo == "ea":
         J = pb.pb_generate_ea(size, dist, 3)
         inst = pb.pb_create_instance(pb.PB_TOPO_EA3D, J, None, L=size)
+    elif topo == "csr":
+        import synth_inputs as syn
+        eu, ev = syn.graph_periodic_cube(size)
+        inst = pb.pb_create_graph_instance(size ** 3, eu, ev, syn.edge_couplings(eu.size, law, 3))
     else:
         J = pb.pb_generate_biclique(size, dist, 3)
         inst = pb.pb_create_instance(pb.PB_TOPO_BICLIQUE, J, None, n=size)
@@ -448,6 +548,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-biclique", action="store_true", help="skip the biclique tensor-core measurement")
     ap.add_argument("--no-mixed", action="store_true", help="skip the 200-instance mixed batch")
+    ap.add_argument("--no-extensions", action="store_true",
+                    help="skip general graphs, tempering, sparsified biclique and Algorithm 1")
     ap.add_argument("--no-serve", action="store_true", help="skip the served Poisson stream")
     ap.add_argument("--serve-requests", type=int, default=1500, help="requests of the served stream")
     ap.add_argument("--case", default=None, choices=sorted(CASES),
@@ -617,6 +719,8 @@ def main():
 
     if rank == 0 and not args.no_biclique:
         line["biclique"] = biclique_block(pb, stream, peaks)
+    if rank == 0 and not args.no_extensions:
+        line["next_rows"] = extensions_block(pb, stream, peaks)
     if rank == 0 and not args.no_mixed:
         line["mixed_batch"] = mixed_block(pb, stream)
     if rank == 0 and not args.no_serve:
