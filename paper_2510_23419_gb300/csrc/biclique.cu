@@ -207,11 +207,39 @@ __global__ void __launch_bounds__(256) bq_cc_half_kernel(BqJob job, int side, in
 }
 
 // Energy of the state after the sweep (the row-tile partials of both sides,
-// summed in a fixed order), running best, snapshot of improved replicas.
-// 32 replicas per block: one thread per replica reads the partials (coalesced
-// across replicas), then the block copies the improved replicas' rows with
-// 16-byte loads and stores.
+// summed in a fixed order) and running best; 32 replicas per block, one thread
+// per replica reads the partials (coalesced across replicas).  Best states are
+// copied lazily: the live states alternate between two buffers per side by
+// sweep parity, so the state of sweep s - 1 survives sweep s, and a replica's
+// rows are copied only when an improving sweep is followed by one that does
+// not improve (and once after the last sweep).
 constexpr int kEndReps = 32;
+
+// Copy the rows of the flagged replicas of a block (one warp per replica, eight
+// independent 16-byte loads in flight per lane) from the live buffers of parity
+// `par` into the best buffers.
+__device__ __forceinline__ void bq_copy_flagged(const BqJob& job, int r0, const int* flag, int par)
+{
+    const int nvec = job.ld * (job.inst.jtype == PB_J_PM1_I8 ? 1 : 2) / 16;  // the row is a multiple of 16 bytes
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int q = warp; q < kEndReps; q += (int)(blockDim.x >> 5)) {
+        if (!flag[q]) continue;
+        const size_t row = (size_t)(r0 + q) * nvec;
+        for (int side = 0; side < 2; ++side) {
+            const uint4* __restrict__ src = static_cast<const uint4*>(job.buf[side][par]) + row;
+            uint4* __restrict__ dst = static_cast<uint4*>(job.best[side]) + row;
+            for (int k0 = lane; k0 < nvec; k0 += 32 * 8) {
+                uint4 t[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (k0 + 32 * u < nvec) t[u] = src[k0 + 32 * u];
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (k0 + 32 * u < nvec) dst[k0 + 32 * u] = t[u];
+            }
+        }
+    }
+}
 
 __global__ void __launch_bounds__(256) bq_sweep_end_kernel(BqJob job, int s_arg, int init, const int32_t* sp_read,
                                                           int32_t* sp_write)
@@ -219,12 +247,13 @@ __global__ void __launch_bounds__(256) bq_sweep_end_kernel(BqJob job, int s_arg,
     const int s = sp_read ? *sp_read : s_arg;
     if (sp_write && blockIdx.x == 0 && threadIdx.x == 0) *sp_write = s + 1;  // read by the next sweep's launches
     if (!init && s >= job.S) return;
-    __shared__ int s_imp[kEndReps];
+    __shared__ int s_copy[kEndReps];
     const int r0 = blockIdx.x * kEndReps;
     const bool pm1 = job.inst.jtype == PB_J_PM1_I8;
     if (threadIdx.x < kEndReps) {
         const int r = r0 + threadIdx.x;
         bool imp;
+        const int prev = init ? -2 : job.best_sweep[r];
         if (pm1) {
             const int32_t* p = static_cast<const int32_t*>(job.part);
             int32_t E = 0;
@@ -244,29 +273,20 @@ __global__ void __launch_bounds__(256) bq_sweep_end_kernel(BqJob job, int s_arg,
         }
         if (init) job.hit_sweep[r] = -1;
         if (imp) job.best_sweep[r] = init ? -1 : s;
-        s_imp[threadIdx.x] = imp ? 1 : 0;
+        // the best is state s - 1, and sweep s + 1 will overwrite its buffers: copy it now
+        s_copy[threadIdx.x] = (!init && !imp && prev == s - 1) ? 1 : 0;
     }
     __syncthreads();
-    // one warp per improved replica row, eight independent 16-byte loads in flight per lane
-    const int nvec = job.ld * (pm1 ? 1 : 2) / 16;  // the row is a multiple of 16 bytes
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int q = warp; q < kEndReps; q += (int)(blockDim.x >> 5)) {
-        if (!s_imp[q]) continue;
-        const size_t row = (size_t)(r0 + q) * nvec;
-        for (int side = 0; side < 2; ++side) {
-            const uint4* __restrict__ src = static_cast<const uint4*>(job.spins[side]) + row;
-            uint4* __restrict__ dst = static_cast<uint4*>(job.best[side]) + row;
-            for (int k0 = lane; k0 < nvec; k0 += 32 * 8) {
-                uint4 t[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u)
-                    if (k0 + 32 * u < nvec) t[u] = src[k0 + 32 * u];
-#pragma unroll
-                for (int u = 0; u < 8; ++u)
-                    if (k0 + 32 * u < nvec) dst[k0 + 32 * u] = t[u];
-            }
-        }
-    }
+    if (!init) bq_copy_flagged(job, r0, s_copy, (s - 1) & 1);
+}
+
+__global__ void __launch_bounds__(256) bq_best_flush_kernel(BqJob job)
+{
+    __shared__ int s_copy[kEndReps];
+    const int r0 = blockIdx.x * kEndReps;
+    if (threadIdx.x < kEndReps) s_copy[threadIdx.x] = job.best_sweep[r0 + threadIdx.x] == job.S - 1 ? 1 : 0;
+    __syncthreads();
+    bq_copy_flagged(job, r0, s_copy, (job.S - 1) & 1);
 }
 
 __global__ void __launch_bounds__(256) bq_readout_kernel(BqJob job, int which, int8_t* __restrict__ out)
@@ -461,6 +481,12 @@ cudaError_t bq_launch_sweep_end(const BqJob& job, int s, int init, const int32_t
                                 cudaStream_t st)
 {
     bq_sweep_end_kernel<<<job.Rpad / kEndReps, 256, 0, st>>>(job, s, init, sp_read, sp_write);
+    return cudaGetLastError();
+}
+
+cudaError_t bq_launch_best_flush(const BqJob& job, cudaStream_t st)
+{
+    bq_best_flush_kernel<<<job.Rpad / kEndReps, 256, 0, st>>>(job);
     return cudaGetLastError();
 }
 

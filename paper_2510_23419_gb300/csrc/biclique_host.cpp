@@ -232,10 +232,14 @@ static pb_status bq_prepare(pb_run* run, pb_instance* I, const pb_schedule* sc, 
     const size_t side_bytes = (size_t)j.Rpad * j.ld * (pm1 ? 1 : 2);
     for (int s = 0; s < 2; ++s) {
         PB_ALLOC(run->extra[s], side_bytes);
+        PB_ALLOC(run->bq_alt[s], side_bytes);
         PB_ALLOC(run->extra[2 + s], side_bytes);
         PB_CUDA_TRY(cudaMemsetAsync(run->extra[s].p, 0, side_bytes, st));
+        PB_CUDA_TRY(cudaMemsetAsync(run->bq_alt[s].p, 0, side_bytes, st));
         PB_CUDA_TRY(cudaMemsetAsync(run->extra[2 + s].p, 0, side_bytes, st));
-        j.spins[s] = run->extra[s].p;
+        j.buf[s][0] = run->extra[s].p;
+        j.buf[s][1] = run->bq_alt[s].p;
+        j.spins[s] = j.buf[s][0];
         j.best[s] = run->extra[2 + s].p;
     }
     PB_ALLOC(run->extra[4], (size_t)2 * j.nblk * j.Rpad * 4);
@@ -262,8 +266,10 @@ static pb_status bq_prepare(pb_run* run, pb_instance* I, const pb_schedule* sc, 
             PB_CUDA_TRY(bq_tc_make_map(&run->maps.a[k], a[k], esz, (uint64_t)n, (uint64_t)n, (uint64_t)q.ldj * esz,
                                        kBqTcRows));
         for (int sd = 0; sd < 2; ++sd)
-            PB_CUDA_TRY(bq_tc_make_map(&run->maps.b[sd], j.spins[sd], esz, (uint64_t)n, (uint64_t)j.Rpad,
-                                       (uint64_t)j.ld * esz, kBqTcReps / 2));  // half a tile per cluster CTA
+            for (int par = 0; par < 2; ++par)
+                PB_CUDA_TRY(bq_tc_make_map(&run->maps.b[2 * sd + par], j.buf[sd][par], esz, (uint64_t)n,
+                                           (uint64_t)j.Rpad, (uint64_t)j.ld * esz,
+                                           kBqTcReps / 2));  // half a tile per cluster CTA
         PB_CUDA_TRY(bq_tc_set_smem());
     }
     PB_CUDA_TRY(cudaEventCreate(&run->ev_start));
@@ -273,12 +279,24 @@ static pb_status bq_prepare(pb_run* run, pb_instance* I, const pb_schedule* sc, 
     return PB_OK;
 }
 
-static cudaError_t bq_half(pb_run* run, int side, int s, const int32_t* sp, int decide, float* fields_out,
-                           cudaStream_t st)
+// The job as one launch sees it: its own side's state in the buffer of parity
+// `own`, the other side's in the buffer of parity `other`.
+static BqJob bq_view(const BqJob& j, int side, int own, int other)
 {
+    BqJob v = j;
+    v.spins[side] = j.buf[side][own];
+    v.spins[1 - side] = j.buf[1 - side][other];
+    return v;
+}
+
+static cudaError_t bq_half(pb_run* run, int side, int own, int other, int s, const int32_t* sp, int decide,
+                           float* fields_out, cudaStream_t st)
+{
+    const BqJob v = bq_view(run->bjob, side, own, other);
     if (run->form == PB_FORM_TENSOR)
-        return bq_launch_tc_half(run->maps, run->bjob, side, s, sp, decide, fields_out, run->dev_err, st);
-    return bq_launch_cc_half(run->bjob, side, s, sp, decide, fields_out, st);
+        return bq_launch_tc_half(run->maps, 2 * (1 - side) + other, v, side, s, sp, decide, fields_out, run->dev_err,
+                                 st);
+    return bq_launch_cc_half(v, side, s, sp, decide, fields_out, st);
 }
 
 // Sweeps per captured chunk (even: the two sweep counters alternate within it).
@@ -295,8 +313,10 @@ static pb_status bq_enqueue_chunk(pb_run* run, int nsweeps, cudaStream_t st)
     for (int k = 0; k < nsweeps; ++k) {
         const int32_t* rd = ctr + (k & 1);
         int32_t* wr = ctr + ((k + 1) & 1);
-        PB_CUDA_TRY(bq_half(run, 0, 0, rd, 1, nullptr, st));
-        PB_CUDA_TRY(bq_half(run, 1, 0, rd, 1, nullptr, st));
+        const int p = k & 1;  // parity of the sweep (chunks start at even sweeps)
+        // side A reads side B of the previous sweep; side B reads side A of this sweep
+        PB_CUDA_TRY(bq_half(run, 0, p, 1 - p, 0, rd, 1, nullptr, st));
+        PB_CUDA_TRY(bq_half(run, 1, p, p, 0, rd, 1, nullptr, st));
         PB_CUDA_TRY(bq_launch_sweep_end(j, 0, 0, rd, wr, st));
     }
     return PB_OK;
@@ -322,10 +342,12 @@ pb_status bq_launch(pb_run* run, cudaStream_t st)
     const BqJob& j = run->bjob;
     PB_CUDA_TRY(cudaEventRecord(run->ev_start, st));
     PB_CUDA_TRY(cudaMemsetAsync(run->dev_err + 2, 0, 2 * sizeof(int32_t), st));
-    PB_CUDA_TRY(bq_launch_init(j, st));
+    // the initial state is "sweep -1": parity 1
+    const BqJob init_view = bq_view(j, 0, 1, 1);
+    PB_CUDA_TRY(bq_launch_init(init_view, st));
     // energy of the initial state: side B fields of the initial A, no decisions
-    PB_CUDA_TRY(bq_half(run, 0, 0, nullptr, 0, nullptr, st));
-    PB_CUDA_TRY(bq_half(run, 1, 0, nullptr, 0, nullptr, st));
+    PB_CUDA_TRY(bq_half(run, 0, 1, 1, 0, nullptr, 0, nullptr, st));
+    PB_CUDA_TRY(bq_half(run, 1, 1, 1, 0, nullptr, 0, nullptr, st));
     PB_CUDA_TRY(bq_launch_sweep_end(j, -1, 1, nullptr, nullptr, st));
     PB_CUDA_TRY(cudaEventRecord(run->ev_k0, st));
     if (j.S > 0) {
@@ -355,8 +377,10 @@ pb_status bq_launch(pb_run* run, cudaStream_t st)
             }
         }
     }
+    PB_CUDA_TRY(bq_launch_best_flush(j, st));
     PB_CUDA_TRY(cudaEventRecord(run->ev_k1, st));
-    PB_CUDA_TRY(bq_launch_readout(j, 0, run->final_pm.as<int8_t>(), run->E_out.as<double>(), st));
+    const int last = (j.S - 1) & 1;  // parity of the final state (S = 0: the initial state)
+    PB_CUDA_TRY(bq_launch_readout(bq_view(j, 0, last, last), 0, run->final_pm.as<int8_t>(), run->E_out.as<double>(), st));
     PB_CUDA_TRY(bq_launch_readout(j, 1, run->best_pm.as<int8_t>(), run->E_out.as<double>() + run->R, st));
     PB_CUDA_TRY(cudaEventRecord(run->ev_stop, st));
     return PB_OK;
@@ -384,8 +408,8 @@ pb_status bq_fields(pb_instance* I, const int8_t* d_states, int R, int form, flo
     pb_status ps = bq_prepare(&run, I, &sc, R, 0, nullptr, form, st);
     if (ps != PB_OK) return ps;
     PB_CUDA_TRY(bq_launch_encode(run.bjob, d_states, st));
-    PB_CUDA_TRY(bq_half(&run, 0, 0, nullptr, 0, d_out, st));
-    PB_CUDA_TRY(bq_half(&run, 1, 0, nullptr, 0, d_out, st));
+    PB_CUDA_TRY(bq_half(&run, 0, 0, 0, 0, nullptr, 0, d_out, st));
+    PB_CUDA_TRY(bq_half(&run, 1, 0, 0, 0, nullptr, 0, d_out, st));
     PB_CUDA_TRY(cudaStreamSynchronize(st));
     int code = 0;
     PB_CUDA_TRY(cudaMemcpy(&code, run.dev_err, sizeof(int), cudaMemcpyDeviceToHost));

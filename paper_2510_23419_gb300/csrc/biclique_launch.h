@@ -39,7 +39,9 @@ struct BqJob {
     const float* betaf;     // F32 [levels]
     int32_t R, Rpad;        // replicas, padded to the replica tile
     int32_t ld;             // leading dimension of a spin row (>= n, padded for the tensor form)
-    void* spins[2];         // [Rpad][ld] live state of side A (colour 0) and side B (colour 1)
+    void* spins[2];         // [Rpad][ld] the state a launch reads and writes: side A (colour 0), side B (colour 1)
+    void* buf[2][2];        // [side][parity] live states: sweep s writes parity s & 1 (the initial state: 1), so
+                            // state s - 1 is intact during sweep s
     void* best[2];          // [Rpad][ld] best states
     int32_t nblk;           // row blocks of the field kernels
     void* part;             // [2][nblk][Rpad] energy partials (int32 PM1 / float F32): [0] -h.a, [1] -b.F_B
@@ -67,8 +69,13 @@ cudaError_t bq_launch_cc_half(const BqJob& job, int side, int s, const int32_t* 
                               cudaStream_t st);
 // End of sweep s (or of sweep *sp_read): energies, running best, snapshots; with
 // sp_write, stores the next sweep index there.
+// The best state of a replica whose last improvement was sweep s - 1 is copied
+// from the parity-(s-1) buffers when sweep s does not improve it (before sweep
+// s + 1 overwrites them), so a run of improving sweeps costs one copy.
 cudaError_t bq_launch_sweep_end(const BqJob& job, int s, int init, const int32_t* sp_read, int32_t* sp_write,
                                 cudaStream_t st);
+// After the last sweep (S): copy the replicas whose best is state S - 1.
+cudaError_t bq_launch_best_flush(const BqJob& job, cudaStream_t st);
 cudaError_t bq_launch_readout(const BqJob& job, int which /*0 final, 1 best*/, int8_t* out_pm, double* out_E,
                               cudaStream_t st);
 cudaError_t bq_launch_encode(const BqJob& job, const int8_t* d_states, cudaStream_t st);

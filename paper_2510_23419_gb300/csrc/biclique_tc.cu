@@ -660,8 +660,8 @@ cudaError_t bq_tc_set_smem()
     return cudaSuccess;
 }
 
-cudaError_t bq_launch_tc_half(const BqTcMaps& maps, const BqJob& job, int side, int s, const int32_t* sp, int decide,
-                              float* fields_out, int* err, cudaStream_t st)
+cudaError_t bq_launch_tc_half(const BqTcMaps& maps, int bsel, const BqJob& job, int side, int s, const int32_t* sp,
+                              int decide, float* fields_out, int* err, cudaStream_t st)
 {
     const int kind = job.inst.jtype == PB_J_PM1_I8 ? 0 : 1;
     const size_t smem = bq_tc_smem_bytes(kind);
@@ -671,7 +671,7 @@ cudaError_t bq_launch_tc_half(const BqTcMaps& maps, const BqJob& job, int side, 
     dim3 grid((unsigned)(2 * nclus));  // persistent clusters of two CTAs
     const CUtensorMap& A = side == 0 ? maps.a[0] : maps.a[2];
     const CUtensorMap& A2 = side == 0 ? maps.a[1] : maps.a[3];
-    const CUtensorMap& B = maps.b[1 - side];
+    const CUtensorMap& B = maps.b[bsel];
     if (kind == 0 && job.tabmode == 2)
         bq_tc_half_kernel<0, 2><<<grid, kThreads, smem, st>>>(A, A2, B, job, side, s, sp, decide, fields_out, err);
     else if (kind == 0 && job.tabmode == 1)

@@ -9,10 +9,10 @@
 namespace pb {
 
 // TMA descriptors of one run: a[0], a[1] = J (e4m3, or bf16 hi and lo),
-// a[2], a[3] = J^T; b[0], b[1] = spins of side A and side B.
+// a[2], a[3] = J^T; b[2 side + parity] = the live spin buffers.
 struct BqTcMaps {
     CUtensorMap a[4];
-    CUtensorMap b[2];
+    CUtensorMap b[4];
 };
 
 constexpr int kBqTcRows = 128;   // rows of a tile (tensor-memory lanes)
@@ -26,7 +26,9 @@ cudaError_t bq_tc_make_map(CUtensorMap* map, const void* base, int elem_bytes, u
 // The sweep index is s, or the device value *sp when sp is not null (see
 // bq_launch_cc_half); the threshold windows are read from job.win, from where
 // job.tabmode says (0 global, 1 shared, 2 shared with 32 copies).
-cudaError_t bq_launch_tc_half(const BqTcMaps& maps, const BqJob& job, int side, int s, const int32_t* sp, int decide,
-                              float* fields_out, int* err, cudaStream_t st);
+// bsel: index in maps.b of the other side's spins (the B operand); job.spins
+// must name the matching buffers.
+cudaError_t bq_launch_tc_half(const BqTcMaps& maps, int bsel, const BqJob& job, int side, int s, const int32_t* sp,
+                              int decide, float* fields_out, int* err, cudaStream_t st);
 
 }  // namespace pb

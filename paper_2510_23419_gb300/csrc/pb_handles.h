@@ -112,7 +112,8 @@ struct pb_run {
     pb::DevBuf table, betaf, best_words, final_words, E_best_i, E_best_f, best_sweep, hit_sweep;
     pb::DevBuf best_pm, final_pm, E_out;  // readout: [R][N] x2, [2R] doubles
     pb::DevBuf extra[8];
-    pb::DevBuf pt[6];  // parallel tempering buffers of a general-graph run
+    pb::DevBuf pt[6];      // parallel tempering buffers of a general-graph run
+    pb::DevBuf bq_alt[2];  // biclique: the parity-1 live spin buffers of sides A and B
     std::vector<int32_t> bq_win;  // biclique +-1: per beta level, (first index, width, offset) of its threshold window
     std::shared_ptr<pb::BatchShared> batch;
     ~pb_run()
