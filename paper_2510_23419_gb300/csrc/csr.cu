@@ -74,10 +74,17 @@ __global__ void __launch_bounds__(256) csr_init_kernel(CsrJob job)
     }
 }
 
+// Block (kCsrLanesQ replica words) x (kCsrLanesV vertex lanes); a thread keeps
+// its replica word and walks kCsrVpt spins of the class, adding the energy
+// change of every flip, -2 m_new F (Eq. 3 fields, exact integers for +-1); the
+// block then sums its lanes in a fixed order into the class chunk's partial.
 template <int JT>
-__global__ void __launch_bounds__(256) csr_class_kernel(CsrJob job, int c, int s)
+__global__ void __launch_bounds__(kCsrLanesQ* kCsrLanesV) csr_class_kernel(CsrJob job, int c, int s)
 {
+    __shared__ double red[kCsrLanesV][kCsrLanesQ][4];
     const int off = job.g.cls_off[c], ncls = job.g.cls_off[c + 1] - off;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int q = blockIdx.y * kCsrLanesQ + tx;
     // annealing: one level for all replicas; tempering: each replica's own temperature
     TabWindow win{0, 0, 1};
     float cexp = 0.0f;
@@ -88,40 +95,62 @@ __global__ void __launch_bounds__(256) csr_class_kernel(CsrJob job, int c, int s
         else
             cexp = f32_cexp(job.betaf[lev]);
     }
-    const long long total = (long long)ncls * job.Rw;
-    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (long long)gridDim.x * blockDim.x) {
-        const int t = (int)(idx / job.Rw), q = (int)(idx - (long long)t * job.Rw);
-        const int i = job.g.cls_v[off + t];
-        const U4 r = philox10((uint32_t)t, (uint32_t)s, (uint32_t)q, (kTagDecision << 24) | (uint32_t)c, job.key0,
-                              job.key1);
-        const uint32_t ws[4] = {r.x, r.y, r.z, r.w};
-        uint32_t w = 0;
-        if (JT == PB_J_PM1_I8) {
-            int G[4];
-            pm1_row(job, job.spins, i, q, G);
-            const int h = job.g.h8 ? job.g.h8[i] : 0;
+    long long di[4] = {0, 0, 0, 0};
+    float df[4] = {0.f, 0.f, 0.f, 0.f};
+    if (q < job.Rw) {
+        for (int k = 0; k < kCsrVpt; ++k) {
+            const int t = blockIdx.x * kCsrClassChunk + k * kCsrLanesV + ty;
+            if (t >= ncls) break;
+            const int i = job.g.cls_v[off + t];
+            const U4 r = philox10((uint32_t)t, (uint32_t)s, (uint32_t)q, (kTagDecision << 24) | (uint32_t)c, job.key0,
+                                  job.key1);
+            const uint32_t ws[4] = {r.x, r.y, r.z, r.w};
+            const uint32_t wold = job.spins[(size_t)i * job.Rw + q];
+            uint32_t w = 0;
+            if (JT == PB_J_PM1_I8) {
+                int G[4];
+                pm1_row(job, job.spins, i, q, G);
+                const int h = job.g.h8 ? job.g.h8[i] : 0;
 #pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                TabWindow wb = win;
-                if (job.temp) {
-                    const int l = job.temp[4 * q + b];
-                    wb = TabWindow{job.win[3 * l + 2], job.win[3 * l], job.win[3 * l + 1]};
+                for (int b = 0; b < 4; ++b) {
+                    TabWindow wb = win;
+                    if (job.temp) {
+                        const int l = job.temp[4 * q + b];
+                        wb = TabWindow{job.win[3 * l + 2], job.win[3 * l], job.win[3 * l + 1]};
+                    }
+                    const int F = G[b] + h;
+                    const int f = min(max(F - job.fmin, wb.lo), wb.lo + wb.width - 1) - wb.lo;
+                    const uint32_t nb = decide_bit(ws[b], job.table[wb.off + f]);
+                    w |= nb << (8 * b);
+                    if (nb != byte_of(wold, b)) di[b] += nb ? 2LL * F : -2LL * F;  // -2 m_new F
                 }
-                const int f = min(max(G[b] + h - job.fmin, wb.lo), wb.lo + wb.width - 1) - wb.lo;
-                w |= decide_bit(ws[b], job.table[wb.off + f]) << (8 * b);
-            }
-        } else {
-            float G[4];
-            f32_row(job, job.spins, i, q, G);
-            const float h = job.g.hf ? job.g.hf[i] : 0.0f;
+            } else {
+                float G[4];
+                f32_row(job, job.spins, i, q, G);
+                const float h = job.g.hf ? job.g.hf[i] : 0.0f;
 #pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                const float cb = job.temp ? f32_cexp(job.betaf[job.temp[4 * q + b]]) : cexp;
-                w |= decide_f32(ws[b], G[b] + h, cb) << (8 * b);
+                for (int b = 0; b < 4; ++b) {
+                    const float cb = job.temp ? f32_cexp(job.betaf[job.temp[4 * q + b]]) : cexp;
+                    const float F = G[b] + h;
+                    const uint32_t nb = decide_f32(ws[b], F, cb);
+                    w |= nb << (8 * b);
+                    if (nb != byte_of(wold, b)) df[b] += nb ? 2.0f * F : -2.0f * F;
+                }
             }
+            job.spins[(size_t)i * job.Rw + q] = w;
         }
-        job.spins[(size_t)i * job.Rw + q] = w;
+    }
+#pragma unroll
+    for (int b = 0; b < 4; ++b) red[ty][tx][b] = JT == PB_J_PM1_I8 ? (double)di[b] : (double)df[b];
+    __syncthreads();
+    if (ty == 0 && q < job.Rw) {
+        double* out = job.dpart + (size_t)(job.dchunk_off[c] + blockIdx.x) * 4 * job.Rw + 4 * q;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            double t = 0.0;
+            for (int v = 0; v < kCsrLanesV; ++v) t += red[v][tx][b];
+            out[b] = t;
+        }
     }
 }
 
@@ -173,12 +202,31 @@ __device__ __forceinline__ double csr_energy_of(const CsrJob& job, int r)
     return 0.5 * t;
 }
 
+// 32 replicas per block, 8 warps: warp w sums the class-chunk changes w, w + 8, ...
+// of its lane's replica, then the 8 warp sums are added in order.
 __global__ void __launch_bounds__(256) csr_sweep_end_kernel(CsrJob job, int s, int init)
 {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= 4 * job.Rw) return;
-    const double E = csr_energy_of(job, r);
-    if (job.E_cur) job.E_cur[r] = E;
+    __shared__ double acc[8][32];
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const int r = blockIdx.x * 32 + lane;
+    const bool live = r < 4 * job.Rw;
+    if (!init) {
+        double t = 0.0;
+        if (live)
+            for (int ch = wp; ch < job.ndchunk; ch += 8) t += job.dpart[(size_t)ch * 4 * job.Rw + r];
+        acc[wp][lane] = t;
+    }
+    __syncthreads();
+    if (wp != 0 || !live) return;
+    double E;
+    if (init) {
+        E = csr_energy_of(job, r);
+    } else {
+        double dE = 0.0;
+        for (int w = 0; w < 8; ++w) dE += acc[w][lane];
+        E = job.E_cur[r] + dE;  // energy changes of the sweep's classes
+    }
+    job.E_cur[r] = E;
     bool imp;
     if (init) {
         imp = true;
@@ -290,13 +338,15 @@ cudaError_t csr_launch_init(const CsrJob& job, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t csr_launch_class(const CsrJob& job, int c, int s, cudaStream_t st)
+cudaError_t csr_launch_class(const CsrJob& job, int c, int nchunks, int s, cudaStream_t st)
 {
-    const long long total = (long long)job.Rw * job.g.N;  // an upper bound of the class size
+    if (nchunks < 1) return cudaSuccess;
+    const dim3 grid((unsigned)nchunks, (unsigned)((job.Rw + kCsrLanesQ - 1) / kCsrLanesQ));
+    const dim3 block(kCsrLanesQ, kCsrLanesV);
     if (job.g.jtype == PB_J_PM1_I8)
-        csr_class_kernel<PB_J_PM1_I8><<<grid_for(total / std::max(1, job.g.n_colours) + 1), 256, 0, st>>>(job, c, s);
+        csr_class_kernel<PB_J_PM1_I8><<<grid, block, 0, st>>>(job, c, s);
     else
-        csr_class_kernel<PB_J_F32><<<grid_for(total / std::max(1, job.g.n_colours) + 1), 256, 0, st>>>(job, c, s);
+        csr_class_kernel<PB_J_F32><<<grid, block, 0, st>>>(job, c, s);
     return cudaGetLastError();
 }
 
@@ -314,7 +364,7 @@ cudaError_t csr_launch_energy(const CsrJob& job, const uint32_t* m, int exact, c
 
 cudaError_t csr_launch_sweep_end(const CsrJob& job, int s, int init, cudaStream_t st)
 {
-    csr_sweep_end_kernel<<<(4 * job.Rw + 255) / 256, 256, 0, st>>>(job, s, init);
+    csr_sweep_end_kernel<<<(4 * job.Rw + 31) / 32, 256, 0, st>>>(job, s, init);
     csr_snapshot_kernel<<<grid_for((long long)job.g.N * job.Rw), 256, 0, st>>>(job);
     return cudaGetLastError();
 }

@@ -131,6 +131,7 @@ pb_status csr_build(pb_instance* I, int32_t N, int64_t E, const int32_t* eu, con
     I->hmax = hmax;
     I->maxdeg = maxdeg;
     I->n_colours = k;
+    I->csr_cls_off = cls_off;
     DevBuf* B = I->csr_bufs;  // 0 rowptr, 1 col, 2 J, 3 h, 4 cls_off, 5 cls_v, 6 colour
     auto up = [&](DevBuf& b, const void* src, size_t bytes) -> pb_status {
         PB_ALLOC(b, bytes);
@@ -223,6 +224,23 @@ static pb_status csr_prepare(pb_run* run, pb_instance* I, const std::vector<doub
     PB_ALLOC(run->extra[2], (size_t)4 * j.Rw + 16);
     PB_ALLOC(run->extra[3], (size_t)4 * j.Rw * 8);
     j.E_cur = run->extra[3].as<double>();
+    // class chunks of the energy changes
+    const int k = I->n_colours;
+    run->csr_nchunk.assign((size_t)k, 0);
+    std::vector<int32_t> doff((size_t)k + 1, 0);
+    for (int c = 0; c < k; ++c) {
+        const int ncls = I->csr_cls_off[(size_t)c + 1] - I->csr_cls_off[(size_t)c];
+        run->csr_nchunk[(size_t)c] = (ncls + kCsrClassChunk - 1) / kCsrClassChunk;
+        doff[(size_t)c + 1] = doff[(size_t)c] + run->csr_nchunk[(size_t)c];
+    }
+    j.ndchunk = doff[(size_t)k];
+    PB_ALLOC(run->extra[4], doff.size() * 4);
+    PB_CUDA_TRY(cudaMemcpyAsync(run->extra[4].p, doff.data(), doff.size() * 4, cudaMemcpyHostToDevice, st));
+    PB_ALLOC(run->extra[5], (size_t)std::max(1, j.ndchunk) * 4 * j.Rw * 8);
+    PB_CUDA_TRY(cudaMemsetAsync(run->extra[5].p, 0, (size_t)std::max(1, j.ndchunk) * 4 * j.Rw * 8, st));
+    PB_CUDA_TRY(cudaStreamSynchronize(st));
+    j.dchunk_off = run->extra[4].as<int32_t>();
+    j.dpart = run->extra[5].as<double>();
     j.spins = run->final_words.as<uint32_t>();
     j.best = run->best_words.as<uint32_t>();
     j.part = run->extra[0].as<double>();
@@ -322,8 +340,8 @@ pb_status csr_launch(pb_run* run, cudaStream_t st)
     PB_CUDA_TRY(csr_launch_sweep_end(j, -1, 1, st));
     PB_CUDA_TRY(cudaEventRecord(run->ev_k0, st));
     for (int s = 0; s < j.S; ++s) {
-        for (int c = 0; c < j.g.n_colours; ++c) PB_CUDA_TRY(csr_launch_class(j, c, s, st));
-        PB_CUDA_TRY(csr_launch_energy(j, j.spins, 0, st));
+        for (int c = 0; c < j.g.n_colours; ++c)
+            PB_CUDA_TRY(csr_launch_class(j, c, run->csr_nchunk[(size_t)c], s, st));
         PB_CUDA_TRY(csr_launch_sweep_end(j, s, 0, st));
         if (j.temp) PB_CUDA_TRY(csr_launch_exchange(j, s, st));
     }

@@ -38,6 +38,9 @@ struct CsrJob {
     uint32_t* best;          // [N][Rw]
     int32_t nchunk;          // vertex chunks of the energy partials
     double* part;            // [nchunk][4 Rw] energy partials (PM1: 2E as exact integers)
+    int32_t ndchunk;         // class chunks of the sweep's energy changes, over all classes
+    const int32_t* dchunk_off;  // [n_colours + 1] first class chunk of each class
+    double* dpart;           // [ndchunk][4 Rw] energy change of each class chunk in the last sweep
     double* E_best;          // [4 Rw]
     int32_t* best_sweep;     // [4 Rw]
     int32_t* hit_sweep;      // [4 Rw]
@@ -56,16 +59,23 @@ struct CsrJob {
 };
 
 constexpr int kCsrChunk = 64;  // vertices per energy chunk
+constexpr int kCsrLanesQ = 32;  // class kernel: replica words per block
+constexpr int kCsrLanesV = 8;   // class kernel: vertex lanes per block
+constexpr int kCsrVpt = 8;      // class kernel: class spins per thread
+constexpr int kCsrClassChunk = kCsrLanesV * kCsrVpt;  // class spins per block
 
 cudaError_t csr_launch_init(const CsrJob& job, cudaStream_t st);
-// Update of colour class c in sweep s (Eq. 2, Eq. 3).
-cudaError_t csr_launch_class(const CsrJob& job, int c, int s, cudaStream_t st);
+// Update of colour class c in sweep s (Eq. 2, Eq. 3) and its energy changes
+// (nchunks = class chunks of kCsrClassChunk spins).
+cudaError_t csr_launch_class(const CsrJob& job, int c, int nchunks, int s, cudaStream_t st);
 // Energy partials of the state `m` ([N][Rw] words); exact FP64 per term when exact != 0.
 cudaError_t csr_launch_energy(const CsrJob& job, const uint32_t* m, int exact, cudaStream_t st);
 // Parallel tempering: exchange of temperatures between adjacent pairs of every
 // chain after sweep s (pairs t = s mod 2, t + 2, ...).
 cudaError_t csr_launch_exchange(const CsrJob& job, int s, cudaStream_t st);
-// Running best after sweep s (init: the initial state), snapshot of improved replicas.
+// Running best after sweep s (init: the initial state, whose energy comes from
+// csr_launch_energy; later sweeps add the class launches' energy changes to the
+// previous energy), snapshot of improved replicas.
 cudaError_t csr_launch_sweep_end(const CsrJob& job, int s, int init, cudaStream_t st);
 // States [R][N] int8 +-1 and energies (from the partials of the same state) of `m`.
 cudaError_t csr_launch_readout(const CsrJob& job, const uint32_t* m, int8_t* out_pm, double* out_E, cudaStream_t st);

@@ -73,6 +73,7 @@ struct pb_instance {
     pb::DevBuf bq_bufs[12];
     // general sparse instance
     int n_colours = 0;
+    std::vector<int32_t> csr_cls_off;  // host copy of the class offsets
     pb::CsrDevice csr{};
     pb::DevBuf csr_bufs[10];
 };
@@ -114,6 +115,7 @@ struct pb_run {
     pb::DevBuf extra[8];
     pb::DevBuf pt[6];      // parallel tempering buffers of a general-graph run
     pb::DevBuf bq_alt[2];  // biclique: the parity-1 live spin buffers of sides A and B
+    std::vector<int32_t> csr_nchunk;  // general graph: class chunks of each colour class
     std::vector<int32_t> bq_win;  // biclique +-1: per beta level, (first index, width, offset) of its threshold window
     std::shared_ptr<pb::BatchShared> batch;
     ~pb_run()
