@@ -19,7 +19,7 @@ LIB = os.path.join(BUILD, "libpbit.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 SOURCES = ["ea.cu", "biclique.cu", "biclique_tc.cu", "noalloc.cu", "host_api.cpp", "biclique_host.cpp", "pool.cpp",
-           "batch.cpp", "server.cpp", "csr.cu", "csr_host.cpp", "imin.cpp", "sparsify.cpp"]
+           "batch.cpp", "server.cpp", "csr.cu", "csr_host.cpp", "imin.cpp", "sparsify.cpp", "biclique_res.cu"]
 
 
 def _nvcc() -> str:

@@ -74,6 +74,8 @@ double est_cost(const pb_instance* I, int R, int S, int form)
     if (I->topo == PB_TOPO_EA3D) return upd / (form == PB_FORM_PLAIN ? 9e10 : 7e11);
     if (I->topo == PB_TOPO_CSR) return upd * std::max(1, I->maxdeg) / 4e11 + 3.0 * std::max(1, S) * 2e-6;
     const double flop = upd * 2.0 * I->n * (I->jtype == PB_J_F32 ? 2.0 : 1.0);
+    if (form == PB_FORM_RESIDENT)  // one CTA per 32 replicas: ~8 us per sweep at n = 256 (+-1), FP32 ~4x slower
+        return std::max(1, S) * 8e-6 * (I->n / 256.0) * (I->n / 256.0) * (I->jtype == PB_J_F32 ? 4.0 : 1.0);
     const double rate = form == PB_FORM_CUDACORE ? 2.5e13 : (I->jtype == PB_J_F32 ? 1.5e15 : 1.8e15);
     // small instances fill a fraction of the tensor tiles
     const double fill = form == PB_FORM_TENSOR ? std::min(1.0, (double)I->n / 256.0) * std::min(1.0, R / 256.0) : 1.0;
@@ -117,7 +119,8 @@ void choose_form(const pb_instance* I, int R, int requested, int& form, int& wt)
         if (form == PB_FORM_AUTO) form = PB_FORM_PLAIN;
     } else {
         if (tuned) form = te.form;
-        if (form == PB_FORM_AUTO) form = PB_FORM_TENSOR;
+        // small instances: the resident form (no launch per half-sweep); else tensor cores
+        if (form == PB_FORM_AUTO) form = bq_resident_fits(I) ? PB_FORM_RESIDENT : PB_FORM_TENSOR;
     }
 }
 
@@ -146,7 +149,7 @@ pb_status batch_start(int count, pb_instance* const* insts, const pb_schedule* s
                 return fail(PB_EUNSUPPORTED, "form not available for EA instances");
         } else if (I->topo == PB_TOPO_CSR) {
             if (form != PB_FORM_PLAIN) return fail(PB_EUNSUPPORTED, "general sparse instances run in the plain form");
-        } else if (form != PB_FORM_TENSOR && form != PB_FORM_CUDACORE) {
+        } else if (form != PB_FORM_TENSOR && form != PB_FORM_CUDACORE && form != PB_FORM_RESIDENT) {
             return fail(PB_EUNSUPPORTED, "form not available for biclique instances");
         }
         jobs.push_back(Job{q, I, replicas[q], scheds[q].n_sweeps, form, wt, est_cost(I, replicas[q], scheds[q].n_sweeps, form)});
@@ -156,11 +159,12 @@ pb_status batch_start(int count, pb_instance* const* insts, const pb_schedule* s
         const int sms = sm_count();
         long long tiles = 0;
         for (const Job& j : jobs)
-            if (j.form == PB_FORM_RESIDENT) tiles += ((j.R + 3) / 4 + j.wt - 1) / j.wt;
+            if (j.form == PB_FORM_RESIDENT && j.I->topo == PB_TOPO_EA3D) tiles += ((j.R + 3) / 4 + j.wt - 1) / j.wt;
         while (tiles > 0 && tiles < sms) {
             Job* wide = nullptr;
             for (Job& j : jobs)
-                if (j.form == PB_FORM_RESIDENT && j.wt > 1 && (!wide || j.wt > wide->wt)) wide = &j;
+                if (j.form == PB_FORM_RESIDENT && j.I->topo == PB_TOPO_EA3D && j.wt > 1 && (!wide || j.wt > wide->wt))
+                    wide = &j;
             if (!wide) break;
             const int Rw = (wide->R + 3) / 4;
             tiles -= (Rw + wide->wt - 1) / wide->wt;
@@ -180,7 +184,7 @@ pb_status batch_start(int count, pb_instance* const* insts, const pb_schedule* s
         pb_status ps;
         if (j.I->topo == PB_TOPO_EA3D) {
             ps = ea_prepare_run(r, j.I, &scheds[j.q], j.R, seeds[j.q], o, j.form, j.wt, st);
-            if (ps == PB_OK && j.form == PB_FORM_RESIDENT) resident.push_back(r);
+            if (ps == PB_OK && j.form == PB_FORM_RESIDENT) resident.push_back(r);  // EA resident: the shared launch
         } else if (j.I->topo == PB_TOPO_CSR) {
             ps = csr_setup(r, j.I, &scheds[j.q], j.R, seeds[j.q], o, st);
         } else {
@@ -200,7 +204,7 @@ pb_status batch_start(int count, pb_instance* const* insts, const pb_schedule* s
         // mostly short launches, bounded by latency more than by SMs -- run
         // beside it instead of after it.
         double ea_cost = 0.0, other = 0.0;
-        for (const Job& j : jobs) (j.form == PB_FORM_RESIDENT ? ea_cost : other) += j.cost;
+        for (const Job& j : jobs) (j.form == PB_FORM_RESIDENT && j.I->topo == PB_TOPO_EA3D ? ea_cost : other) += j.cost;
         if (other > 0.0) {
             const int sms = sm_count();
             const int share = ea_cost >= other ? (3 * sms + 3) / 4 : std::max(sms / 4, (sms + 1) / 2);
@@ -235,7 +239,7 @@ pb_status batch_start(int count, pb_instance* const* insts, const pb_schedule* s
         pb_status ps = start_on(ea_k);
         if (ps != PB_OK) return ps;
         for (const Job& j : jobs)
-            if (j.form == PB_FORM_RESIDENT) {
+            if (j.form == PB_FORM_RESIDENT && j.I->topo == PB_TOPO_EA3D) {
                 load[ea_k] += j.cost;
                 if (costs) (*costs)[j.q] = j.cost;
                 if (stream_of) (*stream_of)[j.q] = ea_k;
@@ -246,7 +250,7 @@ pb_status batch_start(int count, pb_instance* const* insts, const pb_schedule* s
     }
     std::vector<const Job*> rest;
     for (const Job& j : jobs)
-        if (j.form != PB_FORM_RESIDENT) rest.push_back(&j);
+        if (!(j.form == PB_FORM_RESIDENT && j.I->topo == PB_TOPO_EA3D)) rest.push_back(&j);
     std::stable_sort(rest.begin(), rest.end(), [](const Job* a, const Job* b) { return a->cost > b->cost; });
     for (const Job* j : rest) {
         int k = -1;
@@ -317,6 +321,7 @@ pb_status pb_autotune(pb_instance* I, int32_t R, int32_t probe_sweeps, void* str
     } else {
         cand.push_back({PB_FORM_TENSOR, 0});
         cand.push_back({PB_FORM_CUDACORE, 0});
+        if (bq_resident_fits(I)) cand.push_back({PB_FORM_RESIDENT, 0});
     }
     pb_schedule sc{};
     sc.kind = PB_SCHED_LINEAR;
@@ -355,6 +360,8 @@ pb_status pb_autotune(pb_instance* I, int32_t R, int32_t probe_sweeps, void* str
             if (form == PB_FORM_TENSOR) {
                 const int nrp = ((I->n + 127) / 128 + 1) / 2;
                 units = std::min(sms, 2 * nrp * ((R + 255) / 256));
+            } else if (form == PB_FORM_RESIDENT) {
+                units = std::min(sms, (R + 31) / 32);
             } else {
                 units = std::min(sms, ((I->n + 63) / 64) * ((R + 63) / 64));
             }

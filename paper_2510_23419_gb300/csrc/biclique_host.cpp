@@ -167,6 +167,15 @@ pb_status bq_build(pb_instance* I, const pb_instance_desc* d, cudaStream_t st)
     return PB_OK;
 }
 
+bool bq_resident_fits(const pb_instance* I)
+{
+    const int nmax = I->jtype == PB_J_PM1_I8 ? kBqResMaxNpm1 : kBqResMaxNf32;
+    if (I->topo != PB_TOPO_BICLIQUE || I->n > nmax) return false;
+    // the widest threshold window is at most the whole row (2 (n + |h|) + 1 entries)
+    const int tab = I->jtype == PB_J_PM1_I8 ? 2 * (I->n + I->hmax) + 1 : 0;
+    return bq_res_smem_bytes(I->jtype, I->n, tab) <= 227 * 1024;
+}
+
 static pb_status bq_prepare(pb_run* run, pb_instance* I, const pb_schedule* sc, int R, uint64_t seed,
                             const pb_anneal_opts* opts, int form, cudaStream_t st)
 {
@@ -190,8 +199,9 @@ static pb_status bq_prepare(pb_run* run, pb_instance* I, const pb_schedule* sc, 
     j.step = step;
     j.R = R;
     const bool tensor = form == PB_FORM_TENSOR;
+    const bool resident = form == PB_FORM_RESIDENT;
     run->form = form;
-    j.Rpad = round_up(R, tensor ? kBqTcReps : kBqTileReps);
+    j.Rpad = round_up(R, tensor ? kBqTcReps : (resident ? kBqResReps : kBqTileReps));
     j.ld = round_up(n, 16);
     j.nblk = (n + (tensor ? kBqTcRows : kBqTileRows) - 1) / (tensor ? kBqTcRows : kBqTileRows);
     if (tensor) j.nblk = (j.nblk + 1) & ~1;  // row tiles come in clusters of two
@@ -205,6 +215,7 @@ static pb_status bq_prepare(pb_run* run, pb_instance* I, const pb_schedule* sc, 
         int wmax = 0;
         for (int l = 0; l < nlev; ++l) wmax = std::max(wmax, run->bq_win[3 * l + 1]);
         j.tabmode = wmax <= kBqTcWindowMax ? 2 : (wmax * 4 <= 33 * 1024 ? 1 : 0);
+        run->res_tab = wmax;
         PB_ALLOC(run->extra[7], run->bq_win.size() * 4);
         PB_CUDA_TRY(cudaMemcpyAsync(run->extra[7].p, run->bq_win.data(), run->bq_win.size() * 4, cudaMemcpyHostToDevice, st));
         j.win = run->extra[7].as<int32_t>();
@@ -272,6 +283,10 @@ static pb_status bq_prepare(pb_run* run, pb_instance* I, const pb_schedule* sc, 
                                            kBqTcReps / 2));  // half a tile per cluster CTA
         PB_CUDA_TRY(bq_tc_set_smem());
     }
+    if (resident) {
+        run->res_smem = bq_res_smem_bytes(I->jtype, n, pm1 ? run->res_tab : 0);
+        PB_CUDA_TRY(bq_res_set_smem(I->jtype, run->res_smem));
+    }
     PB_CUDA_TRY(cudaEventCreate(&run->ev_start));
     PB_CUDA_TRY(cudaEventCreate(&run->ev_stop));
     PB_CUDA_TRY(cudaEventCreate(&run->ev_k0));
@@ -327,8 +342,10 @@ pb_status bq_setup(pb_run* run, pb_instance* I, const pb_schedule* sc, int R, ui
 {
     int form = opts ? opts->form : PB_FORM_AUTO;
     if (form == PB_FORM_AUTO) form = PB_FORM_TENSOR;
-    if (form != PB_FORM_TENSOR && form != PB_FORM_CUDACORE)
+    if (form != PB_FORM_TENSOR && form != PB_FORM_CUDACORE && form != PB_FORM_RESIDENT)
         return fail(PB_EUNSUPPORTED, "form not available for biclique instances");
+    if (form == PB_FORM_RESIDENT && !bq_resident_fits(I))
+        return fail(PB_EUNSUPPORTED, "biclique too large for the resident form (n <= 256 for +-1, n <= 128 for F32)");
     return bq_prepare(run, I, sc, R, seed, opts, form, st);
 }
 
@@ -337,8 +354,24 @@ pb_status bq_setup(pb_run* run, pb_instance* I, const pb_schedule* sc, int R, ui
 // when the stream cannot be captured), then the readout.  The sweep index lives
 // in device memory, so the chunk is the same for every part of the anneal and
 // the host work does not grow with the number of sweeps.
+// Resident form: the whole anneal in one launch, then the readout.
+static pb_status bq_launch_resident(pb_run* run, cudaStream_t st)
+{
+    const BqJob& j = run->bjob;
+    PB_CUDA_TRY(cudaEventRecord(run->ev_start, st));
+    PB_CUDA_TRY(cudaEventRecord(run->ev_k0, st));
+    PB_CUDA_TRY(bq_launch_res(j, j.inst.jtype == PB_J_PM1_I8 ? run->res_tab : 0, run->res_smem, st));
+    PB_CUDA_TRY(cudaEventRecord(run->ev_k1, st));
+    const int last = (j.S - 1) & 1;
+    PB_CUDA_TRY(bq_launch_readout(bq_view(j, 0, last, last), 0, run->final_pm.as<int8_t>(), run->E_out.as<double>(), st));
+    PB_CUDA_TRY(bq_launch_readout(j, 1, run->best_pm.as<int8_t>(), run->E_out.as<double>() + run->R, st));
+    PB_CUDA_TRY(cudaEventRecord(run->ev_stop, st));
+    return PB_OK;
+}
+
 pb_status bq_launch(pb_run* run, cudaStream_t st)
 {
+    if (run->form == PB_FORM_RESIDENT) return bq_launch_resident(run, st);
     const BqJob& j = run->bjob;
     PB_CUDA_TRY(cudaEventRecord(run->ev_start, st));
     PB_CUDA_TRY(cudaMemsetAsync(run->dev_err + 2, 0, 2 * sizeof(int32_t), st));

@@ -56,10 +56,19 @@ struct BqJob {
     int32_t tabmode;        // tensor form: where the decisions read the windows (widest level decides)
 };
 
+constexpr int kBqResReps = 32;      // resident form: replicas per CTA
+constexpr int kBqResMaxNpm1 = 256;  // resident form: largest n (+-1 couplings, int8 J in shared memory)
+constexpr int kBqResMaxNf32 = 128;  // resident form: largest n (real couplings, FP32 J in shared memory)
+
 constexpr int kBqTileRows = 64;   // CUDA-core field kernel: rows (spins of the updated side) per block
 constexpr int kBqTileReps = 64;   // replicas per block
 
 cudaError_t bq_launch_init(const BqJob& job, cudaStream_t st);
+// Resident form: the whole anneal of every 32-replica block in one CTA (grid
+// Rpad / 32); tab_cap = the widest threshold window of the run (+-1).
+size_t bq_res_smem_bytes(int jtype, int n, int tab_cap);
+cudaError_t bq_res_set_smem(int jtype, size_t bytes);
+cudaError_t bq_launch_res(const BqJob& job, int tab_cap, size_t smem, cudaStream_t st);
 // Field + decision of one side (side 0 = A uses J, side 1 = B uses J^T).
 // decide = 0: no update, only the energy partials of the current state.
 // fields_out != null: write F[r][side*n + i] (row stride 2n) and change nothing.

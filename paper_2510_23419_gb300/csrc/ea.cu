@@ -13,6 +13,8 @@
 //    plus one energy/best launch per sweep.
 #include "ea_fast.cuh"
 #include "ea_kernels.cuh"
+#include <mutex>
+
 #include "ea_launch.h"
 
 namespace pb {
@@ -767,9 +769,21 @@ int ea_resident_pick_wt(int L, int jtype, int has_h, int nF, int cap_words)
     return best;
 }
 
+// The limit is a property of the kernel, shared by every run of the process
+// on a device: it only grows, so preparing a run never lowers the limit that
+// another prepared run will launch with.
 cudaError_t ea_resident_set_smem(size_t smem)
 {
-    return cudaFuncSetAttribute(ea_resident_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static std::mutex mu;
+    static size_t current[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(mu);
+    size_t* cur = (dev >= 0 && dev < 64) ? &current[dev] : nullptr;
+    if (cur && smem <= *cur) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(ea_resident_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess && cur) *cur = smem;
+    return e;
 }
 
 cudaError_t ea_launch_resident(const EaJob* d_jobs, const EaWork* d_work, int n_work, int* d_counter, size_t smem,

@@ -116,6 +116,8 @@ struct pb_run {
     pb::DevBuf pt[6];      // parallel tempering buffers of a general-graph run
     pb::DevBuf bq_alt[2];  // biclique: the parity-1 live spin buffers of sides A and B
     std::vector<int32_t> csr_nchunk;  // general graph: class chunks of each colour class
+    int res_tab = 0;                  // biclique resident form: widest threshold window
+    size_t res_smem = 0;              // biclique resident form: dynamic shared memory per CTA
     std::vector<int32_t> bq_win;  // biclique +-1: per beta level, (first index, width, offset) of its threshold window
     std::shared_ptr<pb::BatchShared> batch;
     ~pb_run()
@@ -149,6 +151,7 @@ int ea_choose_wt(const pb_instance* I, int R, int nF);
 pb_status bq_setup(pb_run* run, pb_instance* I, const pb_schedule* sc, int R, uint64_t seed,
                    const pb_anneal_opts* opts, cudaStream_t st);
 pb_status bq_launch(pb_run* run, cudaStream_t st);
+bool bq_resident_fits(const pb_instance* I);
 pb_status csr_build(pb_instance* I, int32_t N, int64_t n_edges, const int32_t* eu, const int32_t* ev, int jtype,
                     const void* J, const void* h, const int32_t* colour, cudaStream_t st);
 pb_status csr_setup(pb_run* run, pb_instance* I, const pb_schedule* sc, int R, uint64_t seed,

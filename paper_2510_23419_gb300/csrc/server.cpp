@@ -57,8 +57,8 @@ int64_t footprint_bytes(const pb_instance* I, const pb_schedule* sc, int R, cons
         return 2 * N * Rw * 4 + (N + kCsrChunk - 1) / kCsrChunk * 4 * Rw * 8 + 4 * Rw * 20 + nlev * nF * 4 + out + 4096;
     }
     const int64_t n = I->n;
-    const bool tensor = form != PB_FORM_CUDACORE;
-    const int64_t tile = tensor ? kBqTcReps : kBqTileReps;
+    const bool tensor = form == PB_FORM_TENSOR;
+    const int64_t tile = tensor ? kBqTcReps : (form == PB_FORM_RESIDENT ? kBqResReps : kBqTileReps);
     const int64_t Rpad = (R + tile - 1) / tile * tile;
     const int64_t ld = (n + 15) / 16 * 16;
     const int64_t esz = I->jtype == PB_J_PM1_I8 ? 1 : 2;

@@ -139,7 +139,7 @@ def test_autotune_records_choice(pb):
     binst, bsc, bR, bseed, _ = _make(pb, JOBS[2])
     try:
         t = pb.pb_autotune(binst, bR, 4)
-        assert t.form in (pb.PB_FORM_TENSOR, pb.PB_FORM_CUDACORE) and t.n_candidates == 2
+        assert t.form in (pb.PB_FORM_TENSOR, pb.PB_FORM_CUDACORE, pb.PB_FORM_RESIDENT) and t.n_candidates == 3
     finally:
         pb.pb_autotune_clear()
         pb.pb_instance_destroy(binst)

@@ -14,7 +14,8 @@ import synth_inputs as syn
 
 pytestmark = pytest.mark.gpu
 
-FORMS = ["cudacore", "tensor"]
+FORMS = ["cudacore", "tensor", "resident"]   # anneal forms
+FIELD_FORMS = ["cudacore", "tensor"]         # forms with a field entry point
 
 
 @pytest.fixture(scope="module")
@@ -26,7 +27,7 @@ def pb():
 
 
 def _form(pb, name):
-    return {"cudacore": pb.PB_FORM_CUDACORE, "tensor": pb.PB_FORM_TENSOR}[name]
+    return {"cudacore": pb.PB_FORM_CUDACORE, "tensor": pb.PB_FORM_TENSOR, "resident": pb.PB_FORM_RESIDENT}[name]
 
 
 def _gpu(pb, n, J, h, sc, R, seed, form):
@@ -74,7 +75,7 @@ def test_ferromagnet_closed_form(pb, form):
     assert np.all(g["best_E"] == -n * n)
 
 
-@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("form", FIELD_FORMS)
 @pytest.mark.parametrize("n", [96, 300])
 def test_f32_fields(pb, orc, form, n):
     J = syn.biclique_couplings(n, "gauss", 11)
@@ -112,7 +113,7 @@ def test_f32_energies_and_ensemble(pb, orc, form):
     assert abs(eg.mean() - eo.mean()) <= 3 * se + 1e-12
 
 
-@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("form", FIELD_FORMS)
 def test_pm1_fields_exact(pb, orc, form):
     n = 160
     J = syn.biclique_couplings(n, "pm1", 31)
@@ -159,3 +160,20 @@ def test_tensor_threshold_row_in_global_memory(pb, orc):
         o = orc.anneal(eu, ev, Jd, None, col, ob, 1, 19, r_first=r)
         assert np.array_equal(o["final_state"][0], g["final_state"][r])
         assert o["best_E"][0] == g["best_E"][r] and o["best_sweep"][0] == g["best_sweep"][r]
+
+
+def test_resident_limits_and_blocks(pb, orc):
+    """Resident form: ragged replica counts over several 32-replica CTAs, bit-exact; too
+    large an instance is refused."""
+    n, R, S = 256, 70, 12
+    J = syn.biclique_couplings(n, "pm1", 61)
+    h = syn.int_fields(2 * n, 2, 62)
+    sc = pb.make_schedule(pb.PB_SCHED_LINEAR, S, 0.35, 3.5)
+    g = _gpu(pb, n, J, h, sc, R, 63, "resident")
+    o = _orc(orc, n, J, h, orc.schedule(orc.SCHED_LINEAR, 0.35, 3.5, S), R, 63)
+    for k in ("final_state", "best_state", "final_E", "best_E", "best_sweep"):
+        assert np.array_equal(g[k], o[k]), k
+    with pytest.raises(pb.PbError, match="PB_EUNSUPPORTED"):
+        _gpu(pb, 300, syn.biclique_couplings(300, "pm1", 1), None, sc, 4, 1, "resident")
+    with pytest.raises(pb.PbError, match="PB_EUNSUPPORTED"):
+        _gpu(pb, 160, syn.biclique_couplings(160, "gauss", 1), None, sc, 4, 1, "resident")
