@@ -208,7 +208,7 @@ pb_status batch_start(int count, pb_instance* const* insts, const pb_schedule* s
         if (other > 0.0) {
             const int sms = sm_count();
             const int share = ea_cost >= other ? (3 * sms + 3) / 4 : std::max(sms / 4, (sms + 1) / 2);
-            ea_shared->grid = std::max(1, std::min(ea_shared->grid, share));
+            ea_batch_limit_sms(*ea_shared, share);
         }
     }
 

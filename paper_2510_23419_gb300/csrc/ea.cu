@@ -376,9 +376,18 @@ __device__ void ea_tile(const EaJob& job, int tile, unsigned char* smem)
     __syncthreads();
 }
 
+// One persistent kernel per coupling type: a kernel holding both types' tiles
+// gets one register allocation for all of them, and the FP32 tiles' pressure
+// then costs the +-1 tiles spill traffic.  The tile code comes with the work
+// item (a branch on the job's own fields also led the compiler to spill).
+// Every CTA lets a programmatically dependent launch (the other type's kernel
+// of the same batch) start at once, so that kernel's CTAs take the SMs this
+// one leaves as its list runs out.
+template <int JT>
 __global__ void __launch_bounds__(kResidentThreads, 1)
     ea_resident_kernel(const EaJob* __restrict__ jobs, const EaWork* __restrict__ work, int n_work, int* counter)
 {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ int s_item;
     for (;;) {
@@ -389,24 +398,23 @@ __global__ void __launch_bounds__(kResidentThreads, 1)
         if (item >= n_work) break;
         const EaWork wk = work[item];
         const EaJob& job = jobs[wk.job];
-        const int L = job.inst.L, WT = job.WT;
-        if (job.inst.jtype == PB_J_PM1_I8) {
-            if (job.inst.has_h)
+        if constexpr (JT == PB_J_PM1_I8) {
+            if (wk.path == kEaPathFieldsGeneric)
                 ea_tile<0, 0, PB_J_PM1_I8, true>(job, wk.tile, smem);
-            else if (L == 32 && WT == 1)
+            else if (wk.path == kEaPathFast32)
                 ea_tile_fast<32, 1, PB_J_PM1_I8>(job, wk.tile, smem);
-            else if (L == 16 && WT == 4)
+            else if (wk.path == kEaPathFast16)
                 ea_tile_fast<16, 4, PB_J_PM1_I8>(job, wk.tile, smem);
-            else if (L == 8 && WT == 16)
+            else if (wk.path == kEaPathFast8)
                 ea_tile_fast<8, 16, PB_J_PM1_I8>(job, wk.tile, smem);
             else
                 ea_tile<0, 0, PB_J_PM1_I8, false>(job, wk.tile, smem);
         } else {
-            if (L == 32 && WT == 1)
+            if (wk.path == kEaPathFast32)
                 ea_tile_fast<32, 1, PB_J_F32>(job, wk.tile, smem);
-            else if (L == 16 && WT == 4)
+            else if (wk.path == kEaPathFast16)
                 ea_tile_fast<16, 4, PB_J_F32>(job, wk.tile, smem);
-            else if (L == 8 && WT == 16)
+            else if (wk.path == kEaPathFast8)
                 ea_tile_fast<8, 16, PB_J_F32>(job, wk.tile, smem);
             else
                 ea_tile<0, 0, PB_J_F32, false>(job, wk.tile, smem);
@@ -772,25 +780,41 @@ int ea_resident_pick_wt(int L, int jtype, int has_h, int nF, int cap_words)
 // The limit is a property of the kernel, shared by every run of the process
 // on a device: it only grows, so preparing a run never lowers the limit that
 // another prepared run will launch with.
-cudaError_t ea_resident_set_smem(size_t smem)
+cudaError_t ea_resident_set_smem(int jtype, size_t smem)
 {
     static std::mutex mu;
-    static size_t current[64] = {};
+    static size_t current[2][64] = {};
     int dev = 0;
     cudaGetDevice(&dev);
+    const int t = jtype == PB_J_F32 ? 1 : 0;
     std::lock_guard<std::mutex> lock(mu);
-    size_t* cur = (dev >= 0 && dev < 64) ? &current[dev] : nullptr;
+    size_t* cur = (dev >= 0 && dev < 64) ? &current[t][dev] : nullptr;
     if (cur && smem <= *cur) return cudaSuccess;
-    const cudaError_t e = cudaFuncSetAttribute(ea_resident_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const cudaError_t e =
+        t ? cudaFuncSetAttribute(ea_resident_kernel<PB_J_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+          : cudaFuncSetAttribute(ea_resident_kernel<PB_J_PM1_I8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess && cur) *cur = smem;
     return e;
 }
 
-cudaError_t ea_launch_resident(const EaJob* d_jobs, const EaWork* d_work, int n_work, int* d_counter, size_t smem,
-                               int grid, cudaStream_t st)
+cudaError_t ea_launch_resident(int jtype, const EaJob* d_jobs, const EaWork* d_work, int n_work, int* d_counter,
+                               size_t smem, int grid, bool after_previous, cudaStream_t st)
 {
-    ea_resident_kernel<<<grid, kResidentThreads, smem, st>>>(d_jobs, d_work, n_work, d_counter);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kResidentThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    if (after_previous) {
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+    }
+    return jtype == PB_J_F32 ? cudaLaunchKernelEx(&cfg, ea_resident_kernel<PB_J_F32>, d_jobs, d_work, n_work, d_counter)
+                             : cudaLaunchKernelEx(&cfg, ea_resident_kernel<PB_J_PM1_I8>, d_jobs, d_work, n_work,
+                                                  d_counter);
 }
 
 static unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }

@@ -39,6 +39,16 @@ __device__ __forceinline__ uint32_t ea_popc6_bytes(uint32_t y)
 // Decision of one replica: new spin bit (1 <=> m = -1) is 1 unless r < T.
 __device__ __forceinline__ uint32_t decide_bit(uint32_t r, uint32_t T) { return r >= T ? 1u : 0u; }
 
+// 2^x on the special-function unit, results below 2^-126 flushed to zero.
+// In the decision below a flushed e cannot change the outcome: u >= 2^-24,
+// so u + u e rounds to u < 1 for every e < 2^-126.
+__device__ __forceinline__ float ex2_ftz(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // FP32 decision of the F32 path (Eq. 2): m = +1 with probability
 // P = 1/2 + tanh(beta F)/2 = 1 / (1 + e^{-2 beta F}).  The word r gives
 // u = ((r >> 9) + 1/2) 2^-23, the comparison u < P is evaluated as
@@ -48,7 +58,7 @@ __device__ __forceinline__ uint32_t decide_bit(uint32_t r, uint32_t T) { return 
 __device__ __forceinline__ uint32_t decide_f32(uint32_t r, float F, float cexp)
 {
     const float u = __uint_as_float(0x3F800000u | (r >> 9)) - 0.99999994f;
-    const float e = exp2f(cexp * F);
+    const float e = ex2_ftz(cexp * F);
     return fmaf(u, e, u) >= 1.0f ? 1u : 0u;
 }
 

@@ -32,10 +32,30 @@ struct EaJob {
     int32_t* hit_sweep;       // [n_tiles*4*WT]
 };
 
+// Tile code of the resident kernels (chosen on the host, so the kernel
+// branches on one word of the work item).
+enum EaTilePath : int32_t {
+    kEaPathFieldsGeneric = 0,  // +-1 couplings with integer fields: generic tile
+    kEaPathFast32 = 1,         // compile-time tile L = 32, WT = 1
+    kEaPathFast16 = 2,         // L = 16, WT = 4
+    kEaPathFast8 = 3,          // L = 8, WT = 16
+    kEaPathGeneric = 4,        // any other even L <= 32
+};
+
 struct EaWork {
     int32_t job;
     int32_t tile;
+    int32_t path;  // EaTilePath of the job
 };
+
+inline int32_t ea_tile_path(const EaJob& j)
+{
+    if (j.inst.jtype == PB_J_PM1_I8 && j.inst.has_h) return kEaPathFieldsGeneric;
+    if (j.inst.L == 32 && j.WT == 1) return kEaPathFast32;
+    if (j.inst.L == 16 && j.WT == 4) return kEaPathFast16;
+    if (j.inst.L == 8 && j.WT == 16) return kEaPathFast8;
+    return kEaPathGeneric;
+}
 
 // Shared memory of one resident tile, in bytes.
 __host__ __device__ inline size_t ea_resident_smem(int L, int WT, int jtype, int has_h, int nF)
@@ -70,10 +90,15 @@ constexpr size_t kResidentSmemLimit = 227 * 1024;
 // z parity, per column) and the tile fits shared memory; 0 if none.
 int ea_resident_pick_wt(int L, int jtype, int has_h, int nF, int cap_words);
 
-// Opt the persistent kernel into `smem` bytes of dynamic shared memory (outside any capture).
-cudaError_t ea_resident_set_smem(size_t smem);
-cudaError_t ea_launch_resident(const EaJob* d_jobs, const EaWork* d_work, int n_work, int* d_counter, size_t smem,
-                               int grid, cudaStream_t st);
+// Opt the persistent kernel of coupling type `jtype` into `smem` bytes of
+// dynamic shared memory (outside any capture).
+cudaError_t ea_resident_set_smem(int jtype, size_t smem);
+// Persistent kernel of coupling type `jtype` over n_work items (all of that
+// type).  after_previous: programmatic dependent launch on the kernel launched
+// just before it on `st` (its CTAs start as that kernel's CTAs leave; the
+// caller orders any later consumer after both).
+cudaError_t ea_launch_resident(int jtype, const EaJob* d_jobs, const EaWork* d_work, int n_work, int* d_counter,
+                               size_t smem, int grid, bool after_previous, cudaStream_t st);
 cudaError_t ea_launch_plain_init(const EaJob& job, cudaStream_t st);
 cudaError_t ea_launch_plain_sweep(const EaJob& job, int s, cudaStream_t st);
 cudaError_t ea_launch_plain_energy(const EaJob& job, int s, bool init, cudaStream_t st);

@@ -385,27 +385,49 @@ struct TileCost {
     double cost;
 };
 
-// One persistent launch for all jobs: tiles ordered longest first.  Set-up
-// (device arrays of jobs and work items) and launch are separate so that a
-// batch can prepare all of its jobs before any of them starts.
+// One persistent kernel per coupling type present, tiles ordered longest
+// first inside each; the kernels run as a chain of programmatic dependent
+// launches (the group holding the longest tile first), so the second one's
+// CTAs take the SMs the first one leaves.  Set-up (device arrays of jobs and
+// work items) and launch are separate so that a batch can prepare all of its
+// jobs before any of them starts.
 pb_status ea_batch_setup(std::vector<pb_run*>& runs, cudaStream_t st, std::shared_ptr<BatchShared>& out)
 {
     auto shared = std::make_shared<BatchShared>();
     PB_CUDA_TRY(cudaEventCreate(&shared->ev_k0));
     PB_CUDA_TRY(cudaEventCreate(&shared->ev_k1));
     std::vector<EaJob> jobs;
-    std::vector<TileCost> tiles;
-    size_t smem = 0;
+    std::vector<TileCost> tiles[2];
+    EaGroup grp[2];
     for (size_t q = 0; q < runs.size(); ++q) {
         const EaJob& j = runs[q]->job;
         jobs.push_back(j);
-        smem = std::max(smem, ea_resident_smem(j.inst.L, j.WT, j.inst.jtype, j.inst.has_h, j.nF));
-        const double per = (double)j.inst.N * 4.0 * j.WT * std::max(1, j.S) * (j.inst.jtype == PB_J_F32 ? 1.8 : 1.0);
-        for (int t = 0; t < j.n_tiles; ++t) tiles.push_back({(int)q, t, per});
+        const int t = j.inst.jtype == PB_J_F32 ? 1 : 0;
+        grp[t].jtype = j.inst.jtype;
+        grp[t].smem = std::max(grp[t].smem, ea_resident_smem(j.inst.L, j.WT, j.inst.jtype, j.inst.has_h, j.nF));
+        const double per = (double)j.inst.N * 4.0 * j.WT * std::max(1, j.S) * (t ? 1.8 : 1.0);
+        for (int k = 0; k < j.n_tiles; ++k) tiles[t].push_back({(int)q, k, per});
+        grp[t].cost += per * j.n_tiles;
+        grp[t].longest = std::max(grp[t].longest, per);
     }
-    std::stable_sort(tiles.begin(), tiles.end(), [](const TileCost& a, const TileCost& b) { return a.cost > b.cost; });
-    std::vector<EaWork> work(tiles.size());
-    for (size_t t = 0; t < tiles.size(); ++t) work[t] = EaWork{tiles[t].job, tiles[t].tile};
+    std::vector<int> order;
+    for (int t = 0; t < 2; ++t)
+        if (!tiles[t].empty()) order.push_back(t);
+    if (order.size() == 2 && grp[1].longest > grp[0].longest) std::swap(order[0], order[1]);
+    std::vector<EaWork> work;
+    const int sms = sm_count();
+    for (int t : order) {
+        std::stable_sort(tiles[t].begin(), tiles[t].end(),
+                         [](const TileCost& a, const TileCost& b) { return a.cost > b.cost; });
+        grp[t].offset = (int)work.size();
+        grp[t].n = (int)tiles[t].size();
+        grp[t].grid = std::max(1, std::min(grp[t].n, sms));
+        for (const TileCost& c : tiles[t]) work.push_back(EaWork{c.job, c.tile, ea_tile_path(jobs[(size_t)c.job])});
+        shared->groups.push_back(grp[t]);
+        cudaEvent_t e = nullptr;
+        PB_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        shared->ev_group.push_back(e);
+    }
     PB_ALLOC(shared->jobs, jobs.size() * sizeof(EaJob));
     PB_ALLOC(shared->work, work.size() * sizeof(EaWork));
     PB_ALLOC(shared->counter, 16);
@@ -413,17 +435,35 @@ pb_status ea_batch_setup(std::vector<pb_run*>& runs, cudaStream_t st, std::share
     PB_CUDA_TRY(cudaMemcpyAsync(shared->work.p, work.data(), work.size() * sizeof(EaWork), cudaMemcpyHostToDevice, st));
     PB_CUDA_TRY(cudaStreamSynchronize(st));
     shared->n_work = (int)work.size();
-    shared->grid = std::max(1, std::min<int>((int)work.size(), sm_count()));
-    shared->smem = smem;
-    PB_CUDA_TRY(ea_resident_set_smem(smem));
+    for (const EaGroup& g : shared->groups) PB_CUDA_TRY(ea_resident_set_smem(g.jtype, g.smem));
     out = shared;
     return PB_OK;
 }
 
+void ea_batch_limit_sms(BatchShared& shared, int sms)
+{
+    double total = 0.0;
+    for (const EaGroup& g : shared.groups) total += g.cost;
+    const int ng = (int)shared.groups.size();
+    int left = std::max(ng, sms);
+    for (int k = 0; k < ng; ++k) {
+        EaGroup& g = shared.groups[(size_t)k];
+        const int later = ng - k - 1;  // at least one SM for each later group
+        const int share = later == 0 ? left
+                                     : std::max(1, std::min(left - later, (int)std::lround(sms * g.cost /
+                                                                                             std::max(total, 1e-30))));
+        g.grid = std::max(1, std::min(g.grid, share));
+        left -= g.grid;
+    }
+}
+
 pb_status ea_batch_launch(std::vector<pb_run*>& runs, const std::shared_ptr<BatchShared>& shared, cudaStream_t st)
 {
-    // The launch sequence (counter reset, persistent kernel, readouts) is
-    // captured into a CUDA graph when the stream allows capture.
+    // The launch sequence (counter reset, persistent kernels, readouts) is
+    // captured into a CUDA graph when the stream allows capture.  Inside the
+    // capture the kernels after the first are programmatic dependents of the
+    // one before, and the readouts wait for every kernel; without a capture
+    // the kernels simply run one after the other.
     const bool capture = st != nullptr && st != cudaStreamLegacy && st != cudaStreamPerThread;
     cudaGraph_t graph = nullptr;
     PB_CUDA_TRY(cudaEventRecord(runs[0]->ev_start, st));
@@ -433,8 +473,15 @@ pb_status ea_batch_launch(std::vector<pb_run*>& runs, const std::shared_ptr<Batc
         // inside a capture an event becomes a graph node only when recorded as external
         const unsigned evf = capture ? cudaEventRecordExternal : cudaEventRecordDefault;
         PB_CUDA_TRY(cudaEventRecordWithFlags(shared->ev_k0, st, evf));
-        PB_CUDA_TRY(ea_launch_resident(shared->jobs.as<EaJob>(), shared->work.as<EaWork>(), shared->n_work,
-                                       shared->counter.as<int>(), shared->smem, shared->grid, st));
+        for (size_t k = 0; k < shared->groups.size(); ++k) {
+            const EaGroup& g = shared->groups[k];
+            PB_CUDA_TRY(ea_launch_resident(g.jtype, shared->jobs.as<EaJob>(), shared->work.as<EaWork>() + g.offset, g.n,
+                                           shared->counter.as<int>() + k, g.smem, g.grid, capture && k > 0, st));
+            if (capture) PB_CUDA_TRY(cudaEventRecord(shared->ev_group[k], st));
+        }
+        if (capture)
+            for (size_t k = 0; k + 1 < shared->groups.size(); ++k)
+                PB_CUDA_TRY(cudaStreamWaitEvent(st, shared->ev_group[k], 0));
         PB_CUDA_TRY(cudaEventRecordWithFlags(shared->ev_k1, st, evf));
         for (pb_run* r : runs) {
             pb_status ps = ea_enqueue_readout(r, st);

@@ -156,7 +156,7 @@ extern "C" pb_status pb_anneal_ea_noalloc(int32_t L, const int8_t* J_dev, const 
     j.best_sweep = reinterpret_cast<int32_t*>(S + o_bs);
     j.hit_sweep = reinterpret_cast<int32_t*>(S + o_hit);
     std::vector<EaWork> work(n_tiles);
-    for (int t = 0; t < n_tiles; ++t) work[t] = EaWork{0, t};
+    for (int t = 0; t < n_tiles; ++t) work[t] = EaWork{0, t, ea_tile_path(j)};
 
     // Every call reuses the same array: reset what must start at zero (the tile
     // counter); everything else is overwritten before it is read.
@@ -173,9 +173,10 @@ extern "C" pb_status pb_anneal_ea_noalloc(int32_t L, const int8_t* J_dev, const 
     if (bad_h) return fail(PB_EINVAL, "PM1 couplings must be +1 or -1");
 
     const size_t smem = ea_resident_smem(L, WT, PB_J_PM1_I8, 0, nF);
-    PB_CUDA_TRY(ea_resident_set_smem(smem));
-    PB_CUDA_TRY(ea_launch_resident(reinterpret_cast<const EaJob*>(S + o_job), reinterpret_cast<const EaWork*>(S + o_work),
-                                   n_tiles, reinterpret_cast<int*>(S + o_ctr), smem, std::min(n_tiles, sms), st));
+    PB_CUDA_TRY(ea_resident_set_smem(PB_J_PM1_I8, smem));
+    PB_CUDA_TRY(ea_launch_resident(PB_J_PM1_I8, reinterpret_cast<const EaJob*>(S + o_job),
+                                   reinterpret_cast<const EaWork*>(S + o_work), n_tiles, reinterpret_cast<int*>(S + o_ctr),
+                                   smem, std::min(n_tiles, sms), false, st));
     PB_CUDA_TRY(ea_launch_readout(j, j.final_words, final_states_dev, final_E_dev, st));
     PB_CUDA_TRY(ea_launch_readout(j, j.best_words, best_states_dev, best_E_dev, st));
     PB_CUDA_TRY(cudaMemcpyAsync(best_sweep_dev, j.best_sweep, (size_t)replicas * 4, cudaMemcpyDeviceToDevice, st));

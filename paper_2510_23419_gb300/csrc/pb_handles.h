@@ -79,19 +79,31 @@ struct pb_instance {
 };
 
 namespace pb {
+// Tiles of one coupling type in a shared EA launch: work[offset, offset + n),
+// counter word `group`, one persistent kernel of `grid` CTAs.
+struct EaGroup {
+    int jtype = 0, offset = 0, n = 0, grid = 0;
+    size_t smem = 0;
+    double cost = 0.0, longest = 0.0;  // estimated SM-time of all tiles / of the longest tile
+};
+
 struct BatchShared {
     DevBuf jobs, work, counter;
-    int n_work = 0, grid = 0;
-    size_t smem = 0;
+    int n_work = 0;
+    std::vector<EaGroup> groups;  // launch order: the group holding the longest tile first
     cudaGraphExec_t exec = nullptr;
-    cudaEvent_t ev_k0 = nullptr, ev_k1 = nullptr;  // around the shared persistent launch
+    cudaEvent_t ev_k0 = nullptr, ev_k1 = nullptr;  // around the shared persistent launches
+    std::vector<cudaEvent_t> ev_group;             // after each group's launch (joins inside the capture)
     ~BatchShared()
     {
         if (exec) cudaGraphExecDestroy(exec);
         if (ev_k0) cudaEventDestroy(ev_k0);
         if (ev_k1) cudaEventDestroy(ev_k1);
+        for (cudaEvent_t e : ev_group)
+            if (e) cudaEventDestroy(e);
     }
 };
+
 }  // namespace pb
 
 struct pb_run {
@@ -147,6 +159,9 @@ pb_status ea_prepare_run(pb_run* run, pb_instance* I, const pb_schedule* sc, int
 pb_status ea_enqueue_plain(pb_run* run, cudaStream_t st);
 pb_status ea_batch_setup(std::vector<pb_run*>& runs, cudaStream_t st, std::shared_ptr<BatchShared>& out);
 pb_status ea_batch_launch(std::vector<pb_run*>& runs, const std::shared_ptr<BatchShared>& shared, cudaStream_t st);
+// Keep the EA kernels of a shared launch within `sms` SMs in total (split over
+// the coupling-type groups in proportion to their work).
+void ea_batch_limit_sms(BatchShared& shared, int sms);
 int ea_choose_wt(const pb_instance* I, int R, int nF);
 pb_status bq_setup(pb_run* run, pb_instance* I, const pb_schedule* sc, int R, uint64_t seed,
                    const pb_anneal_opts* opts, cudaStream_t st);
