@@ -248,25 +248,45 @@ __global__ void __launch_bounds__(256) bq_sweep_end_kernel(BqJob job, int s_arg,
     if (sp_write && blockIdx.x == 0 && threadIdx.x == 0) *sp_write = s + 1;  // read by the next sweep's launches
     if (!init && s >= job.S) return;
     __shared__ int s_copy[kEndReps];
+    constexpr int kSub = 8;  // partial-row subsets, one per warp
+    __shared__ int32_t s_pi[kSub][kEndReps];
+    __shared__ float s_pf[kSub][kEndReps];
     const int r0 = blockIdx.x * kEndReps;
     const bool pm1 = job.inst.jtype == PB_J_PM1_I8;
+    {
+        // warp k adds the partial rows b = k, k + 8, ... of both sides for the
+        // block's 32 replicas (coalesced across replicas); the 8 subset sums are
+        // then added in the fixed order k = 0..7
+        const int k = threadIdx.x >> 5, r = r0 + (threadIdx.x & 31);
+        const int rows = 2 * job.nblk;
+        if (pm1) {
+            const int32_t* p = static_cast<const int32_t*>(job.part);
+            int32_t E = 0;
+            for (int b = k; b < rows; b += kSub) E += p[(size_t)b * job.Rpad + r];
+            s_pi[k][threadIdx.x & 31] = E;
+        } else {
+            const float* p = static_cast<const float*>(job.part);
+            float E = 0.0f;
+            for (int b = k; b < rows; b += kSub) E += p[(size_t)b * job.Rpad + r];
+            s_pf[k][threadIdx.x & 31] = E;
+        }
+    }
+    __syncthreads();
     if (threadIdx.x < kEndReps) {
         const int r = r0 + threadIdx.x;
         bool imp;
         const int prev = init ? -2 : job.best_sweep[r];
         if (pm1) {
-            const int32_t* p = static_cast<const int32_t*>(job.part);
             int32_t E = 0;
-            for (int side = 0; side < 2; ++side)
-                for (int b = 0; b < job.nblk; ++b) E += p[((size_t)side * job.nblk + b) * job.Rpad + r];
+#pragma unroll
+            for (int k = 0; k < kSub; ++k) E += s_pi[k][threadIdx.x];
             imp = init || E < job.E_best_i[r];
             if (imp) job.E_best_i[r] = E;
             if (!init && job.has_target && job.hit_sweep[r] < 0 && E <= job.target_i) job.hit_sweep[r] = s;
         } else {
-            const float* p = static_cast<const float*>(job.part);
             float E = 0.0f;
-            for (int side = 0; side < 2; ++side)
-                for (int b = 0; b < job.nblk; ++b) E += p[((size_t)side * job.nblk + b) * job.Rpad + r];
+#pragma unroll
+            for (int k = 0; k < kSub; ++k) E += s_pf[k][threadIdx.x];
             imp = init || E < job.E_best_f[r];
             if (imp) job.E_best_f[r] = E;
             if (!init && job.has_target && job.hit_sweep[r] < 0 && E <= job.target_f) job.hit_sweep[r] = s;

@@ -204,7 +204,7 @@ static pb_status bq_prepare(pb_run* run, pb_instance* I, const pb_schedule* sc, 
     j.Rpad = round_up(R, tensor ? kBqTcReps : (resident ? kBqResReps : kBqTileReps));
     j.ld = round_up(n, 16);
     j.nblk = (n + (tensor ? kBqTcRows : kBqTileRows) - 1) / (tensor ? kBqTcRows : kBqTileRows);
-    if (tensor) j.nblk = (j.nblk + 1) & ~1;  // row tiles come in clusters of two
+    if (tensor) j.nblk = 4 * ((j.nblk + 1) & ~1);  // row tiles in pairs, one partial row per 32-row quarter
     const int nlev = std::max<int>(1, (int)betas.size());
     if (pm1) {
         const int fmax = n + I->hmax;

@@ -43,7 +43,7 @@ struct BqJob {
     void* buf[2][2];        // [side][parity] live states: sweep s writes parity s & 1 (the initial state: 1), so
                             // state s - 1 is intact during sweep s
     void* best[2];          // [Rpad][ld] best states
-    int32_t nblk;           // row blocks of the field kernels
+    int32_t nblk;           // partial rows per side: row blocks of the field kernels (tensor form: 32-row quarters)
     void* part;             // [2][nblk][Rpad] energy partials (int32 PM1 / float F32): [0] -h.a, [1] -b.F_B
     int32_t* E_best_i;
     float* E_best_f;

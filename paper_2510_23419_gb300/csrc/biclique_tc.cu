@@ -297,7 +297,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint32_t* stab = reinterpret_cast<uint32_t*>(smem + S * Cfg::STAGE_BYTES);
-    float* red = reinterpret_cast<float*>(smem + S * Cfg::STAGE_BYTES + Cfg::TAB_BYTES);  // [4][TBN]
     __shared__ __align__(8) uint64_t full_bar[S];
     __shared__ __align__(8) uint64_t empty_bar[S];
     __shared__ __align__(8) uint64_t accf_bar[2];
@@ -454,6 +453,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
             const float hv = (i < n) ? (pm1 ? (job.inst.h8 ? (float)job.inst.h8[side * n + i] : 0.0f)
                                             : job.inst.hf[side * n + i])
                                      : 0.0f;
+            // +-1 couplings: the accumulator is an exact integer below 2^22 in
+            // magnitude, so v + (h + 1.5 * 2^23) is exact and its bit pattern is
+            // 0x4B400000 + F: the integer field without a float-to-int conversion.
+            const float hmag = hv + 12582912.0f;
+            const int hi_ = (int)hv;
             const uint32_t taddr = tmem + buf * TBN + ((uint32_t)(quarter * 32) << 16);
             const PhiloxFixed pf = philox_fixed((uint32_t)i, (uint32_t)s, (kTagDecision << 24) | (uint32_t)side, job.key0,
                                                 job.key1);
@@ -473,8 +477,16 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                 for (int q = 0; q < 8; ++q) {
                     const int rq = r0 + c * 32 + 4 * q;
                     float F[4];
+                    int Fi[4];  // +-1 couplings: F as an integer
 #pragma unroll
-                    for (int b = 0; b < 4; ++b) F[b] = v[4 * q + b] + hv;
+                    for (int b = 0; b < 4; ++b) {
+                        if (pm1) {
+                            Fi[b] = __float_as_int(v[4 * q + b] + hmag) - 0x4B400000;
+                            F[b] = (float)Fi[b];
+                        } else {
+                            F[b] = v[4 * q + b] + hv;
+                        }
+                    }
                     bool mn[4] = {false, false, false, false};
                     if (live) {
                         if (fields_out) {
@@ -487,7 +499,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
 #pragma unroll
                             for (int b = 0; b < 4; ++b) {
                                 if (pm1) {
-                                    const int f = min(max((int)F[b] - job.fmin, wlo), wlo + ww - 1) - wlo;
+                                    const int f = min(max(Fi[b] - job.fmin - wlo, 0), ww - 1);
                                     uint32_t T;
                                     if (TABMODE == 2)
                                         T = stab[f * 32 + lane];
@@ -517,14 +529,18 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
 #pragma unroll
                     for (int b = 0; b < 4; ++b) {
                         // side 1: -m F (F includes h);  side 0: -h m
-                        const float x = (side == 1) ? F[b] : hv;
-                        e[4 * q + b] = live ? (mn[b] ? x : -x) : 0.0f;
-                        const int xi = (int)x;
-                        ei[4 * q + b] = live ? (mn[b] ? xi : -xi) : 0;
+                        if (pm1) {
+                            const int xi = (side == 1) ? Fi[b] : hi_;
+                            ei[4 * q + b] = live ? (mn[b] ? xi : -xi) : 0;
+                        } else {
+                            const float x = (side == 1) ? F[b] : hv;
+                            e[4 * q + b] = live ? (mn[b] ? x : -x) : 0.0f;
+                        }
                     }
                 }
                 if (energy) {
-                    float colsum;
+                    // one partial row per 32-row quarter of the tile: no CTA barrier
+                    const size_t off = ((size_t)side * job.nblk + 4 * rt + quarter) * job.Rpad + r0 + c * 32 + lane;
                     if (pm1) {
                         // column sums over the warp's 32 rows, one integer reduction per column
                         int mine = 0;
@@ -533,24 +549,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                             const int t = __reduce_add_sync(0xFFFFFFFFu, ei[k]);
                             if (lane == k) mine = t;
                         }
-                        colsum = (float)mine;  // |sum| <= 32 (n + |h|) < 2^24: exact
+                        static_cast<int32_t*>(job.part)[off] = mine;
                     } else {
-                        colsum = warp_transpose_sum(e, lane);
+                        static_cast<float*>(job.part)[off] = warp_transpose_sum(e, lane);
                     }
-                    red[quarter * TBN + c * 32 + lane] = colsum;
                 }
-            }
-            if (energy) {
-                asm volatile("bar.sync 1, %0;" ::"r"(ET) : "memory");
-                for (int col = et; col < TBN; col += ET) {
-                    const float sum = red[col] + red[TBN + col] + red[2 * TBN + col] + red[3 * TBN + col];
-                    const size_t off = ((size_t)side * job.nblk + rt) * job.Rpad + r0 + col;
-                    if (pm1)
-                        static_cast<int32_t*>(job.part)[off] = (int32_t)sum;
-                    else
-                        static_cast<float*>(job.part)[off] = sum;
-                }
-                asm volatile("bar.sync 1, %0;" ::"r"(ET) : "memory");  // red is reused by the next tile
             }
         }
     }
@@ -621,7 +624,7 @@ size_t bq_tc_smem_bytes(int kind)
 {
     const size_t st = kind == 0 ? (size_t)TcCfg<0>::STAGES * TcCfg<0>::STAGE_BYTES + TcCfg<0>::TAB_BYTES
                                 : (size_t)TcCfg<1>::STAGES * TcCfg<1>::STAGE_BYTES + TcCfg<1>::TAB_BYTES;
-    return st + (size_t)4 * TBN * 4 + 1024;  // + reduction buffer + alignment slack
+    return st + 1024;  // + alignment slack
 }
 
 // 2D row-major [rows][cols] matrix of elem_bytes elements (row stride ld_bytes),

@@ -63,7 +63,7 @@ int64_t footprint_bytes(const pb_instance* I, const pb_schedule* sc, int R, cons
     const int64_t ld = (n + 15) / 16 * 16;
     const int64_t esz = I->jtype == PB_J_PM1_I8 ? 1 : 2;
     int64_t nblk = (n + (tensor ? kBqTcRows : kBqTileRows) - 1) / (tensor ? kBqTcRows : kBqTileRows);
-    if (tensor) nblk = (nblk + 1) & ~1LL;
+    if (tensor) nblk = 4 * ((nblk + 1) & ~1LL);
     const int64_t nF = 2 * (n + I->hmax) + 1;
     return 4 * Rpad * ld * esz + 2 * nblk * Rpad * 4 + nlev * (I->jtype == PB_J_PM1_I8 ? nF : 1) * 4 + 3 * Rpad * 4 +
            (n + 63) / 64 * R * 8 + out + 4096;
