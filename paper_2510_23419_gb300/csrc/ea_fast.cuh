@@ -219,9 +219,9 @@ struct EaFastTile {
         } else {
             const size_t site_i = (size_t)C * half + k;
             const float4 ja = __ldg(reinterpret_cast<const float4*>(job.inst.j6) + 2 * site_i);
-            const float2 jb = __ldg(reinterpret_cast<const float2*>(job.inst.j6) + 4 * site_i + 2);
+            const float4 jb = __ldg(reinterpret_cast<const float4*>(job.inst.j6) + 2 * site_i + 1);
             const float jv[6] = {ja.x, ja.y, ja.z, ja.w, jb.x, jb.y};
-            const float hv = __ldg(job.inst.hf + site_i);
+            const float hv = jb.z;  // the site's field rides in the coupling vector
             const uint32_t nb[6] = {n0, n1, n2, n3, n4, n5};
             float F[4];
 #pragma unroll

@@ -231,7 +231,10 @@ static pb_status ea_build(pb_instance* I, const pb_instance_desc* d, cudaStream_
                         if (!std::isfinite(J[bonds[b]])) return fail(PB_EINVAL, "F32 couplings must be finite");
                         j6[slot * 8 + b] = J[bonds[b]];
                     }
-                    if (d->h) hf[slot] = static_cast<const float*>(d->h)[i];
+                    if (d->h) {
+                        hf[slot] = static_cast<const float*>(d->h)[i];
+                        j6[slot * 8 + 6] = hf[slot];  // the field also rides in the site's second vector
+                    }
                 }
             }
     const size_t esz = pm1 ? 1 : 4;

@@ -91,7 +91,7 @@ struct EaDevice {
     int32_t hmax;           // PM1: max |h|
     const uint8_t* jbits;   // PM1 [2][half]: bit (2+b) set <=> bond b negative (pre-shifted by 2)
     const int8_t* h8;       // PM1 [2][half] or null
-    const float* j6;        // F32 [2][half][8]: 6 bond values (+2 pad) per site
+    const float* j6;        // F32 [2][half][8]: 6 bond values, h (0 without a field), 1 pad per site
     const float* hf;        // F32 [2][half] (zeros when no field)
     const void* J3;         // original layout [3][N] (int8 or float) for the energy recompute
     const void* hraw;       // original layout [N] (int8 or float) or null
