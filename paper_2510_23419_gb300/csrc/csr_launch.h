@@ -61,7 +61,7 @@ struct CsrJob {
 constexpr int kCsrChunk = 64;  // vertices per energy chunk
 constexpr int kCsrLanesQ = 32;  // class kernel: replica words per block
 constexpr int kCsrLanesV = 8;   // class kernel: vertex lanes per block
-constexpr int kCsrVpt = 8;      // class kernel: class spins per thread
+constexpr int kCsrVpt = 4;      // class kernel: class spins per thread (measured: 4 beats 1, 2, 8)
 constexpr int kCsrClassChunk = kCsrLanesV * kCsrVpt;  // class spins per block
 
 cudaError_t csr_launch_init(const CsrJob& job, cudaStream_t st);
