@@ -337,26 +337,32 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     if (warp == 0) {
         // ---------------- TMA producer (both CTAs) ----------------
         if (lane == 0) {
-            uint32_t g = 0;
+            // stage index and phase advance incrementally; the even CTA's "full"
+            // barriers are consecutive words, so their cluster addresses are too
+            int st = 0;
+            uint32_t ph = 0;
+            const uint32_t fb0 = map_rank(&full_bar[0], 0);
             bool ok = true;
             for (int ct = clus; ct < nct && ok; ct += nclus) {
                 const int i0 = (2 * (ct % nrp) + (int)crank) * TBM;
                 const int r0 = (ct / nrp) * TBN + (int)crank * (TBN / 2);
-                for (int kb = 0; kb < nkb; ++kb, ++g) {
-                    const int st = (int)(g % S);
-                    const uint32_t ph = (g / S) & 1u;
+                for (int kb = 0; kb < nkb; ++kb) {
                     if (!mbar_wait(&empty_bar[st], ph ^ 1u)) {
                         atomicOr(err, 1);
                         ok = false;
                         break;
                     }
                     unsigned char* sa = smem + st * Cfg::STAGE_BYTES;
-                    const uint32_t fb = map_rank(&full_bar[st], 0);
+                    const uint32_t fb = fb0 + (uint32_t)st * (uint32_t)sizeof(uint64_t);
                     if (crank == 0) mbar_expect_tx(&full_bar[st], (uint32_t)(2 * Cfg::STAGE_BYTES));
                     const int kc = kb * Cfg::KELEM;
                     tma_load_2d_pair(sa, &tmA, fb, kc, i0);
                     if (KIND == 1) tma_load_2d_pair(sa + Cfg::A_BYTES, &tmA2, fb, kc, i0);
                     tma_load_2d_pair(sa + NA * Cfg::A_BYTES, &tmB, fb, kc, r0);
+                    if (++st == S) {
+                        st = 0;
+                        ph ^= 1u;
+                    }
                 }
             }
         }
@@ -364,7 +370,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
         // ---------------- MMA issuer (even CTA only) ----------------
         if (lane == 0 && crank == 0) {
             constexpr uint32_t idesc = instr_desc(KIND == 0 ? 0u : 1u, 2 * TBM, TBN);
-            uint32_t g = 0, j = 0;
+            // descriptor of the ring's first byte; a stage or K offset only adds to
+            // the start-address field (shared addresses stay below 2^18, so the
+            // 14-bit field of addr >> 4 never carries)
+            const uint64_t desc0 = smem_desc(smem_u32(smem));
+            int st = 0;
+            uint32_t ph = 0, j = 0;
             bool ok = true;
             for (int ct = clus; ct < nct && ok; ct += nclus, ++j) {
                 const uint32_t buf = j & 1u, aph = (j >> 1) & 1u;
@@ -375,25 +386,28 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t d = tmem + buf * TBN;
-                for (int kb = 0; kb < nkb; ++kb, ++g) {
-                    const int st = (int)(g % S);
-                    const uint32_t ph = (g / S) & 1u;
+                for (int kb = 0; kb < nkb; ++kb) {
                     if (!mbar_wait(&full_bar[st], ph)) {
                         atomicOr(err, 2);
                         ok = false;
                         break;
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint32_t sa = smem_u32(smem + st * Cfg::STAGE_BYTES);
-                    const uint32_t sb = sa + NA * Cfg::A_BYTES;
+                    const uint64_t da = desc0 + (uint64_t)((st * Cfg::STAGE_BYTES) >> 4);
+                    const uint64_t db = da + (uint64_t)((NA * Cfg::A_BYTES) >> 4);
 #pragma unroll
                     for (int k = 0; k < KBYTES / Cfg::KSTEP_BYTES; ++k) {
-                        const uint64_t bd = smem_desc(sb + k * Cfg::KSTEP_BYTES);
-                        mma_issue<KIND>(d, smem_desc(sa + k * Cfg::KSTEP_BYTES), bd, idesc, (kb | k) ? 1u : 0u);
+                        const uint64_t bd = db + (uint64_t)((k * Cfg::KSTEP_BYTES) >> 4);
+                        mma_issue<KIND>(d, da + (uint64_t)((k * Cfg::KSTEP_BYTES) >> 4), bd, idesc, (kb | k) ? 1u : 0u);
                         if (KIND == 1)
-                            mma_issue<KIND>(d, smem_desc(sa + Cfg::A_BYTES + k * Cfg::KSTEP_BYTES), bd, idesc, 1u);
+                            mma_issue<KIND>(d, da + (uint64_t)((Cfg::A_BYTES + k * Cfg::KSTEP_BYTES) >> 4), bd, idesc,
+                                            1u);
                     }
                     mma_commit_pair(&empty_bar[st]);
+                    if (++st == S) {
+                        st = 0;
+                        ph ^= 1u;
+                    }
                 }
                 if (ok) mma_commit_pair(&accf_bar[buf]);
             }
