@@ -145,6 +145,32 @@ def test_tensor_sampled_large(pb, orc):
         assert o["best_E"][0] == g["best_E"][r] and o["best_sweep"][0] == g["best_sweep"][r]
 
 
+def test_tensor_full_size_sampled(pb, orc):
+    """The biclique bench size and launch configuration: n = 4096, R = 4096 on tensor
+    cores (persistent clusters over 16 x 32 pair tiles).  +-1: replicas 0, 2049 and
+    4095 replayed one by one on the oracle, bit-exact.  N(0, 1) with the BF16 split:
+    the returned best states' energies, recomputed by the oracle in FP64, equal the
+    returned best energies within 1e-9 relative, for sampled replicas."""
+    n, R, S = 4096, 4096, 4
+    eu, ev, col = orc.biclique_graph(n)
+    sc = pb.make_schedule(pb.PB_SCHED_LINEAR, S, 0.35, 3.5)
+    ob = orc.schedule(orc.SCHED_LINEAR, 0.35, 3.5, S)
+    J = pb.pb_generate_biclique(n, pb.PB_DIST_PM1, 41)
+    g = _gpu(pb, n, J, None, sc, R, 43, "tensor")
+    Jd = J.astype(np.float64).reshape(-1)
+    for r in (0, 2049, 4095):
+        o = orc.anneal(eu, ev, Jd, None, col, ob, 1, 43, r_first=r)
+        assert np.array_equal(o["final_state"][0], g["final_state"][r])
+        assert np.array_equal(o["best_state"][0], g["best_state"][r])
+        assert o["best_E"][0] == g["best_E"][r] and o["best_sweep"][0] == g["best_sweep"][r]
+    Jg = pb.pb_generate_biclique(n, pb.PB_DIST_GAUSS, 47)
+    g = _gpu(pb, n, Jg, None, sc, R, 53, "tensor")
+    Jgd = Jg.astype(np.float64).reshape(-1)
+    for r in (1, 1500, 4094):
+        e = orc.energy(eu, ev, Jgd, None, g["best_state"][r])
+        assert abs(g["best_E"][r] - e) <= 1e-9 * abs(e)
+
+
 def test_tensor_threshold_row_in_global_memory(pb, orc):
     """n = 4300 at small beta: the threshold row (2n + 1 entries) is larger than the
     shared-memory table region and its unsaturated window is wider than 256, so the
