@@ -82,6 +82,27 @@ def test_pm1_bit_exact(pb, orc, case):
         assert np.array_equal(g[key], o[key]), key
 
 
+def test_bench_size_sampled(pb, orc):
+    """The general-graph bench configuration: odd periodic cube L = 25 (4 greedy
+    colours), +-1, 1024 replicas (256 replica words), 20 sweeps; replicas 0, 513
+    and 1023 replayed one by one on the oracle, bit-exact."""
+    L, R, S = 25, 1024, 20
+    N = L ** 3
+    eu, ev = syn.graph_periodic_cube(L)
+    J = syn.edge_couplings(eu.size, "pm1", 61)
+    col, k = pb.pb_greedy_colouring(N, eu, ev)
+    sc = pb.make_schedule(pb.PB_SCHED_LINEAR, S, 0.1, 3.0)
+    g, kg = _run(pb, N, eu, ev, J, None, None, sc, R, 67)
+    assert kg == k
+    ob = orc.schedule(orc.SCHED_LINEAR, 0.1, 3.0, S)
+    for r in (0, 513, 1023):
+        o = orc.anneal(eu, ev, J.astype(np.float64), None, col, ob, 1, 67, n_colours=k, r_first=r)
+        for key in ("final_state", "best_state"):
+            assert np.array_equal(o[key][0], g[key][r]), (r, key)
+        assert o["best_E"][0] == g["best_E"][r] and o["best_sweep"][0] == g["best_sweep"][r]
+        assert o["final_E"][0] == g["final_E"][r]
+
+
 def test_f32_fields(pb, orc):
     N, (eu, ev) = _graph("random300")
     J = syn.edge_couplings(eu.size, "gauss", 11)
