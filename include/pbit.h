@@ -115,9 +115,19 @@ typedef enum pb_form {
     PB_FORM_TENSOR = 4     /* biclique: tcgen05 tensor-core field (e4m3 for +-1, split BF16 for F32) */
 } pb_form;
 
+/* pb_anneal_opts.flags.  PB_FLAG_TEST_EXPIRE_WAITS is a test hook for the
+ * failure path of the device-side waits (no counterpart in the paper): with it
+ * the tensor form's load warp issues no loads, so the MMA issuer's and the
+ * epilogue's waits for operands and accumulators run out after 2 ms (instead
+ * of the normal 1 s limit); the kernels record an error word, skip their
+ * writes, release their tensor memory and end, and pb_wait / pb_energy report
+ * PB_ETIMEOUT.  The CUDA context stays usable.  Other forms have no device
+ * waits and ignore the flag. */
+#define PB_FLAG_TEST_EXPIRE_WAITS 0x40000000
+
 typedef struct pb_anneal_opts {
     int32_t form;          /* pb_form */
-    int32_t flags;         /* 0 */
+    int32_t flags;         /* 0, or PB_FLAG_TEST_EXPIRE_WAITS (tests of the failure path only) */
     double target_energy;  /* record, per replica, the first sweep whose energy is <= target;
                               NaN disables the record */
 } pb_anneal_opts;
@@ -211,8 +221,9 @@ pb_status pb_anneal_ex(pb_instance* inst, const pb_schedule* sched, int32_t repl
 /* Start `count` independent anneals of any topology as one batch, ordered on
  * `stream` like a single launch (the batch starts after the work queued on
  * `stream`, and `stream` waits for all of it).  All EA jobs that fit the
- * resident form share ONE persistent, graph-captured launch whose replica
- * blocks are scheduled longest first over all SMs; every biclique job, and EA
+ * resident form share ONE graph-captured launch of persistent kernels (one per
+ * coupling type, the second a programmatic dependent of the first) whose
+ * replica blocks are scheduled longest first over all SMs; every biclique job, and EA
  * jobs too large for the resident form, run as one graph-captured anneal each,
  * spread longest first over the library's launch streams so that small jobs
  * run side by side.  Forms left at PB_FORM_AUTO come from the autotuner's

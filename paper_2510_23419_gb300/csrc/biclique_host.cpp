@@ -192,6 +192,11 @@ static pb_status bq_prepare(pb_run* run, pb_instance* I, const pb_schedule* sc, 
     run->stream = st;
     BqJob& j = run->bjob;
     j = BqJob{};
+    j.wait_ns = kBqWaitNs;
+    if (opts && (opts->flags & PB_FLAG_TEST_EXPIRE_WAITS)) {
+        j.stall_loads = 1;  // failure-path test: the tensor form's waits for operands run out
+        j.wait_ns = kBqTestWaitNs;
+    }
     j.inst = I->bq;
     j.key0 = (uint32_t)(seed & 0xFFFFFFFFu);
     j.key1 = (uint32_t)(seed >> 32);

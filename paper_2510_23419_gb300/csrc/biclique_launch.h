@@ -54,7 +54,12 @@ struct BqJob {
     double* epart;          // [ceil(n/64)][R] row-tile parts of the exact readout energy
     const int32_t* win;     // PM1 [levels][3]: threshold window (lo, width, off) of each beta level
     int32_t tabmode;        // tensor form: where the decisions read the windows (widest level decides)
+    uint64_t wait_ns;       // tensor form: limit of every device-side wait (ns of the global timer)
+    int32_t stall_loads;    // tensor form, failure-path tests only: the load warp issues no loads
 };
+
+constexpr uint64_t kBqWaitNs = 1000000000ull;   // 1 s: far above any tile's MMA chain or epilogue
+constexpr uint64_t kBqTestWaitNs = 2000000ull;  // 2 ms: the limit under PB_FLAG_TEST_EXPIRE_WAITS
 
 constexpr int kBqResReps = 32;      // resident form: replicas per CTA
 constexpr int kBqResMaxNpm1 = 256;  // resident form: largest n (+-1 couplings, int8 J in shared memory)

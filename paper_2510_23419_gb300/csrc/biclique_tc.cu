@@ -43,7 +43,6 @@ constexpr int KBYTES = 128;     // K bytes per stage (one 128-byte swizzle row)
 constexpr int kEpiWarps = 16;   // epilogue warps: four per tensor-memory lane quarter
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kEpiCols = TBN / (kEpiWarps / 4);  // accumulator columns per epilogue warp
-constexpr uint32_t kWaitLimit = 1u << 26;
 
 template <int KIND>
 struct TcCfg;
@@ -83,11 +82,21 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
 
-// Bounded wait for the phase with the given parity; returns false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
+__device__ __forceinline__ uint64_t globaltimer_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait for the phase with the given parity; returns false once
+// `limit_ns` of the global timer have passed without it (the caller records
+// an error word and stops waiting, so the kernel still ends).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns)
 {
     const uint32_t a = smem_u32(bar);
-    for (uint32_t it = 0; it < kWaitLimit; ++it) {
+    uint64_t t0 = 0;
+    for (uint32_t it = 0;; ++it) {
         uint32_t ok;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -95,9 +104,15 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
             : "r"(a), "r"(parity)
             : "memory");
         if (ok) return true;
-        if (it > 64) __nanosleep(64);
+        if (it >= 64) {
+            const uint64_t now = globaltimer_ns();
+            if (it == 64)
+                t0 = now;
+            else if (now - t0 > limit_ns)
+                return false;
+            __nanosleep(64);
+        }
     }
-    return false;
 }
 
 // TMA load into this CTA's shared memory that signals the barrier at shared::cluster
@@ -336,7 +351,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
 
     if (warp == 0) {
         // ---------------- TMA producer (both CTAs) ----------------
-        if (lane == 0) {
+        // (stall_loads: failure-path tests, no loads, so the consumers' waits run out)
+        if (lane == 0 && !job.stall_loads) {
             // stage index and phase advance incrementally; the even CTA's "full"
             // barriers are consecutive words, so their cluster addresses are too
             int st = 0;
@@ -347,7 +363,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                 const int i0 = (2 * (ct % nrp) + (int)crank) * TBM;
                 const int r0 = (ct / nrp) * TBN + (int)crank * (TBN / 2);
                 for (int kb = 0; kb < nkb; ++kb) {
-                    if (!mbar_wait(&empty_bar[st], ph ^ 1u)) {
+                    if (!mbar_wait(&empty_bar[st], ph ^ 1u, job.wait_ns)) {
                         atomicOr(err, 1);
                         ok = false;
                         break;
@@ -379,7 +395,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
             bool ok = true;
             for (int ct = clus; ct < nct && ok; ct += nclus, ++j) {
                 const uint32_t buf = j & 1u, aph = (j >> 1) & 1u;
-                if (!mbar_wait(&acce_bar[buf], aph ^ 1u)) {
+                if (!mbar_wait(&acce_bar[buf], aph ^ 1u, job.wait_ns)) {
                     atomicOr(err, 8);
                     ok = false;
                     break;
@@ -387,7 +403,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t d = tmem + buf * TBN;
                 for (int kb = 0; kb < nkb; ++kb) {
-                    if (!mbar_wait(&full_bar[st], ph)) {
+                    if (!mbar_wait(&full_bar[st], ph, job.wait_ns)) {
                         atomicOr(err, 2);
                         ok = false;
                         break;
@@ -458,7 +474,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
             const int rt = 2 * (ct % nrp) + (int)crank;
             const int i = rt * TBM + row;
             const int r0 = (ct / nrp) * TBN;
-            if (ok && !mbar_wait(&accf_bar[buf], aph)) {
+            if (ok && !mbar_wait(&accf_bar[buf], aph, job.wait_ns)) {
                 atomicOr(err, 4);
                 ok = false;
             }

@@ -22,6 +22,7 @@ PB_J_PM1_I8, PB_J_F32 = 0, 1
 PB_DIST_PM1, PB_DIST_GAUSS, PB_DIST_UNIF = 0, 1, 2
 PB_SCHED_LINEAR, PB_SCHED_GEOMETRIC, PB_SCHED_EXPLICIT = 0, 1, 2
 PB_FORM_AUTO, PB_FORM_PLAIN, PB_FORM_RESIDENT, PB_FORM_CUDACORE, PB_FORM_TENSOR = range(5)
+PB_FLAG_TEST_EXPIRE_WAITS = 0x40000000  # failure-path test hook (see include/pbit.h)
 
 _ERRNAMES = {0: "PB_OK", 1: "PB_EINVAL", 2: "PB_ECOLOUR", 3: "PB_ENOMEM", 4: "PB_EDEVICE", 5: "PB_ETIMEOUT",
              6: "PB_EBUSY", 7: "PB_EUNSUPPORTED"}
@@ -262,8 +263,8 @@ def make_schedule(kind: int, n_sweeps: int, beta0: float = 0.0, beta1: float = 0
     return s
 
 
-def make_opts(form: int = PB_FORM_AUTO, target_energy: float = math.nan):
-    return pb_anneal_opts(form=form, flags=0, target_energy=target_energy)
+def make_opts(form: int = PB_FORM_AUTO, target_energy: float = math.nan, flags: int = 0):
+    return pb_anneal_opts(form=form, flags=flags, target_energy=target_energy)
 
 
 # ------------------------------------------------------------------- runs
