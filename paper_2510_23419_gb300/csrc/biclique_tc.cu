@@ -91,27 +91,25 @@ __device__ __forceinline__ uint64_t globaltimer_ns()
 
 // Bounded wait for the phase with the given parity; returns false once
 // `limit_ns` of the global timer have passed without it (the caller records
-// an error word and stops waiting, so the kernel still ends).
+// an error word and stops waiting, so the kernel still ends).  Each try_wait
+// may suspend the warp for up to 100 us (less under a shorter limit) until the
+// phase completes, so a waiting warp issues almost nothing: the epilogue warps
+// that wait for an accumulator share their schedulers with the load and MMA
+// threads.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns)
 {
     const uint32_t a = smem_u32(bar);
-    uint64_t t0 = 0;
-    for (uint32_t it = 0;; ++it) {
+    const uint32_t hint = (uint32_t)(limit_ns < 100000u ? limit_ns / 4 : 100000u);
+    const uint64_t t0 = globaltimer_ns();
+    for (;;) {
         uint32_t ok;
         asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
             : "=r"(ok)
-            : "r"(a), "r"(parity)
+            : "r"(a), "r"(parity), "r"(hint)
             : "memory");
         if (ok) return true;
-        if (it >= 64) {
-            const uint64_t now = globaltimer_ns();
-            if (it == 64)
-                t0 = now;
-            else if (now - t0 > limit_ns)
-                return false;
-            __nanosleep(64);
-        }
+        if (globaltimer_ns() - t0 > limit_ns) return false;
     }
 }
 
