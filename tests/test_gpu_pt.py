@@ -67,6 +67,22 @@ def test_pm1_bit_exact(pb, orc, graph, M, C, S, hmax):
         assert g["n_accept"].sum() > 0
 
 
+def test_bench_configuration_bit_exact(pb, orc):
+    """The tempering bench configuration: periodic cube L = 25 (4 greedy colours),
+    +-1, linear ladder 0.1 .. 3.0 with 16 rungs x 64 chains (1024 slots); 10 sweeps,
+    every slot bit-exact (states, energies, final temperatures, accepted exchanges)."""
+    L, C, S = 25, 64, 10
+    N = L ** 3
+    eu, ev = syn.graph_periodic_cube(L)
+    J = syn.edge_couplings(eu.size, "pm1", 77)
+    ladder = np.linspace(0.1, 3.0, 16)
+    g, col, k = _pt(pb, N, eu, ev, J, None, ladder, S, C, 9)
+    o = orc.anneal_pt(eu, ev, J.astype(np.float64), None, col, ladder, S, C, 9, n_colours=k)
+    for key in ("final_state", "best_state", "final_E", "best_E", "best_sweep", "slot_temp", "n_accept"):
+        assert np.array_equal(g[key], o[key]), key
+    assert g["n_accept"].sum() > 0
+
+
 def test_f32_mean_energy_per_temperature(pb, orc):
     N, eu, ev = _graph(pb, "king10x8")
     J = syn.edge_couplings(eu.size, "gauss", 5)
