@@ -175,6 +175,25 @@ def test_csr_in_batch_equals_alone(pb):
         pb.pb_instance_destroy(binst)
 
 
+def test_sparsified_bench_size_sampled(pb, orc):
+    """The sparsified-biclique bench configuration: +-1 K_{512,512} as a copy graph
+    (at most 4 edges per copy, copy strength 2: 131072 spins), 256 replicas, 30
+    sweeps; replicas 0 and 255 replayed one by one on the oracle, bit-exact."""
+    n, R, S = 512, 256, 30
+    J = pb.pb_generate_biclique(n, pb.PB_DIST_PM1, 61)
+    sp = pb.pb_sparsify_biclique(J, 4, 2)
+    sc = pb.make_schedule(pb.PB_SCHED_LINEAR, S, 0.35, 3.5)
+    g, k = _run(pb, sp["N"], sp["eu"], sp["ev"], sp["J"], None, sp["colour"], sc, R, 13)
+    assert k == 2
+    ob = orc.schedule(orc.SCHED_LINEAR, 0.35, 3.5, S)
+    for r in (0, 255):
+        o = orc.anneal(sp["eu"], sp["ev"], sp["J"].astype(np.float64), None, sp["colour"], ob, 1, 13, n_colours=2,
+                       r_first=r)
+        for key in ("final_state", "best_state"):
+            assert np.array_equal(o[key][0], g[key][r]), (r, key)
+        assert o["best_E"][0] == g["best_E"][r] and o["best_sweep"][0] == g["best_sweep"][r]
+
+
 @pytest.mark.parametrize("n,cs", [(24, 2), (17, 3)])
 def test_sparsified_biclique_bit_exact(pb, orc, n, cs):
     """The copy graph of a +-J biclique (degree <= 6, two update groups) on the CSR
