@@ -134,6 +134,7 @@ pb_status batch_start(int count, pb_instance* const* insts, const pb_schedule* s
                       std::vector<double>* load_io, std::vector<std::unique_ptr<pb_run>>& runs_out,
                       std::vector<double>* costs, std::vector<int>* stream_of)
 {
+    TraceRange trace_prepare("batch: prepare");
     if (count < 1 || !insts || !scheds || !replicas || !seeds) return fail(PB_EINVAL, "null or empty batch");
     cudaStream_t st = setup_st;
     std::vector<Job> jobs;
@@ -212,6 +213,7 @@ pb_status batch_start(int count, pb_instance* const* insts, const pb_schedule* s
         }
     }
 
+    TraceRange trace_launch("batch: launch");
     // ---- launch: fork from the caller's stream, one stream for the EA batch,
     //      the other jobs longest first onto the least loaded stream
     cudaEvent_t fork = nullptr;
@@ -291,6 +293,7 @@ extern "C" {
 pb_status pb_anneal_batch(int32_t count, pb_instance* const* insts, const pb_schedule* scheds, const int32_t* replicas,
                           const uint64_t* seeds, const pb_anneal_opts* opts, void* stream, pb_run** outs)
 {
+    pb::TraceRange trace_("pb_anneal_batch");
     if (count < 1 || !outs) return fail(PB_EINVAL, "null or empty batch");
     for (int q = 0; q < count; ++q) outs[q] = nullptr;
     std::vector<std::unique_ptr<pb_run>> runs;
@@ -305,6 +308,7 @@ pb_status pb_anneal_batch(int32_t count, pb_instance* const* insts, const pb_sch
 
 pb_status pb_autotune(pb_instance* I, int32_t R, int32_t probe_sweeps, void* stream, pb_tune_result* out)
 {
+    pb::TraceRange trace_("pb_autotune");
     if (!I || !out) return fail(PB_EINVAL, "null argument");
     if (R < 1) return fail(PB_EINVAL, "replicas must be >= 1");
     const int S = std::max(2, std::min(probe_sweeps > 0 ? probe_sweeps : 8, 1000));

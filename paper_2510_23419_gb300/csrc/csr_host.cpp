@@ -378,6 +378,7 @@ int32_t pb_greedy_colouring(int32_t N, int64_t n_edges, const int32_t* eu, const
 
 pb_status pb_create_graph_instance(const pb_graph_desc* d, void* stream, pb_instance** out)
 {
+    pb::TraceRange trace_("pb_create_graph_instance");
     if (!d || !out) return fail(PB_EINVAL, "null argument");
     *out = nullptr;
     if (d->jtype != PB_J_PM1_I8 && d->jtype != PB_J_F32) return fail(PB_EINVAL, "unknown jtype");
@@ -393,6 +394,7 @@ pb_status pb_create_graph_instance(const pb_graph_desc* d, void* stream, pb_inst
 pb_status pb_anneal_pt(pb_instance* I, const double* ladder, int32_t M, int32_t n_sweeps, int32_t chains,
                        uint64_t seed, void* stream, pb_run** out)
 {
+    pb::TraceRange trace_("pb_anneal_pt");
     if (!I || !ladder || !out) return fail(PB_EINVAL, "null argument");
     *out = nullptr;
     if (I->topo != PB_TOPO_CSR)

@@ -600,6 +600,7 @@ pb_status pb_generate_biclique(int32_t n, int32_t dist, uint64_t seed, void* J_o
 
 pb_status pb_create_instance(const pb_instance_desc* d, void* stream, pb_instance** out)
 {
+    pb::TraceRange trace_("pb_create_instance");
     if (!d || !out) return fail(PB_EINVAL, "null argument");
     *out = nullptr;
     if (!d->J) return fail(PB_EINVAL, "J is null");
@@ -628,6 +629,7 @@ int64_t pb_instance_spins(const pb_instance* inst) { return inst ? inst->N : -1;
 pb_status pb_anneal_ex(pb_instance* I, const pb_schedule* sc, int32_t R, uint64_t seed, const pb_anneal_opts* opts,
                        void* stream, pb_run** out)
 {
+    pb::TraceRange trace_("pb_anneal");
     if (!I || !sc || !out) return fail(PB_EINVAL, "null argument");
     *out = nullptr;
     if (R < 1) return fail(PB_EINVAL, "replicas must be >= 1");
@@ -693,6 +695,7 @@ pb_status pb_query(pb_run* run)
 
 pb_status pb_energy(pb_run* run, double* final_E, double* best_E, int32_t* best_sweep)
 {
+    pb::TraceRange trace_("pb_energy");
     if (!run) return fail(PB_EINVAL, "null run");
     pb_status ps = wait_run(run, -1);
     if (ps != PB_OK) return ps;
@@ -716,12 +719,14 @@ static pb_status copy_states(pb_run* run, const DevBuf& src, int8_t* out, int64_
 
 pb_status pb_best_states(pb_run* run, int8_t* out, int64_t out_bytes)
 {
+    pb::TraceRange trace_("pb_best_states");
     if (!run) return fail(PB_EINVAL, "null run");
     return copy_states(run, run->best_pm, out, out_bytes);
 }
 
 pb_status pb_final_states(pb_run* run, int8_t* out, int64_t out_bytes)
 {
+    pb::TraceRange trace_("pb_final_states");
     if (!run) return fail(PB_EINVAL, "null run");
     return copy_states(run, run->final_pm, out, out_bytes);
 }

@@ -31,6 +31,7 @@ extern "C" {
 
 pb_status pb_find_imin(pb_instance* inst, const pb_imin_opts* o, void* stream, pb_imin_result* out)
 {
+    pb::TraceRange trace_("pb_find_imin");
     if (!inst || !o || !out) return fail(PB_EINVAL, "null argument");
     if (o->trials < 1) return fail(PB_EINVAL, "trials must be >= 1");
     if (o->i_start < 1 || o->i_step < 1) return fail(PB_EINVAL, "i_start and i_step must be >= 1");

@@ -170,8 +170,12 @@ void pb_server::run_loop()
             std::vector<std::unique_ptr<pb_run>> runs;
             std::vector<double> costs;
             std::vector<int> streams;
-            pb_status ps = batch_start(m, insts.data(), scheds.data(), reps.data(), seeds.data(), os.data(), setup, false,
-                                       &load_copy, runs, &costs, &streams);
+            pb_status ps;
+            {
+                TraceRange trace_("server: admission round");
+                ps = batch_start(m, insts.data(), scheds.data(), reps.data(), seeds.data(), os.data(), setup, false,
+                                 &load_copy, runs, &costs, &streams);
+            }
             const std::string err = ps == PB_OK ? std::string() : std::string(pb_last_error());
             lk.lock();
             ++rounds;
