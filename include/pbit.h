@@ -190,6 +190,30 @@ int32_t pb_greedy_colouring(int32_t N, int64_t n_edges, const int32_t* eu, const
 /* Number of colour classes of an instance (2 for EA and biclique), or -1. */
 int32_t pb_instance_colours(const pb_instance* inst);
 
+/* Resume an anneal of a general sparse instance (checkpoint / resume; no
+ * counterpart in the paper, which runs each anneal start to end).  `sched` is
+ * the FULL schedule; sweeps first_sweep .. n_sweeps-1 run, from `state`, the
+ * replicas' spins after sweeps 0 .. first_sweep-1, with the running best
+ * (`best_state`, `best_E`, `best_sweep`, the sweep of the best or -1 for the
+ * initial state) carried over.  Arrays are caller-owned host memory, copied
+ * before the call returns: state and best_state [replicas][N] int8 +1/-1,
+ * best_E [replicas] (the energies pb_energy reported), best_sweep [replicas].
+ * The decisions use the absolute sweep index in their Philox counters (Sec.
+ * 1.2.2 update groups, Eq. 2), so for +-1 couplings a run of n_sweeps equals,
+ * bit for bit, a run of the first first_sweep sweeps (an explicit schedule of
+ * those betas) resumed here with that run's final state and best (real
+ * couplings: the carried best energy is the FP64 recomputation, where an
+ * uninterrupted run compares with its running FP32 energies, so a near-tie can
+ * resolve differently).  The target-energy record restarts at first_sweep.
+ * The anneal runs asynchronously on `stream` like pb_anneal.  PB_EINVAL:
+ * first_sweep outside [0, n_sweeps], a best_sweep outside [-1, first_sweep),
+ * a state value other than +-1; PB_EUNSUPPORTED: not a general sparse instance
+ * (an EA cube or a biclique runs here when created by pb_create_graph_instance
+ * from its edge list). */
+pb_status pb_anneal_resume(pb_instance* inst, const pb_schedule* sched, int32_t replicas, uint64_t seed,
+                           int32_t first_sweep, const int8_t* state, const int8_t* best_state, const double* best_E,
+                           const int32_t* best_sweep, void* stream, pb_run** out);
+
 /* Parallel tempering (replica exchange, Hukushima & Nemoto 1996; Sec. 6.1 names
  * it as a PC solving method) on a general sparse instance: M inverse
  * temperatures ladder[0] < ... < ladder[M-1] and `chains` independent chains

@@ -228,10 +228,13 @@ __global__ void __launch_bounds__(256) csr_sweep_end_kernel(CsrJob job, int s, i
     }
     job.E_cur[r] = E;
     bool imp;
-    if (init) {
+    if (init == 1) {
         imp = true;
         job.E_best[r] = E;
         job.best_sweep[r] = -1;
+        job.hit_sweep[r] = -1;
+    } else if (init == 2) {
+        imp = false;  // resumed: the given best stays
         job.hit_sweep[r] = -1;
     } else {
         imp = E < job.E_best[r];

@@ -335,11 +335,11 @@ pb_status csr_launch(pb_run* run, cudaStream_t st)
 {
     const CsrJob& j = run->cjob;
     PB_CUDA_TRY(cudaEventRecord(run->ev_start, st));
-    PB_CUDA_TRY(csr_launch_init(j, st));
+    if (!run->resumed) PB_CUDA_TRY(csr_launch_init(j, st));
     PB_CUDA_TRY(csr_launch_energy(j, j.spins, 0, st));
-    PB_CUDA_TRY(csr_launch_sweep_end(j, -1, 1, st));
+    PB_CUDA_TRY(csr_launch_sweep_end(j, j.s0 - 1, run->resumed ? 2 : 1, st));
     PB_CUDA_TRY(cudaEventRecord(run->ev_k0, st));
-    for (int s = 0; s < j.S; ++s) {
+    for (int s = j.s0; s < j.S; ++s) {
         for (int c = 0; c < j.g.n_colours; ++c)
             PB_CUDA_TRY(csr_launch_class(j, c, run->csr_nchunk[(size_t)c], s, st));
         PB_CUDA_TRY(csr_launch_sweep_end(j, s, 0, st));
@@ -388,6 +388,56 @@ pb_status pb_create_graph_instance(const pb_graph_desc* d, void* stream, pb_inst
                              static_cast<cudaStream_t>(stream));
     if (ps != PB_OK) return ps;
     *out = I.release();
+    return PB_OK;
+}
+
+pb_status pb_anneal_resume(pb_instance* I, const pb_schedule* sched, int32_t replicas, uint64_t seed,
+                           int32_t first_sweep, const int8_t* state, const int8_t* best_state, const double* best_E,
+                           const int32_t* best_sweep, void* stream, pb_run** out)
+{
+    pb::TraceRange trace_("pb_anneal_resume");
+    if (!I || !sched || !state || !best_state || !best_E || !best_sweep || !out) return fail(PB_EINVAL, "null argument");
+    *out = nullptr;
+    if (I->topo != PB_TOPO_CSR)
+        return fail(PB_EUNSUPPORTED, "resume runs on general sparse instances (pb_create_graph_instance)");
+    if (replicas < 1) return fail(PB_EINVAL, "replicas must be >= 1");
+    if (first_sweep < 0 || first_sweep > sched->n_sweeps) return fail(PB_EINVAL, "first_sweep must be in [0, n_sweeps]");
+    const int64_t N = I->N, R = replicas;
+    for (int64_t r = 0; r < R; ++r)
+        if (best_sweep[r] < -1 || best_sweep[r] >= first_sweep) return fail(PB_EINVAL, "best_sweep must be in [-1, first_sweep)");
+    std::unique_ptr<pb_run> run(new (std::nothrow) pb_run());
+    if (!run) return fail(PB_ENOMEM, "host allocation failed");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    pb_status ps = csr_setup(run.get(), I, sched, replicas, seed, nullptr, st);
+    if (ps != PB_OK) return ps;
+    CsrJob& j = run->cjob;
+    j.s0 = first_sweep;
+    run->resumed = true;
+    // [R][N] +-1 -> [N][Rw] words (byte b of word q: replica 4q + b, 1 <=> m = -1; padding replicas +1)
+    const int64_t Rw = j.Rw;
+    std::vector<uint32_t> w((size_t)(N * Rw)), wb((size_t)(N * Rw));
+    for (int64_t i = 0; i < N; ++i)
+        for (int64_t r = 0; r < R; ++r) {
+            const int8_t m = state[r * N + i], mb = best_state[r * N + i];
+            if ((m != 1 && m != -1) || (mb != 1 && mb != -1)) return fail(PB_EINVAL, "states must hold +1 or -1");
+            const uint32_t sh = 8u * (uint32_t)(r & 3);
+            w[(size_t)(i * Rw + (r >> 2))] |= (m < 0 ? 1u : 0u) << sh;
+            wb[(size_t)(i * Rw + (r >> 2))] |= (mb < 0 ? 1u : 0u) << sh;
+        }
+    std::vector<double> eb((size_t)(4 * Rw), 1e300);  // padding replicas: any state improves on it
+    std::vector<int32_t> bs((size_t)(4 * Rw), -1);
+    for (int64_t r = 0; r < R; ++r) {
+        eb[(size_t)r] = best_E[r];
+        bs[(size_t)r] = best_sweep[r];
+    }
+    PB_CUDA_TRY(cudaMemcpyAsync(j.spins, w.data(), w.size() * 4, cudaMemcpyHostToDevice, st));
+    PB_CUDA_TRY(cudaMemcpyAsync(j.best, wb.data(), wb.size() * 4, cudaMemcpyHostToDevice, st));
+    PB_CUDA_TRY(cudaMemcpyAsync(j.E_best, eb.data(), eb.size() * 8, cudaMemcpyHostToDevice, st));
+    PB_CUDA_TRY(cudaMemcpyAsync(j.best_sweep, bs.data(), bs.size() * 4, cudaMemcpyHostToDevice, st));
+    PB_CUDA_TRY(cudaStreamSynchronize(st));  // the host staging arrays go out of scope; the anneal stays asynchronous
+    ps = csr_launch(run.get(), st);
+    if (ps != PB_OK) return ps;
+    *out = run.release();
     return PB_OK;
 }
 

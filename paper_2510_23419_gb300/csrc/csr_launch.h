@@ -30,6 +30,7 @@ struct CsrJob {
     CsrDevice g;
     uint32_t key0, key1;
     int32_t S, step, nF, fmin;
+    int32_t s0;              // first sweep (0, or the sweep a resumed run continues from)
     const uint32_t* table;   // PM1: threshold windows of all levels, concatenated
     const int32_t* win;      // PM1: [levels][3] (lo, width, off)
     const float* betaf;      // F32: [levels]
@@ -73,9 +74,10 @@ cudaError_t csr_launch_energy(const CsrJob& job, const uint32_t* m, int exact, c
 // Parallel tempering: exchange of temperatures between adjacent pairs of every
 // chain after sweep s (pairs t = s mod 2, t + 2, ...).
 cudaError_t csr_launch_exchange(const CsrJob& job, int s, cudaStream_t st);
-// Running best after sweep s (init: the initial state, whose energy comes from
-// csr_launch_energy; later sweeps add the class launches' energy changes to the
-// previous energy), snapshot of improved replicas.
+// Running best after sweep s (init 1: the initial state, whose energy comes from
+// csr_launch_energy, becomes the best; init 2: a resumed run's state, whose
+// energy is set and whose given best is kept; init 0: later sweeps add the class
+// launches' energy changes to the previous energy), snapshot of improved replicas.
 cudaError_t csr_launch_sweep_end(const CsrJob& job, int s, int init, cudaStream_t st);
 // States [R][N] int8 +-1 and energies (from the partials of the same state) of `m`.
 cudaError_t csr_launch_readout(const CsrJob& job, const uint32_t* m, int8_t* out_pm, double* out_E, cudaStream_t st);

@@ -122,6 +122,7 @@ struct BatchShared {
 struct pb_run {
     pb_instance* inst = nullptr;
     int form = 0;
+    bool resumed = false;  // general graphs: state and best were given (pb_anneal_resume)
     int R = 0, S = 0;
     int64_t N = 0;
     cudaStream_t stream = nullptr;

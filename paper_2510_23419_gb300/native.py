@@ -130,6 +130,7 @@ def load():
         "pb_instance_colours": ([P], I32),
         "pb_find_imin": ([P, P, P, P], st),
         "pb_anneal_pt": ([P, P, I32, I32, I32, U64, P, P], st),
+        "pb_anneal_resume": ([P, P, I32, U64, I32, P, P, P, P, P, P], st),
         "pb_pt_state": ([P, P, P], st),
         "pb_sparsify_biclique": ([I32, I32, P, I32, I32, P, P, P, P, P, P, I64, I32], I64),
         "pb_sparse_project": ([I32, P, I32, I32, P, P], I32),
@@ -375,6 +376,20 @@ def pb_anneal_pt(inst, ladder, n_sweeps: int, chains: int, seed: int, stream=Non
     lad = np.ascontiguousarray(ladder, dtype=np.float64)
     out = ctypes.c_void_p()
     _check(load().pb_anneal_pt(inst, _ptr(lad), lad.size, n_sweeps, chains, seed, _stream(stream), ctypes.byref(out)))
+    return out
+
+
+def pb_anneal_resume(inst, sched: pb_schedule, replicas: int, seed: int, first_sweep: int, state: np.ndarray,
+                     best_state: np.ndarray, best_E: np.ndarray, best_sweep: np.ndarray, stream=None) -> ctypes.c_void_p:
+    """Continue an anneal of a general sparse instance at sweep `first_sweep` from the
+    given state and running best (host arrays, copied before the call returns)."""
+    st = np.ascontiguousarray(state, dtype=np.int8)
+    bst = np.ascontiguousarray(best_state, dtype=np.int8)
+    be = np.ascontiguousarray(best_E, dtype=np.float64)
+    bs = np.ascontiguousarray(best_sweep, dtype=np.int32)
+    out = ctypes.c_void_p()
+    _check(load().pb_anneal_resume(inst, ctypes.byref(sched), replicas, seed, first_sweep, _ptr(st), _ptr(bst), _ptr(be),
+                                   _ptr(bs), _stream(stream), ctypes.byref(out)))
     return out
 
 

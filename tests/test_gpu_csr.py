@@ -103,6 +103,77 @@ def test_bench_size_sampled(pb, orc):
         assert o["final_E"][0] == g["final_E"][r]
 
 
+def _read_run(pb, run, R, N):
+    fe, be, bs = pb.pb_energy(run, R)
+    return dict(final_E=fe, best_E=be, best_sweep=bs, final_state=pb.pb_final_states(run, R, N),
+                best_state=pb.pb_best_states(run, R, N))
+
+
+@pytest.mark.parametrize("name,s0", [("cube5", 17), ("king12x10", 1), ("biclique24", 29), ("cube5", 0),
+                                     ("random300", 40)])
+def test_resume_split_equals_one_run(pb, orc, name, s0):
+    """Checkpoint / resume: sweeps 0..s0-1, then pb_anneal_resume from that run's final
+    state and running best, equal one uninterrupted run bit for bit (+-1 couplings)."""
+    if name == "biclique24":
+        n = 24
+        eu, ev, _ = orc.biclique_graph(n)
+        N = 2 * n
+    else:
+        N, (eu, ev) = _graph(name)
+    R, S, seed = 37, 40, 3
+    J = syn.edge_couplings(eu.size, "pm1", 90 + s0)
+    h = syn.int_fields(N, 2, 5) if name == "king12x10" else None
+    betas = orc.schedule(orc.SCHED_LINEAR, 0.1, 3.0, S)
+    full = pb.make_schedule(pb.PB_SCHED_EXPLICIT, S, betas=betas)
+    first = pb.make_schedule(pb.PB_SCHED_EXPLICIT, s0, betas=betas[:s0] if s0 else None)
+    inst = pb.pb_create_graph_instance(N, eu, ev, J, h)
+    try:
+        runs = []
+        try:
+            runs.append(pb.pb_anneal(inst, full, R, seed))
+            one = _read_run(pb, runs[-1], R, N)
+            runs.append(pb.pb_anneal(inst, first, R, seed))
+            a = _read_run(pb, runs[-1], R, N)
+            runs.append(pb.pb_anneal_resume(inst, full, R, seed, s0, a["final_state"], a["best_state"], a["best_E"],
+                                            a["best_sweep"]))
+            b = _read_run(pb, runs[-1], R, N)
+        finally:
+            for r in runs:
+                pb.pb_run_destroy(r)
+        for key in ("final_state", "best_state", "final_E", "best_E", "best_sweep"):
+            assert np.array_equal(b[key], one[key]), key
+    finally:
+        pb.pb_instance_destroy(inst)
+
+
+def test_resume_errors(pb):
+    N, (eu, ev) = _graph("cube5")
+    J = syn.edge_couplings(eu.size, "pm1", 1)
+    inst = pb.pb_create_graph_instance(N, eu, ev, J)
+    try:
+        sc = pb.make_schedule(pb.PB_SCHED_LINEAR, 10, 0.1, 1.0)
+        st = np.ones((4, N), np.int8)
+        be = np.zeros(4)
+        bs = np.full(4, -1, np.int32)
+        with pytest.raises(pb.PbError, match="PB_EINVAL"):
+            pb.pb_anneal_resume(inst, sc, 4, 1, 11, st, st, be, bs)       # first_sweep beyond the schedule
+        with pytest.raises(pb.PbError, match="PB_EINVAL"):
+            pb.pb_anneal_resume(inst, sc, 4, 1, 3, st, st, be, np.full(4, 3, np.int32))  # best after first_sweep
+        bad = st.copy()
+        bad[1, 7] = 0
+        with pytest.raises(pb.PbError, match="PB_EINVAL"):
+            pb.pb_anneal_resume(inst, sc, 4, 1, 3, bad, st, be, bs)       # not a +-1 state
+    finally:
+        pb.pb_instance_destroy(inst)
+    Jb = pb.pb_generate_biclique(16, pb.PB_DIST_PM1, 2)
+    binst = pb.pb_create_instance(pb.PB_TOPO_BICLIQUE, Jb, None, n=16)
+    try:
+        with pytest.raises(pb.PbError, match="PB_EUNSUPPORTED"):
+            pb.pb_anneal_resume(binst, sc, 4, 1, 3, np.ones((4, 32), np.int8), np.ones((4, 32), np.int8), be, bs)
+    finally:
+        pb.pb_instance_destroy(binst)
+
+
 def test_f32_fields(pb, orc):
     N, (eu, ev) = _graph("random300")
     J = syn.edge_couplings(eu.size, "gauss", 11)
