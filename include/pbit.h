@@ -190,7 +190,7 @@ int32_t pb_greedy_colouring(int32_t N, int64_t n_edges, const int32_t* eu, const
 /* Number of colour classes of an instance (2 for EA and biclique), or -1. */
 int32_t pb_instance_colours(const pb_instance* inst);
 
-/* Resume an anneal of a general sparse instance (checkpoint / resume; no
+/* Resume an anneal of an EA cube or a general sparse instance (checkpoint / resume; no
  * counterpart in the paper, which runs each anneal start to end).  `sched` is
  * the FULL schedule; sweeps first_sweep .. n_sweeps-1 run, from `state`, the
  * replicas' spins after sweeps 0 .. first_sweep-1, with the running best
@@ -207,9 +207,10 @@ int32_t pb_instance_colours(const pb_instance* inst);
  * resolve differently).  The target-energy record restarts at first_sweep.
  * The anneal runs asynchronously on `stream` like pb_anneal.  PB_EINVAL:
  * first_sweep outside [0, n_sweeps], a best_sweep outside [-1, first_sweep),
- * a state value other than +-1; PB_EUNSUPPORTED: not a general sparse instance
- * (an EA cube or a biclique runs here when created by pb_create_graph_instance
- * from its edge list). */
+ * a state value other than +-1, a non-integer best energy of a +-1 instance;
+ * PB_EUNSUPPORTED: a biclique instance (resume it through its edge list with
+ * pb_create_graph_instance) or an EA cube too large for the resident form,
+ * which EA resumes use. */
 pb_status pb_anneal_resume(pb_instance* inst, const pb_schedule* sched, int32_t replicas, uint64_t seed,
                            int32_t first_sweep, const int8_t* state, const int8_t* best_state, const double* best_E,
                            const int32_t* best_sweep, void* stream, pb_run** out);

@@ -391,23 +391,18 @@ pb_status pb_create_graph_instance(const pb_graph_desc* d, void* stream, pb_inst
     return PB_OK;
 }
 
-pb_status pb_anneal_resume(pb_instance* I, const pb_schedule* sched, int32_t replicas, uint64_t seed,
-                           int32_t first_sweep, const int8_t* state, const int8_t* best_state, const double* best_E,
-                           const int32_t* best_sweep, void* stream, pb_run** out)
+}  // extern "C"
+
+namespace pb {
+
+// General-graph part of pb_anneal_resume (arguments checked by the caller).
+pb_status csr_anneal_resume(pb_instance* I, const pb_schedule* sched, int32_t replicas, uint64_t seed,
+                            int32_t first_sweep, const int8_t* state, const int8_t* best_state, const double* best_E,
+                            const int32_t* best_sweep, cudaStream_t st, pb_run** out)
 {
-    pb::TraceRange trace_("pb_anneal_resume");
-    if (!I || !sched || !state || !best_state || !best_E || !best_sweep || !out) return fail(PB_EINVAL, "null argument");
-    *out = nullptr;
-    if (I->topo != PB_TOPO_CSR)
-        return fail(PB_EUNSUPPORTED, "resume runs on general sparse instances (pb_create_graph_instance)");
-    if (replicas < 1) return fail(PB_EINVAL, "replicas must be >= 1");
-    if (first_sweep < 0 || first_sweep > sched->n_sweeps) return fail(PB_EINVAL, "first_sweep must be in [0, n_sweeps]");
     const int64_t N = I->N, R = replicas;
-    for (int64_t r = 0; r < R; ++r)
-        if (best_sweep[r] < -1 || best_sweep[r] >= first_sweep) return fail(PB_EINVAL, "best_sweep must be in [-1, first_sweep)");
     std::unique_ptr<pb_run> run(new (std::nothrow) pb_run());
     if (!run) return fail(PB_ENOMEM, "host allocation failed");
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
     pb_status ps = csr_setup(run.get(), I, sched, replicas, seed, nullptr, st);
     if (ps != PB_OK) return ps;
     CsrJob& j = run->cjob;
@@ -440,6 +435,10 @@ pb_status pb_anneal_resume(pb_instance* I, const pb_schedule* sched, int32_t rep
     *out = run.release();
     return PB_OK;
 }
+
+}  // namespace pb
+
+extern "C" {
 
 pb_status pb_anneal_pt(pb_instance* I, const double* ladder, int32_t M, int32_t n_sweeps, int32_t chains,
                        uint64_t seed, void* stream, pb_run** out)

@@ -169,6 +169,10 @@ __device__ void ea_tile(const EaJob& job, int tile, unsigned char* smem)
             for (int i = t; i < N; i += kResidentThreads) sh8[i] = job.inst.h8[i];
     }
     for (int j = t; j < N * WT; j += kResidentThreads) {
+        if (job.resume) {  // resumed run: the given state, in the tile layout of final_words
+            sp[j] = job.final_words[(size_t)tile * N * WT + j];
+            continue;
+        }
         const int w2 = j % WT;
         const int ck = j / WT;
         const int c = ck >= half ? 1 : 0;
@@ -312,8 +316,9 @@ __device__ void ea_tile(const EaJob& job, int tile, unsigned char* smem)
         }
     };
 
-    // ---- initial energy; the initial state is the first best state ----
-    build_table(0, 0);
+    // ---- initial energy; the initial state is the first best state (unless resumed) ----
+    const int s_first = job.s0 < job.S ? job.s0 : 0;
+    build_table(s_first, s_first & 1);
     __syncthreads();
     {
         uint32_t uacc = 0;
@@ -327,10 +332,21 @@ __device__ void ea_tile(const EaJob& job, int tile, unsigned char* smem)
     int32_t bestEi = 0, hit = -1, bsweep = -1;
     float bestEf = 0.0f;
     if (t < nrep) energy_of(t, bestEi, bestEf);
-    tile_store_words<LT, WTT>(g, sp, job.best_words, tile, 0xFFFFFFFFu);
+    if (job.resume) {  // the running best carried over
+        if (t < nrep) {
+            const int r = tile * nrep + t;
+            if (JT == PB_J_PM1_I8)
+                bestEi = job.E_best_i[r];
+            else
+                bestEf = job.E_best_f[r];
+            bsweep = job.best_sweep[r];
+        }
+    } else {
+        tile_store_words<LT, WTT>(g, sp, job.best_words, tile, 0xFFFFFFFFu);
+    }
 
     // ---- sweeps ----
-    for (int s = 0; s < job.S; ++s) {
+    for (int s = job.s0; s < job.S; ++s) {
         uint32_t uacc = 0;
         int32_t hm[4] = {0, 0, 0, 0};
         float ef[4] = {0.f, 0.f, 0.f, 0.f};

@@ -138,6 +138,14 @@ struct EaFastTile {
 
     __device__ __forceinline__ void init_state()
     {
+        if (job.resume) {  // resumed run: the given state, in the tile layout of final_words
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const uint32_t* src = job.final_words + ((size_t)tile * 2 + c) * CLS + base0;
+                for (int z = zp; z < L; z += 2) sp[c * CLS + base0 + z * SZ] = src[z * SZ];
+            }
+            return;
+        }
 #pragma unroll
         for (int c = 0; c < 2; ++c)
 #pragma unroll 4
@@ -324,7 +332,7 @@ struct EaFastTile {
     __device__ __forceinline__ void run()
     {
         init_state();
-        load_table(0);
+        load_table(job.s0 < job.S ? job.s0 : 0);
         __syncthreads();
         {
             uint32_t uacc = 0;
@@ -337,9 +345,20 @@ struct EaFastTile {
         int32_t bestEi = 0, hit = -1, bsweep = -1;
         float bestEf = 0.0f;
         if (t < NREP) energy_of(t, bestEi, bestEf);
-        store_words(job.best_words, 0xFFFFFFFFu);
+        if (job.resume) {  // the running best carried over
+            if (t < NREP) {
+                const int r = tile * NREP + t;
+                if constexpr (PM1)
+                    bestEi = job.E_best_i[r];
+                else
+                    bestEf = job.E_best_f[r];
+                bsweep = job.best_sweep[r];
+            }
+        } else {
+            store_words(job.best_words, 0xFFFFFFFFu);
+        }
 
-        for (int s = 0; s < job.S; ++s) {
+        for (int s = job.s0; s < job.S; ++s) {
             uint32_t uacc = 0;
             float ef[4] = {0.f, 0.f, 0.f, 0.f};
             half_sweep<0, true>(s, uacc, ef);

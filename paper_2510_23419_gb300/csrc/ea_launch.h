@@ -30,6 +30,9 @@ struct EaJob {
     float* E_best_f;          // F32 running-best energy
     int32_t* best_sweep;      // [n_tiles*4*WT]
     int32_t* hit_sweep;       // [n_tiles*4*WT]
+    int32_t s0;               // first sweep (resident form: > 0 only for a resumed run)
+    int32_t resume;           // resident form: the initial state is final_words, the running best
+                              // (best_words, E_best_*, best_sweep) is given
 };
 
 // Tile code of the resident kernels (chosen on the host, so the kernel

@@ -678,6 +678,91 @@ pb_status pb_anneal(pb_instance* inst, const pb_schedule* sched, int32_t replica
     return pb_anneal_ex(inst, sched, replicas, seed, nullptr, stream, out);
 }
 
+// EA part of pb_anneal_resume: the resident form, with the given state and
+// running best written into the run's tile-layout buffers before the launch.
+static pb_status ea_anneal_resume(pb_instance* I, const pb_schedule* sc, int32_t R, uint64_t seed, int32_t s0,
+                                  const int8_t* state, const int8_t* best_state, const double* best_E,
+                                  const int32_t* best_sweep, cudaStream_t st, pb_run** out)
+{
+    int f = 0, WT = 0;
+    choose_form(I, R, PB_FORM_RESIDENT, f, WT);
+    if (f != PB_FORM_RESIDENT || WT == 0) return fail(PB_EUNSUPPORTED, "lattice too large for the resident form");
+    const int sms = sm_count();
+    while (WT > 1 && ((R + 3) / 4 + WT - 1) / WT < sms) WT /= 2;
+    std::unique_ptr<pb_run> run(new (std::nothrow) pb_run());
+    if (!run) return fail(PB_ENOMEM, "host allocation failed");
+    pb_status ps = ea_prepare_run(run.get(), I, sc, R, seed, nullptr, PB_FORM_RESIDENT, WT, st);
+    if (ps != PB_OK) return ps;
+    EaJob& j = run->job;
+    const bool pm1 = I->jtype == PB_J_PM1_I8;
+    const int64_t N = I->N, half = N / 2, L = I->L, Rpad = (int64_t)j.n_tiles * 4 * j.WT;
+    // [R][N] +-1 -> tile layout: word ((tile * 2 + c) * half + k) * WT + w, byte b of replica
+    // r = (tile * WT + w) * 4 + b; +-1: bit 8b set <=> m = -1; FP32: byte 0x3F / 0xBF; padding replicas +1
+    const uint32_t fill = pm1 ? 0u : 0x3F3F3F3Fu;
+    std::vector<uint32_t> w((size_t)(Rpad / 4 * N), fill), wb((size_t)(Rpad / 4 * N), fill);
+    for (int64_t r = 0; r < R; ++r) {
+        const int64_t tile = r / (4 * j.WT), ww = (r / 4) % j.WT, b = r & 3;
+        const uint32_t bit = pm1 ? (1u << (8 * b)) : (0x80u << (8 * b));
+        for (int64_t i = 0; i < N; ++i) {
+            const int8_t m = state[r * N + i], mb = best_state[r * N + i];
+            if ((m != 1 && m != -1) || (mb != 1 && mb != -1)) return fail(PB_EINVAL, "states must hold +1 or -1");
+            const int64_t x = i % L, y = (i / L) % L, z = i / (L * L);
+            const int64_t c = (x + y + z) & 1, k = i >> 1;
+            const size_t idx = (size_t)(((tile * 2 + c) * half + k) * j.WT + ww);
+            if (m < 0) w[idx] |= bit;
+            if (mb < 0) wb[idx] |= bit;
+        }
+    }
+    std::vector<int32_t> bs((size_t)Rpad, -1), ei((size_t)Rpad, INT32_MAX);
+    std::vector<float> ef((size_t)Rpad, 3.0e38f);  // padding replicas: any state improves on it
+    for (int64_t r = 0; r < R; ++r) {
+        bs[(size_t)r] = best_sweep[r];
+        if (pm1) {
+            if (best_E[r] != std::floor(best_E[r]) || std::fabs(best_E[r]) > 2.0e9)
+                return fail(PB_EINVAL, "best energies of +-1 instances are integers");
+            ei[(size_t)r] = (int32_t)best_E[r];
+        } else {
+            ef[(size_t)r] = (float)best_E[r];
+        }
+    }
+    PB_CUDA_TRY(cudaMemcpyAsync(j.final_words, w.data(), w.size() * 4, cudaMemcpyHostToDevice, st));
+    PB_CUDA_TRY(cudaMemcpyAsync(j.best_words, wb.data(), wb.size() * 4, cudaMemcpyHostToDevice, st));
+    PB_CUDA_TRY(cudaMemcpyAsync(j.best_sweep, bs.data(), bs.size() * 4, cudaMemcpyHostToDevice, st));
+    if (pm1)
+        PB_CUDA_TRY(cudaMemcpyAsync(j.E_best_i, ei.data(), ei.size() * 4, cudaMemcpyHostToDevice, st));
+    else
+        PB_CUDA_TRY(cudaMemcpyAsync(j.E_best_f, ef.data(), ef.size() * 4, cudaMemcpyHostToDevice, st));
+    PB_CUDA_TRY(cudaStreamSynchronize(st));  // staging arrays go out of scope; the anneal stays asynchronous
+    j.s0 = s0;
+    j.resume = 1;
+    std::vector<pb_run*> v{run.get()};
+    ps = ea_enqueue_resident(v, st);
+    if (ps != PB_OK) return ps;
+    *out = run.release();
+    return PB_OK;
+}
+
+pb_status pb_anneal_resume(pb_instance* I, const pb_schedule* sched, int32_t replicas, uint64_t seed,
+                           int32_t first_sweep, const int8_t* state, const int8_t* best_state, const double* best_E,
+                           const int32_t* best_sweep, void* stream, pb_run** out)
+{
+    pb::TraceRange trace_("pb_anneal_resume");
+    if (!I || !sched || !state || !best_state || !best_E || !best_sweep || !out) return fail(PB_EINVAL, "null argument");
+    *out = nullptr;
+    if (replicas < 1) return fail(PB_EINVAL, "replicas must be >= 1");
+    if (first_sweep < 0 || first_sweep > sched->n_sweeps) return fail(PB_EINVAL, "first_sweep must be in [0, n_sweeps]");
+    for (int64_t r = 0; r < replicas; ++r)
+        if (best_sweep[r] < -1 || best_sweep[r] >= first_sweep)
+            return fail(PB_EINVAL, "best_sweep must be in [-1, first_sweep)");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (I->topo == PB_TOPO_CSR)
+        return csr_anneal_resume(I, sched, replicas, seed, first_sweep, state, best_state, best_E, best_sweep, st, out);
+    if (I->topo == PB_TOPO_EA3D)
+        return ea_anneal_resume(I, sched, replicas, seed, first_sweep, state, best_state, best_E, best_sweep, st, out);
+    return fail(PB_EUNSUPPORTED,
+                "resume runs on EA cubes (resident form) and general sparse instances (a biclique via its edge list)");
+}
+
 pb_status pb_wait(pb_run* run, int32_t timeout_ms)
 {
     if (!run) return fail(PB_EINVAL, "null run");

@@ -176,6 +176,10 @@ pb_status ea_batch_launch(std::vector<pb_run*>& runs, const std::shared_ptr<Batc
 // Keep the EA kernels of a shared launch within `sms` SMs in total (split over
 // the coupling-type groups in proportion to their work).
 void ea_batch_limit_sms(BatchShared& shared, int sms);
+// The topology parts of pb_anneal_resume (arguments checked by the caller).
+pb_status csr_anneal_resume(pb_instance* I, const pb_schedule* sched, int32_t replicas, uint64_t seed,
+                            int32_t first_sweep, const int8_t* state, const int8_t* best_state, const double* best_E,
+                            const int32_t* best_sweep, cudaStream_t st, pb_run** out);
 int ea_choose_wt(const pb_instance* I, int R, int nF);
 pb_status bq_setup(pb_run* run, pb_instance* I, const pb_schedule* sc, int R, uint64_t seed,
                    const pb_anneal_opts* opts, cudaStream_t st);

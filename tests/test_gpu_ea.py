@@ -278,6 +278,44 @@ def test_full_size_batch_sampled(pb, orc):
 
 
 # ------------------------------------------------------------------- errors
+@pytest.mark.parametrize("L,R,hmax,s0", [(8, 64, 0, 23), (6, 20, 0, 1), (16, 48, 0, 40), (10, 9, 2, 11),
+                                         (32, 4, 0, 5)])
+def test_resume_split_equals_one_run(pb, L, R, hmax, s0):
+    """Checkpoint / resume on the resident form (fast and generic tiles, with and
+    without fields): sweeps 0..s0-1, then pb_anneal_resume from that run's final state
+    and running best, equal one uninterrupted run bit for bit."""
+    S, seed = 40, 8
+    J = syn.ea_couplings(L, "pm1", 60 + L)
+    h = syn.int_fields(L ** 3, hmax, 4) if hmax else None
+    betas = np.geomspace(0.1, 5.0, S)
+    full = pb.make_schedule(pb.PB_SCHED_EXPLICIT, S, betas=betas)
+    first = pb.make_schedule(pb.PB_SCHED_EXPLICIT, s0, betas=betas[:s0])
+    inst = pb.pb_create_instance(pb.PB_TOPO_EA3D, J, h, L=L)
+    N = L ** 3
+    opts = pb.make_opts(pb.PB_FORM_RESIDENT)
+
+    def read(run):
+        fe, be, bs = pb.pb_energy(run, R)
+        return dict(final_E=fe, best_E=be, best_sweep=bs, final_state=pb.pb_final_states(run, R, N),
+                    best_state=pb.pb_best_states(run, R, N))
+
+    runs = []
+    try:
+        runs.append(pb.pb_anneal(inst, full, R, seed, opts))
+        one = read(runs[-1])
+        runs.append(pb.pb_anneal(inst, first, R, seed, opts))
+        a = read(runs[-1])
+        runs.append(pb.pb_anneal_resume(inst, full, R, seed, s0, a["final_state"], a["best_state"], a["best_E"],
+                                        a["best_sweep"]))
+        b = read(runs[-1])
+    finally:
+        for r in runs:
+            pb.pb_run_destroy(r)
+        pb.pb_instance_destroy(inst)
+    for key in ("final_state", "best_state", "final_E", "best_E", "best_sweep"):
+        assert np.array_equal(b[key], one[key]), key
+
+
 def test_errors(pb):
     E = pb.PbError
     with pytest.raises(E) as ei:
