@@ -170,6 +170,35 @@ def oracle_sample(sweeps: int):
     return upd, dt
 
 
+def _oracle_replica(task):
+    """One host core's share of the all-cores CPU baseline: replica r of each job
+    for the first `sweeps` sweeps (the oracle as it stands, single-threaded)."""
+    sweeps, r = task
+    if r < 0:
+        return 0, 0.0  # pool warm-up
+    from oracle import oracle as orc
+    betas = orc.schedule(orc.SCHED_GEOMETRIC, BETA0, BETA1, S_SWEEPS)[:sweeps]
+    insts = [(L, orc.gen_ea(L, orc.DIST_PM1 if law == "pm1" else orc.DIST_GAUSS, seed)) for L, law, seed in JOBS]
+    t0 = time.perf_counter()
+    for L, J in insts:
+        orc.anneal_ea(L, J, None, betas, 1, 100, r_first=r)
+    return sum(L ** 3 * sweeps for L, _ in insts), time.perf_counter() - t0
+
+
+def oracle_sample_all_cores(sweeps: int, cores: int):
+    """The same sample spread over `cores` processes (spawned: no CUDA state is
+    inherited), replica r in process r; returns (updates, wall seconds of the
+    concurrent runs)."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_replica, [(0, -1)] * cores)  # start and import in every process first
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_replica, [(sweeps, r) for r in range(cores)], chunksize=1)
+        wall = time.perf_counter() - t0
+    return sum(u for u, _ in res), wall
+
+
 def run_reference(args, rank):
     if rank != 0:
         return
@@ -737,6 +766,11 @@ def main():
         u, dt = oracle_sample(3000)
         line["cpu_baseline"] = {"value": u / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": "replica 0 of each of the 4 jobs, first 3000 sweeps of the schedule"}
+        cores = max(1, os.cpu_count() or 1)
+        ua, wa = oracle_sample_all_cores(3000, cores)
+        line["cpu_baseline"]["all_cores"] = {
+            "value": ua / wa, "unit": UNIT, "cores": cores, "kind": "oracle, one process per core",
+            "sample": f"replicas 0..{cores - 1} (one per process) of each of the 4 jobs, first 3000 sweeps"}
     for i in insts:
         pb.pb_instance_destroy(i)
     if rank == 0:
