@@ -108,7 +108,7 @@ typedef enum pb_form {
     PB_FORM_AUTO = 0,      /* the autotuner's choice for the shape if it has one; else: EA resident where it fits,
                               else plain; biclique resident where it fits, else tensor */
     PB_FORM_PLAIN = 1,     /* EA: spins in global memory, one launch per colour class and sweep */
-    PB_FORM_RESIDENT = 2,  /* EA: one persistent launch, each replica block's lattice kept in shared memory;
+    PB_FORM_RESIDENT = 2,  /* EA: persistent kernels, each replica block's lattice kept in shared memory;
                               biclique (n <= 256 for +-1, n <= 128 for F32): one CTA per 32 replicas runs the
                               whole anneal with J, J^T and both sides' spins in shared memory */
     PB_FORM_CUDACORE = 3,  /* biclique: CUDA-core field (FP32 FMA; exact integers for +-1) */

@@ -4,8 +4,9 @@
 //
 // A batch prepares every job first (allocations, threshold tables, copies on
 // the caller's stream, one synchronisation), then launches:
-//   * all EA jobs that fit the resident form share ONE persistent launch,
-//     graph-captured, whose replica tiles are scheduled longest first;
+//   * all EA jobs that fit the resident form share ONE graph-captured launch of
+//     persistent kernels (one per coupling type, chained by programmatic
+//     dependent launch), whose replica tiles are scheduled longest first;
 //   * every biclique job (and every EA job too large for the resident form) is
 //     one graph-captured anneal, spread longest-first over the library's
 //     launch streams so that small jobs run side by side on separate SMs.

@@ -4,7 +4,7 @@
 //
 // Two forms compute identical trajectories (same random words, same fields,
 // same thresholds):
-//  * resident: one persistent launch; a CTA takes a tile (one job, 4*WT
+//  * resident: one persistent kernel per coupling type; a CTA takes a tile (one job, 4*WT
 //    replicas), keeps that tile's whole lattice in shared memory for all
 //    sweeps, and only touches global memory for best-state snapshots and the
 //    final state.  The shared-neighbour reuse of Sec. 1.2.2 is total: every

@@ -235,7 +235,7 @@ def test_f32_ensemble_mean_energy(pb, orc):
 # ------------------------------------------------ full size, sampled replicas
 def test_full_size_batch_sampled(pb, orc):
     """The benchmark's batch (L=16 and L=32, +-1 and Gaussian, 1024 replicas, 10^4
-    geometric sweeps 0.1 -> 5.0, one persistent launch): sampled replicas are
+    geometric sweeps 0.1 -> 5.0, one graph launch of the per-type persistent kernels): sampled replicas are
     replayed one by one on the oracle (bit-exact for +-1); every returned
     energy is checked against the oracle's FP64 energy of the returned state."""
     S, R = 10000, 1024
