@@ -530,6 +530,7 @@ CASES = {
     "ea-L16-pm1-small": ("ea", 16, "pm1", 2432, 50, "resident"),
     "ea-L24-pm1-small": ("ea", 24, "pm1", 608, 50, "resident"),      # generic tile (WT = 1)
     "ea-L12-pm1-small": ("ea", 12, "pm1", 2432, 50, "resident"),     # generic tile (WT = 4)
+    "ea-L24-gauss-small": ("ea", 24, "gauss", 608, 50, "resident"),  # generic tile, FP32
     "bq-n4096-R4096-pm1-tensor": ("bq", 4096, "pm1", 4096, 2, "tensor"),
     "bq-n4096-R4096-gauss-tensor": ("bq", 4096, "gauss", 4096, 2, "tensor"),
     "bq-n4096-R1024-pm1-cudacore": ("bq", 4096, "pm1", 1024, 1, "cudacore"),

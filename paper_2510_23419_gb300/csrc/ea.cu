@@ -263,7 +263,7 @@ __device__ void ea_tile(const EaJob& job, int tile, unsigned char* smem)
                     const float4 ja = __ldg(reinterpret_cast<const float4*>(job.inst.j6) + 2 * site);
                     const float4 jb = __ldg(reinterpret_cast<const float4*>(job.inst.j6) + 2 * site + 1);
                     const float jv[6] = {ja.x, ja.y, ja.z, ja.w, jb.x, jb.y};
-                    const float hv = __ldg(job.inst.hf + site);
+                    const float hv = jb.z;  // the site's field rides in the coupling vector
                     const uint32_t nb[6] = {n0, n1, n2, n3, n4, n5};
                     uint32_t snew = 0;
                     float F[4];
