@@ -24,22 +24,24 @@ __device__ __forceinline__ void pm1_row(const CsrJob& job, const uint32_t* m, in
     const int a0 = job.g.rowptr[i], a1 = job.g.rowptr[i + 1];
     int sumJ = 0;
     int d[4] = {0, 0, 0, 0};
-    uint32_t accp = 0, accn = 0;
-    int cnt = 0;
-    for (int a = a0; a < a1; ++a) {
-        const uint32_t w = m[(size_t)job.g.col[a] * job.Rw + q];
-        const int J = job.g.J8[a];
-        sumJ += J;
-        if (J > 0) accp += w; else accn += w;
-        if (++cnt == 255) {
-#pragma unroll
-            for (int b = 0; b < 4; ++b) d[b] += (int)byte_of(accp, b) - (int)byte_of(accn, b);
-            accp = accn = 0;
-            cnt = 0;
+    // byte-lane counters of the replicas' -1 spins under J = +1 (accp) and J = -1
+    // (accn), flushed every 255 neighbours so no byte overflows
+    for (int seg = a0; seg < a1; seg += 255) {
+        const int end = min(a1, seg + 255);
+        uint32_t accp = 0, accn = 0;
+        for (int a = seg; a < end; ++a) {
+            const uint32_t w = m[(size_t)job.g.col[a] * job.Rw + q];
+            const int J = job.g.J8[a];
+            sumJ += J;
+            const uint32_t pos = J > 0 ? w : 0u;
+            accp += pos;
+            accn += w - pos;
         }
+#pragma unroll
+        for (int b = 0; b < 4; ++b) d[b] += (int)byte_of(accp, b) - (int)byte_of(accn, b);
     }
 #pragma unroll
-    for (int b = 0; b < 4; ++b) G[b] = sumJ - 2 * (d[b] + (int)byte_of(accp, b) - (int)byte_of(accn, b));
+    for (int b = 0; b < 4; ++b) G[b] = sumJ - 2 * d[b];
 }
 
 template <typename T>
@@ -78,24 +80,41 @@ __global__ void __launch_bounds__(256) csr_init_kernel(CsrJob job)
 // its replica word and walks kCsrVpt spins of the class, adding the energy
 // change of every flip, -2 m_new F (Eq. 3 fields, exact integers for +-1); the
 // block then sums its lanes in a fixed order into the class chunk's partial.
-template <int JT>
+// TEMP: tempering (each replica slot has its own temperature); otherwise one
+// level for the launch, whose +-1 threshold window the block stages in shared
+// memory (windows wider than kCsrWinSmem stay in global memory).
+constexpr int kCsrWinSmem = 256;
+
+template <int JT, bool TEMP>
 __global__ void __launch_bounds__(kCsrLanesQ* kCsrLanesV) csr_class_kernel(CsrJob job, int c, int s)
 {
-    __shared__ double red[kCsrLanesV][kCsrLanesQ][4];
+    constexpr bool PM1 = JT == PB_J_PM1_I8;
+    __shared__ int32_t red_i[kCsrLanesV][kCsrLanesQ][4];
+    __shared__ float red_f[kCsrLanesV][kCsrLanesQ][4];
+    __shared__ uint32_t s_win[kCsrWinSmem];
     const int off = job.g.cls_off[c], ncls = job.g.cls_off[c + 1] - off;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int q = blockIdx.y * kCsrLanesQ + tx;
-    // annealing: one level for all replicas; tempering: each replica's own temperature
     TabWindow win{0, 0, 1};
     float cexp = 0.0f;
-    if (!job.temp) {
+    const uint32_t* wtab = nullptr;  // the window's entries (shared or global)
+    if constexpr (!TEMP) {
         const int lev = s / job.step;
-        if (JT == PB_J_PM1_I8)
+        if constexpr (PM1) {
             win = TabWindow{job.win[3 * lev + 2], job.win[3 * lev], job.win[3 * lev + 1]};
-        else
+            if (win.width <= kCsrWinSmem) {
+                for (int e = ty * kCsrLanesQ + tx; e < win.width; e += kCsrLanesQ * kCsrLanesV)
+                    s_win[e] = job.table[win.off + e];
+                __syncthreads();
+                wtab = s_win;
+            } else {
+                wtab = job.table + win.off;
+            }
+        } else {
             cexp = f32_cexp(job.betaf[lev]);
+        }
     }
-    long long di[4] = {0, 0, 0, 0};
+    int32_t di[4] = {0, 0, 0, 0};  // |changes| <= kCsrVpt * 2 (maxdeg + hmax): int32
     float df[4] = {0.f, 0.f, 0.f, 0.f};
     if (q < job.Rw) {
         for (int k = 0; k < kCsrVpt; ++k) {
@@ -107,22 +126,24 @@ __global__ void __launch_bounds__(kCsrLanesQ* kCsrLanesV) csr_class_kernel(CsrJo
             const uint32_t ws[4] = {r.x, r.y, r.z, r.w};
             const uint32_t wold = job.spins[(size_t)i * job.Rw + q];
             uint32_t w = 0;
-            if (JT == PB_J_PM1_I8) {
+            if constexpr (PM1) {
                 int G[4];
                 pm1_row(job, job.spins, i, q, G);
                 const int h = job.g.h8 ? job.g.h8[i] : 0;
 #pragma unroll
                 for (int b = 0; b < 4; ++b) {
-                    TabWindow wb = win;
-                    if (job.temp) {
-                        const int l = job.temp[4 * q + b];
-                        wb = TabWindow{job.win[3 * l + 2], job.win[3 * l], job.win[3 * l + 1]};
-                    }
                     const int F = G[b] + h;
-                    const int f = min(max(F - job.fmin, wb.lo), wb.lo + wb.width - 1) - wb.lo;
-                    const uint32_t nb = decide_bit(ws[b], job.table[wb.off + f]);
+                    uint32_t T;
+                    if constexpr (TEMP) {
+                        const int l = job.temp[4 * q + b];
+                        const TabWindow wb{job.win[3 * l + 2], job.win[3 * l], job.win[3 * l + 1]};
+                        T = job.table[wb.off + min(max(F - job.fmin, wb.lo), wb.lo + wb.width - 1) - wb.lo];
+                    } else {
+                        T = wtab[min(max(F - job.fmin - win.lo, 0), win.width - 1)];
+                    }
+                    const uint32_t nb = decide_bit(ws[b], T);
                     w |= nb << (8 * b);
-                    if (nb != byte_of(wold, b)) di[b] += nb ? 2LL * F : -2LL * F;  // -2 m_new F
+                    if (nb != byte_of(wold, b)) di[b] += nb ? 2 * F : -2 * F;  // -2 m_new F
                 }
             } else {
                 float G[4];
@@ -130,7 +151,7 @@ __global__ void __launch_bounds__(kCsrLanesQ* kCsrLanesV) csr_class_kernel(CsrJo
                 const float h = job.g.hf ? job.g.hf[i] : 0.0f;
 #pragma unroll
                 for (int b = 0; b < 4; ++b) {
-                    const float cb = job.temp ? f32_cexp(job.betaf[job.temp[4 * q + b]]) : cexp;
+                    const float cb = TEMP ? f32_cexp(job.betaf[job.temp[4 * q + b]]) : cexp;
                     const float F = G[b] + h;
                     const uint32_t nb = decide_f32(ws[b], F, cb);
                     w |= nb << (8 * b);
@@ -141,14 +162,19 @@ __global__ void __launch_bounds__(kCsrLanesQ* kCsrLanesV) csr_class_kernel(CsrJo
         }
     }
 #pragma unroll
-    for (int b = 0; b < 4; ++b) red[ty][tx][b] = JT == PB_J_PM1_I8 ? (double)di[b] : (double)df[b];
+    for (int b = 0; b < 4; ++b) {
+        if constexpr (PM1)
+            red_i[ty][tx][b] = di[b];
+        else
+            red_f[ty][tx][b] = df[b];
+    }
     __syncthreads();
     if (ty == 0 && q < job.Rw) {
         double* out = job.dpart + (size_t)(job.dchunk_off[c] + blockIdx.x) * 4 * job.Rw + 4 * q;
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
             double t = 0.0;
-            for (int v = 0; v < kCsrLanesV; ++v) t += red[v][tx][b];
+            for (int v = 0; v < kCsrLanesV; ++v) t += PM1 ? (double)red_i[v][tx][b] : (double)red_f[v][tx][b];
             out[b] = t;
         }
     }
@@ -346,10 +372,15 @@ cudaError_t csr_launch_class(const CsrJob& job, int c, int nchunks, int s, cudaS
     if (nchunks < 1) return cudaSuccess;
     const dim3 grid((unsigned)nchunks, (unsigned)((job.Rw + kCsrLanesQ - 1) / kCsrLanesQ));
     const dim3 block(kCsrLanesQ, kCsrLanesV);
-    if (job.g.jtype == PB_J_PM1_I8)
-        csr_class_kernel<PB_J_PM1_I8><<<grid, block, 0, st>>>(job, c, s);
+    const bool pm1 = job.g.jtype == PB_J_PM1_I8, temp = job.temp != nullptr;
+    if (pm1 && !temp)
+        csr_class_kernel<PB_J_PM1_I8, false><<<grid, block, 0, st>>>(job, c, s);
+    else if (pm1)
+        csr_class_kernel<PB_J_PM1_I8, true><<<grid, block, 0, st>>>(job, c, s);
+    else if (!temp)
+        csr_class_kernel<PB_J_F32, false><<<grid, block, 0, st>>>(job, c, s);
     else
-        csr_class_kernel<PB_J_F32><<<grid, block, 0, st>>>(job, c, s);
+        csr_class_kernel<PB_J_F32, true><<<grid, block, 0, st>>>(job, c, s);
     return cudaGetLastError();
 }
 
