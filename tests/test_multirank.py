@@ -100,3 +100,16 @@ def test_reference_arm_other_ranks_exit_quietly(capsys):
         steps, warmup, gpus = 1, 0, 2
     bench.run_reference(A(), rank=1)
     assert capsys.readouterr().out == ""
+
+
+def test_all_cores_oracle_sample_matches_single_process():
+    """The all-cores CPU baseline runs the unmodified oracle in spawned processes, one
+    replica each: its update count is the single-process sample's times the process
+    count, and every process computes (replica r of each job) independently."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from oracle import oracle as orc
+    orc.build()
+    u1, t1 = bench.oracle_sample(3)
+    u2, w2 = bench.oracle_sample_all_cores(3, 2)
+    assert u2 == 2 * u1 and t1 > 0 and w2 > 0
