@@ -188,11 +188,19 @@ struct EaFastTile {
             const uint32_t* bym = o + base0 + oym;
             const uint32_t* bz = o + base0;
             // the wrapping sites (z = 0 for the even pass, z = L-1 for the odd pass) are
-            // peeled; the others take their z neighbours at z +- 1
+            // peeled; the others take their z neighbours at z +- 1.  Two +-1 sites per
+            // iteration let their Philox chains overlap (no spills at 64 registers); the
+            // FP32 sites hold their couplings too and would spill, so they go one at a time.
             if (zp == 0) site<C, DECIDE>(0, 1, L - 1, bxp, bxm, byp, bym, bz, own, pre, cexp, uacc, ef);
+            if constexpr (PM1) {
+#pragma unroll 2
+                for (int z = 2 - zp; z < L - 1 - zp; z += 2)
+                    site<C, DECIDE>(z, z + 1, z - 1, bxp, bxm, byp, bym, bz, own, pre, cexp, uacc, ef);
+            } else {
 #pragma unroll 1
-            for (int z = 2 - zp; z < L - 1 - zp; z += 2)
-                site<C, DECIDE>(z, z + 1, z - 1, bxp, bxm, byp, bym, bz, own, pre, cexp, uacc, ef);
+                for (int z = 2 - zp; z < L - 1 - zp; z += 2)
+                    site<C, DECIDE>(z, z + 1, z - 1, bxp, bxm, byp, bym, bz, own, pre, cexp, uacc, ef);
+            }
             if (zp == 1) site<C, DECIDE>(L - 1, 0, L - 2, bxp, bxm, byp, bym, bz, own, pre, cexp, uacc, ef);
         }
     }
