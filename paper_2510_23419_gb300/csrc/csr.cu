@@ -8,6 +8,8 @@
 // decision (Eq. 2) with the Philox word of (class rank of i, s, word, colour).
 // Spins of one class have no edge between them, so the class is updated in
 // place.
+#include <algorithm>
+
 #include "csr_launch.h"
 #include "ea_kernels.cuh"
 
@@ -76,10 +78,16 @@ __global__ void __launch_bounds__(256) csr_init_kernel(CsrJob job)
     }
 }
 
-// Block (kCsrLanesQ replica words) x (kCsrLanesV vertex lanes); a thread keeps
-// its replica word and walks kCsrVpt spins of the class, adding the energy
-// change of every flip, -2 m_new F (Eq. 3 fields, exact integers for +-1); the
-// block then sums its lanes in a fixed order into the class chunk's partial.
+// Block (kCsrLanesQ replica words) x (kCsrLanesV vertex lanes); block x takes
+// the x-th of gridDim.x even, contiguous shares of the class's spins (the
+// class chunk) and its vertex lanes walk that share with stride kCsrLanesV.  A
+// thread keeps its replica word, adding the energy change of every flip,
+// -2 m_new F (Eq. 3 fields); the block sums its lanes in a fixed order, then
+// adds the +-1 sums (exact integers, so in any order) to the sweep's per-replica
+// accumulator with 64-bit atomics, or stores the FP32 sums as the class chunk's
+// partial.  Before a spin is overwritten, its value (the state at the end of the
+// previous sweep: a class is not touched by the other classes' launches) is
+// merged into the best state for the replicas whose energy improved then.
 // TEMP: tempering (each replica slot has its own temperature); otherwise one
 // level for the launch, whose +-1 threshold window the block stages in shared
 // memory (windows wider than kCsrWinSmem stay in global memory).
@@ -114,17 +122,23 @@ __global__ void __launch_bounds__(kCsrLanesQ* kCsrLanesV) csr_class_kernel(CsrJo
             cexp = f32_cexp(job.betaf[lev]);
         }
     }
-    int32_t di[4] = {0, 0, 0, 0};  // |changes| <= kCsrVpt * 2 (maxdeg + hmax): int32
+    int32_t di[4] = {0, 0, 0, 0};  // |changes| <= kCsrMaxVpt * 2 (maxdeg + hmax) < 2^31 (checked at setup)
     float df[4] = {0.f, 0.f, 0.f, 0.f};
     if (q < job.Rw) {
-        for (int k = 0; k < kCsrVpt; ++k) {
-            const int t = blockIdx.x * kCsrClassChunk + k * kCsrLanesV + ty;
-            if (t >= ncls) break;
+        const uint32_t fl = *reinterpret_cast<const uint32_t*>(job.improved + 4 * q);  // 4 flag bytes
+        const uint32_t fmask = fl * 0xFFu;                                             // 0x01 -> 0xFF per byte
+        const int t0 = (int)((long long)ncls * blockIdx.x / gridDim.x);
+        const int t1 = (int)((long long)ncls * (blockIdx.x + 1) / gridDim.x);
+        for (int t = t0 + ty; t < t1; t += kCsrLanesV) {
             const int i = job.g.cls_v[off + t];
             const U4 r = philox10((uint32_t)t, (uint32_t)s, (uint32_t)q, (kTagDecision << 24) | (uint32_t)c, job.key0,
                                   job.key1);
             const uint32_t ws[4] = {r.x, r.y, r.z, r.w};
             const uint32_t wold = job.spins[(size_t)i * job.Rw + q];
+            if (fmask) {
+                uint32_t* bp = job.best + (size_t)i * job.Rw + q;
+                *bp = (wold & fmask) | (*bp & ~fmask);
+            }
             uint32_t w = 0;
             if constexpr (PM1) {
                 int G[4];
@@ -170,12 +184,21 @@ __global__ void __launch_bounds__(kCsrLanesQ* kCsrLanesV) csr_class_kernel(CsrJo
     }
     __syncthreads();
     if (ty == 0 && q < job.Rw) {
-        double* out = job.dpart + (size_t)(job.dchunk_off[c] + blockIdx.x) * 4 * job.Rw + 4 * q;
+        if constexpr (PM1) {
 #pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            double t = 0.0;
-            for (int v = 0; v < kCsrLanesV; ++v) t += PM1 ? (double)red_i[v][tx][b] : (double)red_f[v][tx][b];
-            out[b] = t;
+            for (int b = 0; b < 4; ++b) {
+                long long t = 0;
+                for (int v = 0; v < kCsrLanesV; ++v) t += red_i[v][tx][b];
+                if (t) atomicAdd(job.dacc + 4 * q + b, (unsigned long long)t);
+            }
+        } else {
+            double* out = job.dpart + (size_t)(job.dchunk_off[c] + blockIdx.x) * 4 * job.Rw + 4 * q;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                double t = 0.0;
+                for (int v = 0; v < kCsrLanesV; ++v) t += (double)red_f[v][tx][b];
+                out[b] = t;
+            }
         }
     }
 }
@@ -228,18 +251,22 @@ __device__ __forceinline__ double csr_energy_of(const CsrJob& job, int r)
     return 0.5 * t;
 }
 
-// 32 replicas per block, 8 warps: warp w sums the class-chunk changes w, w + 8, ...
-// of its lane's replica, then the 8 warp sums are added in order.
-__global__ void __launch_bounds__(256) csr_sweep_end_kernel(CsrJob job, int s, int init)
+// 32 replicas per block.  +-1: the sweep's change is the accumulator, which is
+// reset for the next sweep; FP32: kSweepEndWarps warps, warp w sums the
+// class-chunk changes w, w + kSweepEndWarps, ... of its lane's replica, then
+// the warp sums are added in order.
+constexpr int kSweepEndWarps = 32;
+
+__global__ void __launch_bounds__(kSweepEndWarps * 32) csr_sweep_end_kernel(CsrJob job, int s, int init)
 {
-    __shared__ double acc[8][32];
+    __shared__ double acc[kSweepEndWarps][32];
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     const int r = blockIdx.x * 32 + lane;
     const bool live = r < 4 * job.Rw;
-    if (!init) {
+    if (!init && !job.dacc) {
         double t = 0.0;
         if (live)
-            for (int ch = wp; ch < job.ndchunk; ch += 8) t += job.dpart[(size_t)ch * 4 * job.Rw + r];
+            for (int ch = wp; ch < job.ndchunk; ch += kSweepEndWarps) t += job.dpart[(size_t)ch * 4 * job.Rw + r];
         acc[wp][lane] = t;
     }
     __syncthreads();
@@ -249,7 +276,12 @@ __global__ void __launch_bounds__(256) csr_sweep_end_kernel(CsrJob job, int s, i
         E = csr_energy_of(job, r);
     } else {
         double dE = 0.0;
-        for (int w = 0; w < 8; ++w) dE += acc[w][lane];
+        if (job.dacc) {
+            dE = (double)(long long)job.dacc[r];
+            job.dacc[r] = 0ull;
+        } else {
+            for (int w = 0; w < kSweepEndWarps; ++w) dE += acc[w][lane];
+        }
         E = job.E_cur[r] + dE;  // energy changes of the sweep's classes
     }
     job.E_cur[r] = E;
@@ -274,15 +306,19 @@ __global__ void __launch_bounds__(256) csr_sweep_end_kernel(CsrJob job, int s, i
 }
 
 // best <- spins for the replicas flagged as improved (byte masks per word).
+// A thread owns one replica word q and walks the vertices with a stride; it
+// reads its 4 flag bytes once and leaves at once when none is set, which late
+// in an anneal is nearly every word.
 __global__ void __launch_bounds__(256) csr_snapshot_kernel(CsrJob job)
 {
-    const long long total = (long long)job.g.N * job.Rw;
-    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (long long)gridDim.x * blockDim.x) {
-        const int q = (int)(idx % job.Rw);
-        const uint32_t f = *reinterpret_cast<const uint32_t*>(job.improved + 4 * q);  // 4 flag bytes
-        if (!f) continue;
-        const uint32_t mask = f * 0xFFu;  // 0x01 -> 0xFF per byte
+    const int q = blockIdx.x * 32 + (threadIdx.x & 31);
+    if (q >= job.Rw) return;
+    const uint32_t f = *reinterpret_cast<const uint32_t*>(job.improved + 4 * q);  // 4 flag bytes
+    if (!f) return;
+    const uint32_t mask = f * 0xFFu;  // 0x01 -> 0xFF per byte
+    const int N = job.g.N;
+    for (int i = blockIdx.y * 8 + (threadIdx.x >> 5); i < N; i += gridDim.y * 8) {
+        const size_t idx = (size_t)i * job.Rw + q;
         job.best[idx] = (job.spins[idx] & mask) | (job.best[idx] & ~mask);
     }
 }
@@ -367,6 +403,34 @@ cudaError_t csr_launch_init(const CsrJob& job, cudaStream_t st)
     return cudaGetLastError();
 }
 
+int csr_class_blocks(int jtype, bool temp, int Rw, int ncls, int maxdeg, int hmax)
+{
+    if (ncls <= 0) return 0;
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return -1;
+    const int threads = kCsrLanesQ * kCsrLanesV;
+    cudaError_t e;
+    if (jtype == PB_J_PM1_I8)
+        e = temp ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, csr_class_kernel<PB_J_PM1_I8, true>, threads, 0)
+                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, csr_class_kernel<PB_J_PM1_I8, false>, threads, 0);
+    else
+        e = temp ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, csr_class_kernel<PB_J_F32, true>, threads, 0)
+                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, csr_class_kernel<PB_J_F32, false>, threads, 0);
+    if (e != cudaSuccess || per_sm < 1) return -1;
+    // spins per thread: at most kCsrMaxVpt, and few enough that the int32 energy
+    // changes cannot overflow
+    const long long per_spin = 2LL * ((long long)maxdeg + hmax) + 1;
+    const long long vpt = std::max(1LL, std::min<long long>(kCsrMaxVpt, 0x7FFFFFFFLL / per_spin));
+    const long long gy = (Rw + kCsrLanesQ - 1) / kCsrLanesQ;
+    const long long wave = std::max(1LL, (long long)per_sm * sms / gy);  // class blocks per full wave
+    const long long lanes = ((long long)ncls + kCsrLanesV - 1) / kCsrLanesV;
+    const long long need = (lanes + vpt - 1) / vpt;  // fewest blocks within the per-thread cap
+    const long long waves = (need + wave - 1) / wave;
+    return (int)std::min(lanes, waves * wave);
+}
+
 cudaError_t csr_launch_class(const CsrJob& job, int c, int nchunks, int s, cudaStream_t st)
 {
     if (nchunks < 1) return cudaSuccess;
@@ -398,8 +462,15 @@ cudaError_t csr_launch_energy(const CsrJob& job, const uint32_t* m, int exact, c
 
 cudaError_t csr_launch_sweep_end(const CsrJob& job, int s, int init, cudaStream_t st)
 {
-    csr_sweep_end_kernel<<<(4 * job.Rw + 31) / 32, 256, 0, st>>>(job, s, init);
-    csr_snapshot_kernel<<<grid_for((long long)job.g.N * job.Rw), 256, 0, st>>>(job);
+    csr_sweep_end_kernel<<<(4 * job.Rw + 31) / 32, kSweepEndWarps * 32, 0, st>>>(job, s, init);
+    return cudaGetLastError();
+}
+
+cudaError_t csr_launch_snapshot(const CsrJob& job, cudaStream_t st)
+{
+    const int gx = (job.Rw + 31) / 32;
+    const int gy = std::max(1, std::min((job.g.N + 7) / 8, 152 * 8 / gx));
+    csr_snapshot_kernel<<<dim3((unsigned)gx, (unsigned)gy), 256, 0, st>>>(job);
     return cudaGetLastError();
 }
 

@@ -170,7 +170,7 @@ pb_status csr_build(pb_instance* I, int32_t N, int64_t E, const int32_t* eu, con
 // Buffers and tables of a run of R replicas over the levels `betas` (schedule
 // levels for annealing, the temperature ladder for tempering).
 static pb_status csr_prepare(pb_run* run, pb_instance* I, const std::vector<double>& betas, int step, int S, int R,
-                             uint64_t seed, const pb_anneal_opts* opts, cudaStream_t st)
+                             uint64_t seed, const pb_anneal_opts* opts, cudaStream_t st, bool temp = false)
 {
     run->inst = I;
     run->form = PB_FORM_PLAIN;
@@ -230,17 +230,23 @@ static pb_status csr_prepare(pb_run* run, pb_instance* I, const std::vector<doub
     std::vector<int32_t> doff((size_t)k + 1, 0);
     for (int c = 0; c < k; ++c) {
         const int ncls = I->csr_cls_off[(size_t)c + 1] - I->csr_cls_off[(size_t)c];
-        run->csr_nchunk[(size_t)c] = (ncls + kCsrClassChunk - 1) / kCsrClassChunk;
+        const int nb = csr_class_blocks(I->jtype, temp, j.Rw, ncls, I->maxdeg, I->hmax);
+        if (nb < 0) return fail(PB_EDEVICE, "occupancy query of the class kernel failed");
+        run->csr_nchunk[(size_t)c] = nb;
         doff[(size_t)c + 1] = doff[(size_t)c] + run->csr_nchunk[(size_t)c];
     }
     j.ndchunk = doff[(size_t)k];
     PB_ALLOC(run->extra[4], doff.size() * 4);
     PB_CUDA_TRY(cudaMemcpyAsync(run->extra[4].p, doff.data(), doff.size() * 4, cudaMemcpyHostToDevice, st));
-    PB_ALLOC(run->extra[5], (size_t)std::max(1, j.ndchunk) * 4 * j.Rw * 8);
-    PB_CUDA_TRY(cudaMemsetAsync(run->extra[5].p, 0, (size_t)std::max(1, j.ndchunk) * 4 * j.Rw * 8, st));
+    // +-1: one int64 accumulator per replica; FP32: a partial per class chunk
+    const bool pm1 = I->jtype == PB_J_PM1_I8;
+    const size_t dbytes = (pm1 ? (size_t)1 : (size_t)std::max(1, j.ndchunk)) * 4 * j.Rw * 8;
+    PB_ALLOC(run->extra[5], dbytes);
+    PB_CUDA_TRY(cudaMemsetAsync(run->extra[5].p, 0, dbytes, st));
     PB_CUDA_TRY(cudaStreamSynchronize(st));
     j.dchunk_off = run->extra[4].as<int32_t>();
-    j.dpart = run->extra[5].as<double>();
+    j.dpart = pm1 ? nullptr : run->extra[5].as<double>();
+    j.dacc = pm1 ? run->extra[5].as<unsigned long long>() : nullptr;
     j.spins = run->final_words.as<uint32_t>();
     j.best = run->best_words.as<uint32_t>();
     j.part = run->extra[0].as<double>();
@@ -279,7 +285,7 @@ static pb_status csr_setup_pt(pb_run* run, pb_instance* I, const double* ladder,
                               cudaStream_t st)
 {
     std::vector<double> lad(ladder, ladder + M);
-    pb_status ps = csr_prepare(run, I, lad, 1, S, M * C, seed, nullptr, st);
+    pb_status ps = csr_prepare(run, I, lad, 1, S, M * C, seed, nullptr, st, true);
     if (ps != PB_OK) return ps;
     CsrJob& j = run->cjob;
     j.M = M;
@@ -345,6 +351,7 @@ pb_status csr_launch(pb_run* run, cudaStream_t st)
         PB_CUDA_TRY(csr_launch_sweep_end(j, s, 0, st));
         if (j.temp) PB_CUDA_TRY(csr_launch_exchange(j, s, st));
     }
+    PB_CUDA_TRY(csr_launch_snapshot(j, st));  // the last sweep's improvements
     PB_CUDA_TRY(cudaEventRecord(run->ev_k1, st));
     PB_CUDA_TRY(csr_launch_readout(j, j.spins, run->final_pm.as<int8_t>(), run->E_out.as<double>(), st));
     PB_CUDA_TRY(csr_launch_readout(j, j.best, run->best_pm.as<int8_t>(), run->E_out.as<double>() + run->R, st));

@@ -41,7 +41,8 @@ struct CsrJob {
     double* part;            // [nchunk][4 Rw] energy partials (PM1: 2E as exact integers)
     int32_t ndchunk;         // class chunks of the sweep's energy changes, over all classes
     const int32_t* dchunk_off;  // [n_colours + 1] first class chunk of each class
-    double* dpart;           // [ndchunk][4 Rw] energy change of each class chunk in the last sweep
+    double* dpart;           // F32: [ndchunk][4 Rw] energy change of each class chunk in the last sweep
+    unsigned long long* dacc;  // PM1: [4 Rw] energy change of the sweep so far (int64 two's complement)
     double* E_best;          // [4 Rw]
     int32_t* best_sweep;     // [4 Rw]
     int32_t* hit_sweep;      // [4 Rw]
@@ -62,12 +63,17 @@ struct CsrJob {
 constexpr int kCsrChunk = 64;  // vertices per energy chunk
 constexpr int kCsrLanesQ = 32;  // class kernel: replica words per block
 constexpr int kCsrLanesV = 8;   // class kernel: vertex lanes per block
-constexpr int kCsrVpt = 4;      // class kernel: class spins per thread (measured: 4 beats 1, 2, 8)
-constexpr int kCsrClassChunk = kCsrLanesV * kCsrVpt;  // class spins per block
+constexpr int kCsrMaxVpt = 16;  // class kernel: most class spins one thread takes in a launch
 
 cudaError_t csr_launch_init(const CsrJob& job, cudaStream_t st);
+// Blocks (class chunks) of one class launch for a class of ncls spins: whole
+// waves of resident blocks (SMs x blocks per SM of the kernel variant), at most
+// kCsrMaxVpt spins per thread; a function of the device and the shapes only, so
+// a run's energy partials are summed in the same order whatever runs beside it.
+// -1 on a CUDA error.
+int csr_class_blocks(int jtype, bool temp, int Rw, int ncls, int maxdeg, int hmax);
 // Update of colour class c in sweep s (Eq. 2, Eq. 3) and its energy changes
-// (nchunks = class chunks of kCsrClassChunk spins).
+// (nchunks = csr_class_blocks(...) of the class).
 cudaError_t csr_launch_class(const CsrJob& job, int c, int nchunks, int s, cudaStream_t st);
 // Energy partials of the state `m` ([N][Rw] words); exact FP64 per term when exact != 0.
 cudaError_t csr_launch_energy(const CsrJob& job, const uint32_t* m, int exact, cudaStream_t st);
@@ -77,8 +83,11 @@ cudaError_t csr_launch_exchange(const CsrJob& job, int s, cudaStream_t st);
 // Running best after sweep s (init 1: the initial state, whose energy comes from
 // csr_launch_energy, becomes the best; init 2: a resumed run's state, whose
 // energy is set and whose given best is kept; init 0: later sweeps add the class
-// launches' energy changes to the previous energy), snapshot of improved replicas.
+// launches' energy changes to the previous energy) and the improved flags.  The
+// next sweep's class launches copy the flagged replicas' state into the best
+// state as they read it; csr_launch_snapshot does so after the last sweep.
 cudaError_t csr_launch_sweep_end(const CsrJob& job, int s, int init, cudaStream_t st);
+cudaError_t csr_launch_snapshot(const CsrJob& job, cudaStream_t st);
 // States [R][N] int8 +-1 and energies (from the partials of the same state) of `m`.
 cudaError_t csr_launch_readout(const CsrJob& job, const uint32_t* m, int8_t* out_pm, double* out_E, cudaStream_t st);
 // Fields F[r][i] = sum_j J_ij m_j + h_i of given +-1 states [R][N] (written as [R][N] float).
