@@ -19,29 +19,33 @@ namespace {
 
 __device__ __forceinline__ uint32_t byte_of(uint32_t w, int b) { return (w >> (8 * b)) & 0xFFu; }
 
-// sum_j J_ij (1 - 2 bit_j) for 4 replicas of a +-1 row: packed byte counters of
-// the set bits under J = +1 and J = -1, emptied every 255 neighbours.
+// Per-byte counts of the replicas' -1 spins over the neighbours x in [a, e),
+// added to d with sign sgn: packed byte counters, emptied every 255 neighbours
+// so no byte overflows.
+__device__ __forceinline__ void count_minus(const CsrJob& job, const uint32_t* m, int a, int e, int q, int sgn,
+                                            int (&d)[4])
+{
+    for (int seg = a; seg < e; seg += 255) {
+        const int end = min(e, seg + 255);
+        uint32_t acc = 0;
+#pragma unroll 4
+        for (int x = seg; x < end; ++x) acc += m[(size_t)job.g.col[x] * job.Rw + q];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) d[b] += sgn * (int)byte_of(acc, b);
+    }
+}
+
+// sum_j J_ij (1 - 2 bit_j) for 4 replicas of a +-1 row.  A row lists its
+// J = +1 neighbours first and its J = -1 neighbours from rowneg[i] on, so the
+// walk reads no coupling: G = sum_j J_ij - 2 (minus spins among the J = +1
+// neighbours - minus spins among the J = -1 neighbours).
 __device__ __forceinline__ void pm1_row(const CsrJob& job, const uint32_t* m, int i, int q, int (&G)[4])
 {
-    const int a0 = job.g.rowptr[i], a1 = job.g.rowptr[i + 1];
-    int sumJ = 0;
+    const int a0 = job.g.rowptr[i], an = job.g.rowneg[i], a1 = job.g.rowptr[i + 1];
     int d[4] = {0, 0, 0, 0};
-    // byte-lane counters of the replicas' -1 spins under J = +1 (accp) and J = -1
-    // (accn), flushed every 255 neighbours so no byte overflows
-    for (int seg = a0; seg < a1; seg += 255) {
-        const int end = min(a1, seg + 255);
-        uint32_t accp = 0, accn = 0;
-        for (int a = seg; a < end; ++a) {
-            const uint32_t w = m[(size_t)job.g.col[a] * job.Rw + q];
-            const int J = job.g.J8[a];
-            sumJ += J;
-            const uint32_t pos = J > 0 ? w : 0u;
-            accp += pos;
-            accn += w - pos;
-        }
-#pragma unroll
-        for (int b = 0; b < 4; ++b) d[b] += (int)byte_of(accp, b) - (int)byte_of(accn, b);
-    }
+    count_minus(job, m, a0, an, q, 1, d);
+    count_minus(job, m, an, a1, q, -1, d);
+    const int sumJ = (an - a0) - (a1 - an);
 #pragma unroll
     for (int b = 0; b < 4; ++b) G[b] = sumJ - 2 * d[b];
 }

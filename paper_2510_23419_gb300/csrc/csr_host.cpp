@@ -109,6 +109,23 @@ pb_status csr_build(pb_instance* I, int32_t N, int64_t E, const int32_t* eu, con
             else Jf[(size_t)a] = static_cast<const float*>(J)[e];
         }
     }
+    // +-1 rows: J = +1 half-edges first (stable), so the field walk needs no coupling
+    std::vector<int32_t> rowneg(pm1 ? (size_t)N : 0);
+    if (pm1) {
+        std::vector<int32_t> tc;
+        for (int32_t i = 0; i < N; ++i) {
+            const int32_t a0 = rowptr[i], a1 = rowptr[(size_t)i + 1];
+            tc.clear();
+            int32_t w = a0;
+            for (int32_t a = a0; a < a1; ++a) {
+                if (J8[(size_t)a] > 0) col[(size_t)w++] = col[(size_t)a];
+                else tc.push_back(col[(size_t)a]);
+            }
+            rowneg[(size_t)i] = w;
+            for (int32_t v : tc) col[(size_t)w++] = v;
+            for (int32_t a = a0; a < a1; ++a) J8[(size_t)a] = a < rowneg[(size_t)i] ? 1 : -1;
+        }
+    }
     int maxdeg = 0;
     for (int32_t i = 0; i < N; ++i) maxdeg = std::max(maxdeg, rowptr[(size_t)i + 1] - rowptr[i]);
     // classes in ascending index
@@ -132,7 +149,7 @@ pb_status csr_build(pb_instance* I, int32_t N, int64_t E, const int32_t* eu, con
     I->maxdeg = maxdeg;
     I->n_colours = k;
     I->csr_cls_off = cls_off;
-    DevBuf* B = I->csr_bufs;  // 0 rowptr, 1 col, 2 J, 3 h, 4 cls_off, 5 cls_v, 6 colour
+    DevBuf* B = I->csr_bufs;  // 0 rowptr, 1 col, 2 J, 3 h, 4 cls_off, 5 cls_v, 6 colour, 7 rowneg
     auto up = [&](DevBuf& b, const void* src, size_t bytes) -> pb_status {
         PB_ALLOC(b, bytes);
         if (bytes) PB_CUDA_TRY(cudaMemcpyAsync(b.p, src, bytes, cudaMemcpyHostToDevice, st));
@@ -146,6 +163,7 @@ pb_status csr_build(pb_instance* I, int32_t N, int64_t E, const int32_t* eu, con
     if ((ps = up(B[4], cls_off.data(), cls_off.size() * 4)) != PB_OK) return ps;
     if ((ps = up(B[5], cls_v.data(), cls_v.size() * 4)) != PB_OK) return ps;
     if ((ps = up(B[6], colour.data(), colour.size() * 4)) != PB_OK) return ps;
+    if (pm1 && (ps = up(B[7], rowneg.data(), rowneg.size() * 4)) != PB_OK) return ps;
     PB_CUDA_TRY(cudaStreamSynchronize(st));
     CsrDevice& g = I->csr;
     g = CsrDevice{};
@@ -157,6 +175,7 @@ pb_status csr_build(pb_instance* I, int32_t N, int64_t E, const int32_t* eu, con
     g.hmax = hmax;
     g.rowptr = B[0].as<int32_t>();
     g.col = B[1].as<int32_t>();
+    g.rowneg = pm1 ? B[7].as<int32_t>() : nullptr;
     g.J8 = pm1 ? B[2].as<int8_t>() : nullptr;
     g.Jf = pm1 ? nullptr : B[2].as<float>();
     g.h8 = (h && pm1) ? B[3].as<int8_t>() : nullptr;

@@ -8,12 +8,14 @@
 namespace pb {
 
 // Device copy of a general instance: each undirected edge (u, v, J) stored
-// from both ends in compressed rows; colour classes listed in ascending index,
+// from both ends in compressed rows (+-1 rows: the J = +1 half-edges first,
+// each part in edge order); colour classes listed in ascending index,
 // so a spin's position inside its class list is its class rank (the Philox
 // counter word 0).
 struct CsrDevice {
     int32_t N, jtype, n_colours, maxdeg, has_h, hmax;
     const int32_t* rowptr;   // [N + 1]
+    const int32_t* rowneg;   // PM1: [N] first half-edge of row i with J = -1 (J = +1 ones come first)
     const int32_t* col;      // [2E] neighbour of each half-edge
     const int8_t* J8;        // [2E] +-1 couplings (PM1)
     const float* Jf;         // [2E] real couplings (F32)
