@@ -70,8 +70,8 @@ __global__ void __launch_bounds__(256) csr_init_kernel(CsrJob job)
     for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (long long)gridDim.x * blockDim.x) {
         const int p = (int)(idx / job.Rw), q = (int)(idx - (long long)p * job.Rw);
-        const int i = job.g.cls_v[p];
-        const int c = job.g.colour[i];
+        const int i = p;  // label
+        const int c = job.g.colour[p];
         const uint32_t k = (uint32_t)(p - job.g.cls_off[c]);
         const U4 r = philox10(k, 0u, (uint32_t)q, (kTagInit << 24) | (uint32_t)c, job.key0, job.key1);
         const uint32_t ws[4] = {r.x, r.y, r.z, r.w};
@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(kCsrLanesQ* kCsrLanesV) csr_class_kernel(CsrJo
         const int t0 = (int)((long long)ncls * blockIdx.x / gridDim.x);
         const int t1 = (int)((long long)ncls * (blockIdx.x + 1) / gridDim.x);
         for (int t = t0 + ty; t < t1; t += kCsrLanesV) {
-            const int i = job.g.cls_v[off + t];
+            const int i = off + t;  // label
             const U4 r = philox10((uint32_t)t, (uint32_t)s, (uint32_t)q, (kTagDecision << 24) | (uint32_t)c, job.key0,
                                   job.key1);
             const uint32_t ws[4] = {r.x, r.y, r.z, r.w};
@@ -370,8 +370,9 @@ __global__ void __launch_bounds__(256) csr_states_kernel(CsrJob job, const uint3
     const long long total = (long long)job.R * job.g.N;
     for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (long long)gridDim.x * blockDim.x) {
-        const int r = (int)(idx / job.g.N), i = (int)(idx - (long long)r * job.g.N);
-        out[idx] = byte_of(m[(size_t)i * job.Rw + (r >> 2)], r & 3) ? (int8_t)-1 : (int8_t)1;
+        const int r = (int)(idx / job.g.N), i = (int)(idx - (long long)r * job.g.N);  // original order
+        const int p = job.g.pos[i];
+        out[idx] = byte_of(m[(size_t)p * job.Rw + (r >> 2)], r & 3) ? (int8_t)-1 : (int8_t)1;
     }
 }
 
@@ -386,12 +387,13 @@ __global__ void __launch_bounds__(256) csr_fields_kernel(CsrJob job, const int8_
     const long long total = (long long)job.R * job.g.N;
     for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (long long)gridDim.x * blockDim.x) {
-        const int r = (int)(idx / job.g.N), i = (int)(idx - (long long)r * job.g.N);
+        const int r = (int)(idx / job.g.N), i = (int)(idx - (long long)r * job.g.N);  // original order
+        const int p = job.g.pos[i];
         const int8_t* mr = st + (size_t)r * job.g.N;
-        float F = job.g.jtype == PB_J_PM1_I8 ? (job.g.h8 ? (float)job.g.h8[i] : 0.0f) : (job.g.hf ? job.g.hf[i] : 0.0f);
-        for (int a = job.g.rowptr[i]; a < job.g.rowptr[i + 1]; ++a) {
+        float F = job.g.jtype == PB_J_PM1_I8 ? (job.g.h8 ? (float)job.g.h8[p] : 0.0f) : (job.g.hf ? job.g.hf[p] : 0.0f);
+        for (int a = job.g.rowptr[p]; a < job.g.rowptr[p + 1]; ++a) {
             const float J = job.g.jtype == PB_J_PM1_I8 ? (float)job.g.J8[a] : job.g.Jf[a];
-            F = fmaf(J, (float)mr[job.g.col[a]], F);
+            F = fmaf(J, (float)mr[job.g.orig[job.g.col[a]]], F);
         }
         out[idx] = F;
     }

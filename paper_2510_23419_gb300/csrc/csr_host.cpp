@@ -89,19 +89,30 @@ pb_status csr_build(pb_instance* I, int32_t N, int64_t E, const int32_t* eu, con
         k = greedy_colouring(N, E, eu, ev, colour.data());
         if (k > 255) return fail(PB_ECOLOUR, "greedy colouring needs more than 255 colours");
     }
-    // compressed rows, half-edges in edge order
+    // classes in ascending index; a spin's label is its position in the class
+    // list, so class c holds the labels cls_off[c] .. cls_off[c+1]-1
+    std::vector<int32_t> cls_off((size_t)k + 1, 0);
+    for (int32_t i = 0; i < N; ++i) cls_off[(size_t)colour[i] + 1]++;
+    for (int c = 0; c < k; ++c) cls_off[(size_t)c + 1] += cls_off[c];
+    std::vector<int32_t> orig((size_t)N), pos((size_t)N), cf(cls_off.begin(), cls_off.end() - 1);
+    for (int32_t i = 0; i < N; ++i) {
+        const int32_t p = cf[colour[i]]++;
+        orig[(size_t)p] = i;
+        pos[(size_t)i] = p;
+    }
+    // compressed rows over the labels, half-edges in edge order
     std::vector<int32_t> rowptr((size_t)N + 1, 0);
     for (int64_t e = 0; e < E; ++e) {
-        rowptr[(size_t)eu[e] + 1]++;
-        rowptr[(size_t)ev[e] + 1]++;
+        rowptr[(size_t)pos[eu[e]] + 1]++;
+        rowptr[(size_t)pos[ev[e]] + 1]++;
     }
-    for (int32_t i = 0; i < N; ++i) rowptr[(size_t)i + 1] += rowptr[i];
+    for (int32_t p = 0; p < N; ++p) rowptr[(size_t)p + 1] += rowptr[p];
     std::vector<int32_t> col((size_t)(2 * E));
     std::vector<int8_t> J8(pm1 ? (size_t)(2 * E) : 0);
     std::vector<float> Jf(pm1 ? 0 : (size_t)(2 * E));
     std::vector<int32_t> fill(rowptr.begin(), rowptr.end() - 1);
     for (int64_t e = 0; e < E; ++e) {
-        const int32_t ends[2][2] = {{eu[e], ev[e]}, {ev[e], eu[e]}};
+        const int32_t ends[2][2] = {{pos[eu[e]], pos[ev[e]]}, {pos[ev[e]], pos[eu[e]]}};
         for (auto& uv : ends) {
             const int32_t a = fill[uv[0]]++;
             col[(size_t)a] = uv[1];
@@ -113,27 +124,30 @@ pb_status csr_build(pb_instance* I, int32_t N, int64_t E, const int32_t* eu, con
     std::vector<int32_t> rowneg(pm1 ? (size_t)N : 0);
     if (pm1) {
         std::vector<int32_t> tc;
-        for (int32_t i = 0; i < N; ++i) {
-            const int32_t a0 = rowptr[i], a1 = rowptr[(size_t)i + 1];
+        for (int32_t p = 0; p < N; ++p) {
+            const int32_t a0 = rowptr[p], a1 = rowptr[(size_t)p + 1];
             tc.clear();
             int32_t w = a0;
             for (int32_t a = a0; a < a1; ++a) {
                 if (J8[(size_t)a] > 0) col[(size_t)w++] = col[(size_t)a];
                 else tc.push_back(col[(size_t)a]);
             }
-            rowneg[(size_t)i] = w;
+            rowneg[(size_t)p] = w;
             for (int32_t v : tc) col[(size_t)w++] = v;
-            for (int32_t a = a0; a < a1; ++a) J8[(size_t)a] = a < rowneg[(size_t)i] ? 1 : -1;
+            for (int32_t a = a0; a < a1; ++a) J8[(size_t)a] = a < rowneg[(size_t)p] ? 1 : -1;
         }
     }
     int maxdeg = 0;
-    for (int32_t i = 0; i < N; ++i) maxdeg = std::max(maxdeg, rowptr[(size_t)i + 1] - rowptr[i]);
-    // classes in ascending index
-    std::vector<int32_t> cls_off((size_t)k + 1, 0);
-    for (int32_t i = 0; i < N; ++i) cls_off[(size_t)colour[i] + 1]++;
-    for (int c = 0; c < k; ++c) cls_off[(size_t)c + 1] += cls_off[c];
-    std::vector<int32_t> cls_v((size_t)N), cf(cls_off.begin(), cls_off.end() - 1);
-    for (int32_t i = 0; i < N; ++i) cls_v[(size_t)cf[colour[i]]++] = i;
+    for (int32_t p = 0; p < N; ++p) maxdeg = std::max(maxdeg, rowptr[(size_t)p + 1] - rowptr[p]);
+    // per-label colour and field
+    std::vector<int32_t> colour_l((size_t)N);
+    for (int32_t p = 0; p < N; ++p) colour_l[(size_t)p] = colour[orig[(size_t)p]];
+    std::vector<int8_t> h8l(h && pm1 ? (size_t)N : 0);
+    std::vector<float> hfl(h && !pm1 ? (size_t)N : 0);
+    for (int32_t p = 0; h && p < N; ++p) {
+        if (pm1) h8l[(size_t)p] = static_cast<const int8_t*>(h)[orig[(size_t)p]];
+        else hfl[(size_t)p] = static_cast<const float*>(h)[orig[(size_t)p]];
+    }
     int hmax = 0;
     if (h && pm1) {
         for (int32_t i = 0; i < N; ++i) hmax = std::max(hmax, std::abs((int)static_cast<const int8_t*>(h)[i]));
@@ -149,7 +163,8 @@ pb_status csr_build(pb_instance* I, int32_t N, int64_t E, const int32_t* eu, con
     I->maxdeg = maxdeg;
     I->n_colours = k;
     I->csr_cls_off = cls_off;
-    DevBuf* B = I->csr_bufs;  // 0 rowptr, 1 col, 2 J, 3 h, 4 cls_off, 5 cls_v, 6 colour, 7 rowneg
+    I->csr_orig = orig;
+    DevBuf* B = I->csr_bufs;  // 0 rowptr, 1 col, 2 J, 3 h, 4 cls_off, 5 orig, 6 colour, 7 rowneg, 8 pos
     auto up = [&](DevBuf& b, const void* src, size_t bytes) -> pb_status {
         PB_ALLOC(b, bytes);
         if (bytes) PB_CUDA_TRY(cudaMemcpyAsync(b.p, src, bytes, cudaMemcpyHostToDevice, st));
@@ -159,11 +174,12 @@ pb_status csr_build(pb_instance* I, int32_t N, int64_t E, const int32_t* eu, con
     if ((ps = up(B[0], rowptr.data(), rowptr.size() * 4)) != PB_OK) return ps;
     if ((ps = up(B[1], col.data(), col.size() * 4)) != PB_OK) return ps;
     if ((ps = pm1 ? up(B[2], J8.data(), J8.size()) : up(B[2], Jf.data(), Jf.size() * 4)) != PB_OK) return ps;
-    if (h && (ps = up(B[3], h, (size_t)N * (pm1 ? 1 : 4))) != PB_OK) return ps;
+    if (h && (ps = pm1 ? up(B[3], h8l.data(), h8l.size()) : up(B[3], hfl.data(), hfl.size() * 4)) != PB_OK) return ps;
     if ((ps = up(B[4], cls_off.data(), cls_off.size() * 4)) != PB_OK) return ps;
-    if ((ps = up(B[5], cls_v.data(), cls_v.size() * 4)) != PB_OK) return ps;
-    if ((ps = up(B[6], colour.data(), colour.size() * 4)) != PB_OK) return ps;
+    if ((ps = up(B[5], orig.data(), orig.size() * 4)) != PB_OK) return ps;
+    if ((ps = up(B[6], colour_l.data(), colour_l.size() * 4)) != PB_OK) return ps;
     if (pm1 && (ps = up(B[7], rowneg.data(), rowneg.size() * 4)) != PB_OK) return ps;
+    if ((ps = up(B[8], pos.data(), pos.size() * 4)) != PB_OK) return ps;
     PB_CUDA_TRY(cudaStreamSynchronize(st));
     CsrDevice& g = I->csr;
     g = CsrDevice{};
@@ -181,7 +197,8 @@ pb_status csr_build(pb_instance* I, int32_t N, int64_t E, const int32_t* eu, con
     g.h8 = (h && pm1) ? B[3].as<int8_t>() : nullptr;
     g.hf = (h && !pm1) ? B[3].as<float>() : nullptr;
     g.cls_off = B[4].as<int32_t>();
-    g.cls_v = B[5].as<int32_t>();
+    g.orig = B[5].as<int32_t>();
+    g.pos = B[8].as<int32_t>();
     g.colour = B[6].as<int32_t>();
     return PB_OK;
 }
@@ -434,17 +451,20 @@ pb_status csr_anneal_resume(pb_instance* I, const pb_schedule* sched, int32_t re
     CsrJob& j = run->cjob;
     j.s0 = first_sweep;
     run->resumed = true;
-    // [R][N] +-1 -> [N][Rw] words (byte b of word q: replica 4q + b, 1 <=> m = -1; padding replicas +1)
+    // [R][N] +-1 (original order) -> [N][Rw] words by label (byte b of word q: replica
+    // 4q + b, 1 <=> m = -1; padding replicas +1)
     const int64_t Rw = j.Rw;
     std::vector<uint32_t> w((size_t)(N * Rw)), wb((size_t)(N * Rw));
-    for (int64_t i = 0; i < N; ++i)
+    for (int64_t p = 0; p < N; ++p) {
+        const int64_t i = I->csr_orig[(size_t)p];
         for (int64_t r = 0; r < R; ++r) {
             const int8_t m = state[r * N + i], mb = best_state[r * N + i];
             if ((m != 1 && m != -1) || (mb != 1 && mb != -1)) return fail(PB_EINVAL, "states must hold +1 or -1");
             const uint32_t sh = 8u * (uint32_t)(r & 3);
-            w[(size_t)(i * Rw + (r >> 2))] |= (m < 0 ? 1u : 0u) << sh;
-            wb[(size_t)(i * Rw + (r >> 2))] |= (mb < 0 ? 1u : 0u) << sh;
+            w[(size_t)(p * Rw + (r >> 2))] |= (m < 0 ? 1u : 0u) << sh;
+            wb[(size_t)(p * Rw + (r >> 2))] |= (mb < 0 ? 1u : 0u) << sh;
         }
+    }
     std::vector<double> eb((size_t)(4 * Rw), 1e300);  // padding replicas: any state improves on it
     std::vector<int32_t> bs((size_t)(4 * Rw), -1);
     for (int64_t r = 0; r < R; ++r) {

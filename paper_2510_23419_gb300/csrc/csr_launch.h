@@ -7,23 +7,27 @@
 
 namespace pb {
 
-// Device copy of a general instance: each undirected edge (u, v, J) stored
-// from both ends in compressed rows (+-1 rows: the J = +1 half-edges first,
-// each part in edge order); colour classes listed in ascending index,
-// so a spin's position inside its class list is its class rank (the Philox
-// counter word 0).
+// Device copy of a general instance.  Spins carry labels: the classes are
+// listed one after the other, each in ascending original index, and a spin's
+// label is its position in that list, so class c is the label range
+// cls_off[c] .. cls_off[c+1]-1 and label - cls_off[c] is the class rank (the
+// Philox counter word 0).  Each undirected edge (u, v, J) is stored from both
+// ends in compressed rows over the labels (+-1 rows: the J = +1 half-edges
+// first, each part in edge order); fields and colours are per label.  States
+// cross the interface in the original order (orig / pos translate).
 struct CsrDevice {
     int32_t N, jtype, n_colours, maxdeg, has_h, hmax;
-    const int32_t* rowptr;   // [N + 1]
+    const int32_t* rowptr;   // [N + 1] rows by label
     const int32_t* rowneg;   // PM1: [N] first half-edge of row i with J = -1 (J = +1 ones come first)
     const int32_t* col;      // [2E] neighbour of each half-edge
     const int8_t* J8;        // [2E] +-1 couplings (PM1)
     const float* Jf;         // [2E] real couplings (F32)
     const int8_t* h8;        // [N] or null (PM1)
     const float* hf;         // [N] or null (F32)
-    const int32_t* cls_off;  // [n_colours + 1]
-    const int32_t* cls_v;    // [N] vertices of class c at cls_off[c] .. cls_off[c+1]-1, ascending
-    const int32_t* colour;   // [N]
+    const int32_t* cls_off;  // [n_colours + 1] first label of each class
+    const int32_t* orig;     // [N] original index of label p
+    const int32_t* pos;      // [N] label of original vertex i
+    const int32_t* colour;   // [N] colour of label p
 };
 
 // Spin words: 4 replicas per uint32, one byte each, byte = 0 <=> m = +1,

@@ -87,6 +87,7 @@ struct pb_instance {
     // general sparse instance
     int n_colours = 0;
     std::vector<int32_t> csr_cls_off;  // host copy of the class offsets
+    std::vector<int32_t> csr_orig;     // host copy of the original index of each label
     pb::CsrDevice csr{};
     pb::DevBuf csr_bufs[10];
 };
