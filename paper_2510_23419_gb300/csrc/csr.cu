@@ -50,6 +50,28 @@ __device__ __forceinline__ void pm1_row(const CsrJob& job, const uint32_t* m, in
     for (int b = 0; b < 4; ++b) G[b] = sumJ - 2 * d[b];
 }
 
+// pm1_row of a padded row: all kCsrEllSlots neighbour words are fetched at once
+// (unused slots read the zero row), then added to the J = +1 or J = -1 counter.
+__device__ __forceinline__ void pm1_row_ell(const CsrJob& job, const uint32_t* m, int p, int q, int (&G)[4])
+{
+    const int4 s0 = __ldg(job.g.ell + 2 * p), s1 = __ldg(job.g.ell + 2 * p + 1);
+    const int nd = __ldg(job.g.ell_nd + p);
+    const int np = nd & 0xFF, deg = nd >> 8;
+    const int nb[kCsrEllSlots] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
+    uint32_t w[kCsrEllSlots];
+#pragma unroll
+    for (int u = 0; u < kCsrEllSlots; ++u) w[u] = m[(size_t)nb[u] * job.Rw + q];
+    uint32_t accp = 0, accn = 0;  // at most 8 per byte: no overflow
+#pragma unroll
+    for (int u = 0; u < kCsrEllSlots; ++u) {
+        if (u < np) accp += w[u];
+        else accn += w[u];
+    }
+    const int sumJ = 2 * np - deg;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) G[b] = sumJ - 2 * ((int)byte_of(accp, b) - (int)byte_of(accn, b));
+}
+
 template <typename T>
 __device__ __forceinline__ void f32_row(const CsrJob& job, const uint32_t* m, int i, int q, T (&G)[4])
 {
@@ -146,7 +168,10 @@ __global__ void __launch_bounds__(kCsrLanesQ* kCsrLanesV) csr_class_kernel(CsrJo
             uint32_t w = 0;
             if constexpr (PM1) {
                 int G[4];
-                pm1_row(job, job.spins, i, q, G);
+                if (job.g.ell)
+                    pm1_row_ell(job, job.spins, i, q, G);
+                else
+                    pm1_row(job, job.spins, i, q, G);
                 const int h = job.g.h8 ? job.g.h8[i] : 0;
 #pragma unroll
                 for (int b = 0; b < 4; ++b) {

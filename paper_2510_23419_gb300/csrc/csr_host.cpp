@@ -139,6 +139,15 @@ pb_status csr_build(pb_instance* I, int32_t N, int64_t E, const int32_t* eu, con
     }
     int maxdeg = 0;
     for (int32_t p = 0; p < N; ++p) maxdeg = std::max(maxdeg, rowptr[(size_t)p + 1] - rowptr[p]);
+    // +-1, degree <= kCsrEllSlots: padded rows (unused slots name the zero row N)
+    const bool ell = pm1 && maxdeg <= kCsrEllSlots;
+    std::vector<int32_t> ellv(ell ? (size_t)N * kCsrEllSlots : 0, N);
+    std::vector<uint16_t> ellnd(ell ? (size_t)N : 0);
+    for (int32_t p = 0; ell && p < N; ++p) {
+        const int32_t a0 = rowptr[p], a1 = rowptr[(size_t)p + 1];
+        for (int32_t a = a0; a < a1; ++a) ellv[(size_t)p * kCsrEllSlots + (a - a0)] = col[(size_t)a];
+        ellnd[(size_t)p] = (uint16_t)((rowneg[(size_t)p] - a0) | ((a1 - a0) << 8));
+    }
     // per-label colour and field
     std::vector<int32_t> colour_l((size_t)N);
     for (int32_t p = 0; p < N; ++p) colour_l[(size_t)p] = colour[orig[(size_t)p]];
@@ -180,6 +189,8 @@ pb_status csr_build(pb_instance* I, int32_t N, int64_t E, const int32_t* eu, con
     if ((ps = up(B[6], colour_l.data(), colour_l.size() * 4)) != PB_OK) return ps;
     if (pm1 && (ps = up(B[7], rowneg.data(), rowneg.size() * 4)) != PB_OK) return ps;
     if ((ps = up(B[8], pos.data(), pos.size() * 4)) != PB_OK) return ps;
+    if (ell && (ps = up(B[9], ellv.data(), ellv.size() * 4)) != PB_OK) return ps;
+    if (ell && (ps = up(B[10], ellnd.data(), ellnd.size() * 2)) != PB_OK) return ps;
     PB_CUDA_TRY(cudaStreamSynchronize(st));
     CsrDevice& g = I->csr;
     g = CsrDevice{};
@@ -200,6 +211,8 @@ pb_status csr_build(pb_instance* I, int32_t N, int64_t E, const int32_t* eu, con
     g.orig = B[5].as<int32_t>();
     g.pos = B[8].as<int32_t>();
     g.colour = B[6].as<int32_t>();
+    g.ell = ell ? B[9].as<int4>() : nullptr;
+    g.ell_nd = ell ? B[10].as<uint16_t>() : nullptr;
     return PB_OK;
 }
 
@@ -251,7 +264,8 @@ static pb_status csr_prepare(pb_run* run, pb_instance* I, const std::vector<doub
     }
     const size_t words = (size_t)I->N * j.Rw;
     j.nchunk = (int)((I->N + kCsrChunk - 1) / kCsrChunk);
-    PB_ALLOC(run->final_words, words * 4);
+    PB_ALLOC(run->final_words, words * 4 + (size_t)j.Rw * 4);  // + the zero row of the padded rows
+    PB_CUDA_TRY(cudaMemsetAsync(run->final_words.as<uint32_t>() + words, 0, (size_t)j.Rw * 4, st));
     PB_ALLOC(run->best_words, words * 4);
     PB_ALLOC(run->extra[0], (size_t)j.nchunk * 4 * j.Rw * 8);
     PB_ALLOC(run->extra[1], (size_t)4 * j.Rw * 8);

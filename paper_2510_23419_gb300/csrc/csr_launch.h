@@ -28,6 +28,11 @@ struct CsrDevice {
     const int32_t* orig;     // [N] original index of label p
     const int32_t* pos;      // [N] label of original vertex i
     const int32_t* colour;   // [N] colour of label p
+    // +-1 instances of degree <= kCsrEllSlots (else null): row p as kCsrEllSlots
+    // labels (the J = +1 neighbours first), unused slots naming label N, whose
+    // spin words are kept zero; ell_nd[p] = (J = +1 count) | degree << 8
+    const int4* ell;         // [N][kCsrEllSlots / 4]
+    const uint16_t* ell_nd;  // [N]
 };
 
 // Spin words: 4 replicas per uint32, one byte each, byte = 0 <=> m = +1,
@@ -41,7 +46,7 @@ struct CsrJob {
     const int32_t* win;      // PM1: [levels][3] (lo, width, off)
     const float* betaf;      // F32: [levels]
     int32_t R, Rw;
-    uint32_t* spins;         // [N][Rw]
+    uint32_t* spins;         // [N][Rw] (+ one zero row, label N, for the padded rows)
     uint32_t* best;          // [N][Rw]
     int32_t nchunk;          // vertex chunks of the energy partials
     double* part;            // [nchunk][4 Rw] energy partials (PM1: 2E as exact integers)
@@ -69,6 +74,7 @@ struct CsrJob {
 constexpr int kCsrChunk = 64;  // vertices per energy chunk
 constexpr int kCsrLanesQ = 32;  // class kernel: replica words per block
 constexpr int kCsrLanesV = 8;   // class kernel: vertex lanes per block
+constexpr int kCsrEllSlots = 8;  // padded rows for +-1 instances of degree <= 8
 constexpr int kCsrMaxVpt = 16;  // class kernel: most class spins one thread takes in a launch
 
 cudaError_t csr_launch_init(const CsrJob& job, cudaStream_t st);

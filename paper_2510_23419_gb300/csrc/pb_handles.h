@@ -89,7 +89,7 @@ struct pb_instance {
     std::vector<int32_t> csr_cls_off;  // host copy of the class offsets
     std::vector<int32_t> csr_orig;     // host copy of the original index of each label
     pb::CsrDevice csr{};
-    pb::DevBuf csr_bufs[10];
+    pb::DevBuf csr_bufs[12];
 };
 
 namespace pb {
