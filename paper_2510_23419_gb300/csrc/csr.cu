@@ -52,6 +52,8 @@ __device__ __forceinline__ void pm1_row(const CsrJob& job, const uint32_t* m, in
 
 // pm1_row of a padded row: all kCsrEllSlots neighbour words are fetched at once
 // (unused slots read the zero row), then added to the J = +1 or J = -1 counter.
+// The words go through the read-only data path: a class launch never writes
+// another class's rows, and the zero row is never written.
 __device__ __forceinline__ void pm1_row_ell(const CsrJob& job, const uint32_t* m, int p, int q, int (&G)[4])
 {
     const int4 s0 = __ldg(job.g.ell + 2 * p), s1 = __ldg(job.g.ell + 2 * p + 1);
@@ -60,7 +62,7 @@ __device__ __forceinline__ void pm1_row_ell(const CsrJob& job, const uint32_t* m
     const int nb[kCsrEllSlots] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
     uint32_t w[kCsrEllSlots];
 #pragma unroll
-    for (int u = 0; u < kCsrEllSlots; ++u) w[u] = m[(size_t)nb[u] * job.Rw + q];
+    for (int u = 0; u < kCsrEllSlots; ++u) w[u] = __ldg(m + (size_t)nb[u] * job.Rw + q);
     uint32_t accp = 0, accn = 0;  // at most 8 per byte: no overflow
 #pragma unroll
     for (int u = 0; u < kCsrEllSlots; ++u) {
@@ -114,12 +116,13 @@ __global__ void __launch_bounds__(256) csr_init_kernel(CsrJob job)
 // partial.  Before a spin is overwritten, its value (the state at the end of the
 // previous sweep: a class is not touched by the other classes' launches) is
 // merged into the best state for the replicas whose energy improved then.
+// ELL: +-1 rows padded to kCsrEllSlots labels (degree <= kCsrEllSlots).
 // TEMP: tempering (each replica slot has its own temperature); otherwise one
 // level for the launch, whose +-1 threshold window the block stages in shared
 // memory (windows wider than kCsrWinSmem stay in global memory).
 constexpr int kCsrWinSmem = 256;
 
-template <int JT, bool TEMP>
+template <int JT, bool TEMP, bool ELL>
 __global__ void __launch_bounds__(kCsrLanesQ* kCsrLanesV) csr_class_kernel(CsrJob job, int c, int s)
 {
     constexpr bool PM1 = JT == PB_J_PM1_I8;
@@ -168,7 +171,7 @@ __global__ void __launch_bounds__(kCsrLanesQ* kCsrLanesV) csr_class_kernel(CsrJo
             uint32_t w = 0;
             if constexpr (PM1) {
                 int G[4];
-                if (job.g.ell)
+                if constexpr (ELL)
                     pm1_row_ell(job, job.spins, i, q, G);
                 else
                     pm1_row(job, job.spins, i, q, G);
@@ -443,12 +446,16 @@ int csr_class_blocks(int jtype, bool temp, int Rw, int ncls, int maxdeg, int hma
         return -1;
     const int threads = kCsrLanesQ * kCsrLanesV;
     cudaError_t e;
-    if (jtype == PB_J_PM1_I8)
-        e = temp ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, csr_class_kernel<PB_J_PM1_I8, true>, threads, 0)
-                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, csr_class_kernel<PB_J_PM1_I8, false>, threads, 0);
+    const bool ell = jtype == PB_J_PM1_I8 && maxdeg <= kCsrEllSlots;
+    if (jtype == PB_J_PM1_I8 && ell)
+        e = temp ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, csr_class_kernel<PB_J_PM1_I8, true, true>, threads, 0)
+                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, csr_class_kernel<PB_J_PM1_I8, false, true>, threads, 0);
+    else if (jtype == PB_J_PM1_I8)
+        e = temp ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, csr_class_kernel<PB_J_PM1_I8, true, false>, threads, 0)
+                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, csr_class_kernel<PB_J_PM1_I8, false, false>, threads, 0);
     else
-        e = temp ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, csr_class_kernel<PB_J_F32, true>, threads, 0)
-                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, csr_class_kernel<PB_J_F32, false>, threads, 0);
+        e = temp ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, csr_class_kernel<PB_J_F32, true, false>, threads, 0)
+                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, csr_class_kernel<PB_J_F32, false, false>, threads, 0);
     if (e != cudaSuccess || per_sm < 1) return -1;
     // spins per thread: at most kCsrMaxVpt, and few enough that the int32 energy
     // changes cannot overflow
@@ -468,14 +475,17 @@ cudaError_t csr_launch_class(const CsrJob& job, int c, int nchunks, int s, cudaS
     const dim3 grid((unsigned)nchunks, (unsigned)((job.Rw + kCsrLanesQ - 1) / kCsrLanesQ));
     const dim3 block(kCsrLanesQ, kCsrLanesV);
     const bool pm1 = job.g.jtype == PB_J_PM1_I8, temp = job.temp != nullptr;
-    if (pm1 && !temp)
-        csr_class_kernel<PB_J_PM1_I8, false><<<grid, block, 0, st>>>(job, c, s);
+    const bool ell = job.g.ell != nullptr;
+    if (pm1 && ell)
+        temp ? csr_class_kernel<PB_J_PM1_I8, true, true><<<grid, block, 0, st>>>(job, c, s)
+             : csr_class_kernel<PB_J_PM1_I8, false, true><<<grid, block, 0, st>>>(job, c, s);
     else if (pm1)
-        csr_class_kernel<PB_J_PM1_I8, true><<<grid, block, 0, st>>>(job, c, s);
+        temp ? csr_class_kernel<PB_J_PM1_I8, true, false><<<grid, block, 0, st>>>(job, c, s)
+             : csr_class_kernel<PB_J_PM1_I8, false, false><<<grid, block, 0, st>>>(job, c, s);
     else if (!temp)
-        csr_class_kernel<PB_J_F32, false><<<grid, block, 0, st>>>(job, c, s);
+        csr_class_kernel<PB_J_F32, false, false><<<grid, block, 0, st>>>(job, c, s);
     else
-        csr_class_kernel<PB_J_F32, true><<<grid, block, 0, st>>>(job, c, s);
+        csr_class_kernel<PB_J_F32, true, false><<<grid, block, 0, st>>>(job, c, s);
     return cudaGetLastError();
 }
 
