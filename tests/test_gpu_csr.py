@@ -82,6 +82,32 @@ def test_pm1_bit_exact(pb, orc, case):
         assert np.array_equal(g[key], o[key]), key
 
 
+@pytest.mark.parametrize("variant", ["isolated", "degree9"])
+def test_pm1_padded_row_limits(pb, orc, variant):
+    """The padded-row form (+-1, degree <= 8) at its edges: spins with no
+    neighbour (every slot names the zero row; F = h) and, one past the limit, a
+    hub of degree 9 (the compressed-row form); bit-exact against the oracle."""
+    N0 = 120
+    eu, ev = syn.graph_king(12, 10)
+    if variant == "isolated":
+        N = N0 + 7  # seven spins without edges
+    else:
+        N = N0 + 1  # a hub joined to 9 spins of the king graph
+        hub = np.full(9, N0, np.int32)
+        eu = np.concatenate([eu, hub])
+        ev = np.concatenate([ev, np.arange(0, 90, 10, dtype=np.int32)])
+    J = syn.edge_couplings(eu.size, "pm1", 91)
+    h = syn.int_fields(N, 3, 92)
+    col, k = pb.pb_greedy_colouring(N, eu, ev)
+    R, S = 21, 18
+    g, kg = _run(pb, N, eu, ev, J, h, None, pb.make_schedule(pb.PB_SCHED_LINEAR, S, 0.1, 3.0), R, 93)
+    assert kg == k
+    o = orc.anneal(eu, ev, J.astype(np.float64), h.astype(np.float64), col, orc.schedule(orc.SCHED_LINEAR, 0.1, 3.0, S),
+                   R, 93, n_colours=k)
+    for key in ("final_state", "best_state", "final_E", "best_E", "best_sweep"):
+        assert np.array_equal(g[key], o[key]), key
+
+
 def test_bench_size_sampled(pb, orc):
     """The general-graph bench configuration: odd periodic cube L = 25 (4 greedy
     colours), +-1, 1024 replicas (256 replica words), 20 sweeps; replicas 0, 513
