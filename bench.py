@@ -293,6 +293,26 @@ def make_instances(pb, jobs, stream):
     return insts, list(cache.values())
 
 
+def ks_2samp_p(a, b):
+    """p-value of the two-sample Kolmogorov-Smirnov test of two best-energy samples
+    (None when scipy is missing or a sample has fewer than two values)."""
+    try:
+        from scipy import stats
+    except ImportError:
+        return None
+    if np.asarray(a).size < 2 or np.asarray(b).size < 2:
+        return None
+    return float(stats.ks_2samp(np.asarray(a, np.float64), np.asarray(b, np.float64)).pvalue)
+
+
+def ks_summary(ps):
+    ps = [p for p in ps if p is not None]
+    if not ps:
+        return {"jobs": 0}
+    return {"jobs": len(ps), "p_at_least_0.01": sum(int(p >= 0.01) for p in ps), "min_p": min(ps),
+            "median_p": float(np.median(ps))}
+
+
 def mixed_block(pb, stream):
     """200 mixed instances in one batch (EA jobs in one persistent graph-captured launch,
     bicliques as graph-captured anneals side by side), forms from the autotuner; against
@@ -352,8 +372,9 @@ def mixed_block(pb, stream):
         pb.pb_run_destroy(r)
     # +-1 jobs: the same trajectories bit for bit; N(0,1) jobs (split BF16 tensor
     # products vs FP32 CUDA-core fields round differently): mean best energy per
-    # spin within 3 standard errors
-    pm1_same, g_ok, g_n = True, 0, 0
+    # spin within 3 standard errors; their best-energy distributions are also
+    # compared by a two-sample Kolmogorov-Smirnov test (p-values reported)
+    pm1_same, g_ok, g_n, ks_p = True, 0, 0, []
     for q, a, b in zip(sub, sbest, pbest):
         if jobs[q][2] == "pm1":
             pm1_same &= bool(np.array_equal(a, b))
@@ -361,6 +382,7 @@ def mixed_block(pb, stream):
             g_n += 1
             se = math.sqrt(a.var(ddof=1) / a.size + b.var(ddof=1) / b.size) if a.size > 1 else 0.0
             g_ok += int(abs(a.mean() - b.mean()) <= 3 * se + 1e-9 * abs(a.mean()))
+            ks_p.append(ks_2samp_p(a, b))
     for i in owned:
         pb.pb_instance_destroy(i)
     return {"workload": "200 instances, seed 7: EA L in {8,12,16,24} / biclique n in {128,...,2048}, +-1 / N(0,1), "
@@ -372,6 +394,7 @@ def mixed_block(pb, stream):
                 "jobs": len(sub), "updates": sub_upd, "batched_ms": sms, "plain_ms": pms,
                 "batched_value": sub_upd / (sms / 1e3), "plain_value": sub_upd / (pms / 1e3), "speedup": pms / sms,
                 "pm1_jobs_identical": pm1_same, "gauss_jobs_mean_within_3se": f"{g_ok}/{g_n}",
+                "gauss_jobs_ks_2samp": ks_summary(ks_p),
                 "plain_forms": "EA plain (one launch per colour and sweep), biclique FP32 CUDA-core"}}
 
 
