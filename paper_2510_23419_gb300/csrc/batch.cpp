@@ -67,20 +67,37 @@ bool tune_lookup(const pb_instance* I, int R, TuneEntry& out)
 }
 
 // ------------------------------------------------------------------ cost model
-// Rough device-time estimate (seconds) of a job, only used to order work
-// longest first; rates are round figures of the forms on one GB300.
-double est_cost(const pb_instance* I, int R, int S, int form)
+// Rough device-time estimate (seconds on the whole GPU) of a job, used to order
+// work longest first and to split the SMs between the EA launch and the other
+// jobs; rates are round figures of the forms on one GB300.  `compute` is the
+// part that needs SMs; the rest is per-sweep launch latency.
+double est_cost(const pb_instance* I, int R, int S, int form, double* compute = nullptr)
 {
     const double upd = (double)I->N * R * std::max(1, S);
-    if (I->topo == PB_TOPO_EA3D) return upd / (form == PB_FORM_PLAIN ? 9e10 : 7e11);
-    if (I->topo == PB_TOPO_CSR) return upd * std::max(1, I->maxdeg) / 4e11 + 3.0 * std::max(1, S) * 2e-6;
-    const double flop = upd * 2.0 * I->n * (I->jtype == PB_J_F32 ? 2.0 : 1.0);
-    if (form == PB_FORM_RESIDENT)  // one CTA per 32 replicas: ~8 us per sweep at n = 256 (+-1), FP32 ~4x slower
-        return std::max(1, S) * 8e-6 * (I->n / 256.0) * (I->n / 256.0) * (I->jtype == PB_J_F32 ? 4.0 : 1.0);
-    const double rate = form == PB_FORM_CUDACORE ? 2.5e13 : (I->jtype == PB_J_F32 ? 1.5e15 : 1.8e15);
-    // small instances fill a fraction of the tensor tiles
-    const double fill = form == PB_FORM_TENSOR ? std::min(1.0, (double)I->n / 256.0) * std::min(1.0, R / 256.0) : 1.0;
-    return flop / (rate * std::max(0.02, fill)) + 3.0 * std::max(1, S) * 2e-6;
+    double c, lat = 0.0;
+    if (I->topo == PB_TOPO_EA3D) {
+        // resident form: the fast tiles (L = 8, 16, 32) vs the generic tile, +-1 vs FP32
+        const bool fast = I->L == 8 || I->L == 16 || I->L == 32, f32 = I->jtype == PB_J_F32;
+        const double rate = form == PB_FORM_PLAIN ? 9e10 : fast ? (f32 ? 6e11 : 8.5e11) : (f32 ? 4e11 : 6e11);
+        c = upd / rate;
+    } else if (I->topo == PB_TOPO_CSR) {
+        c = upd * std::max(1, I->maxdeg) / 4e11;
+        lat = 3.0 * std::max(1, S) * 2e-6;
+    } else {
+        const double flop = upd * 2.0 * I->n * (I->jtype == PB_J_F32 ? 2.0 : 1.0);
+        if (form == PB_FORM_RESIDENT) {  // one CTA per 32 replicas: ~8 us per sweep at n = 256 (+-1), FP32 ~4x slower
+            c = std::max(1, S) * 8e-6 * (I->n / 256.0) * (I->n / 256.0) * (I->jtype == PB_J_F32 ? 4.0 : 1.0);
+        } else {
+            const double rate = form == PB_FORM_CUDACORE ? 2.5e13 : (I->jtype == PB_J_F32 ? 1.5e15 : 1.8e15);
+            // small instances fill a fraction of the tensor tiles
+            const double fill =
+                form == PB_FORM_TENSOR ? std::min(1.0, (double)I->n / 256.0) * std::min(1.0, R / 256.0) : 1.0;
+            c = flop / (rate * std::max(0.02, fill));
+            lat = 3.0 * std::max(1, S) * 2e-6;
+        }
+    }
+    if (compute) *compute = c;
+    return c + lat;
 }
 
 struct Job {
@@ -129,11 +146,12 @@ void choose_form(const pb_instance* I, int R, int requested, int& form, int& wt)
 // work already queued on `setup_st`.  With `join`, `setup_st` waits for every
 // job at the end.  `load` (per launch stream, seconds of queued work) picks the
 // stream of each job and is updated with the job's estimated cost; `costs`
-// receives each job's estimate.
+// receives each job's estimate.  `latency_first` (the request server) favours
+// the other jobs' latency over the batch's total time when splitting the SMs.
 pb_status batch_start(int count, pb_instance* const* insts, const pb_schedule* scheds, const int32_t* replicas,
                       const uint64_t* seeds, const pb_anneal_opts* opts, cudaStream_t setup_st, bool join,
                       std::vector<double>* load_io, std::vector<std::unique_ptr<pb_run>>& runs_out,
-                      std::vector<double>* costs, std::vector<int>* stream_of)
+                      std::vector<double>* costs, std::vector<int>* stream_of, bool latency_first)
 {
     TraceRange trace_prepare("batch: prepare");
     if (count < 1 || !insts || !scheds || !replicas || !seeds) return fail(PB_EINVAL, "null or empty batch");
@@ -201,15 +219,33 @@ pb_status batch_start(int count, pb_instance* const* insts, const pb_schedule* s
         pb_status ps = ea_batch_setup(resident, st, ea_shared);
         if (ps != PB_OK) return ps;
         // The persistent EA launch keeps every SM it is given until its last tile
-        // ends.  With other jobs in the batch it gets three quarters of the SMs
-        // (fewer if its own work is the smaller part), so that the other jobs --
-        // mostly short launches, bounded by latency more than by SMs -- run
-        // beside it instead of after it.
-        double ea_cost = 0.0, other = 0.0;
-        for (const Job& j : jobs) (j.form == PB_FORM_RESIDENT && j.I->topo == PB_TOPO_EA3D ? ea_cost : other) += j.cost;
-        if (other > 0.0) {
+        // ends, so with other jobs in the batch it gets a share of the SMs and
+        // the other jobs -- often short launches -- run beside it instead of
+        // after it.  For the batch's total time the share follows the EA part of
+        // the work that needs SMs (launch latency of the other jobs' sweeps does
+        // not), between a quarter and three quarters; for latency (the server)
+        // the EA launch gets three quarters only when its work dominates the
+        // others' whole time, else half.
+        double ea_cost = 0.0, other = 0.0, other_all = 0.0;
+        for (const Job& j : jobs) {
+            if (j.form == PB_FORM_RESIDENT && j.I->topo == PB_TOPO_EA3D) {
+                ea_cost += j.cost;
+            } else {
+                double c = 0.0;
+                est_cost(j.I, j.R, j.S, j.form, &c);
+                other += c;
+                other_all += j.cost;
+            }
+        }
+        if (other_all > 0.0) {
             const int sms = sm_count();
-            const int share = ea_cost >= other ? (3 * sms + 3) / 4 : std::max(sms / 4, (sms + 1) / 2);
+            int share;
+            if (latency_first) {
+                share = ea_cost >= other_all ? (3 * sms + 3) / 4 : std::max(sms / 4, (sms + 1) / 2);
+            } else {
+                const int prop = (int)std::lround(sms * ea_cost / (ea_cost + other));
+                share = std::min((3 * sms + 3) / 4, std::max(sms / 4, prop));
+            }
             ea_batch_limit_sms(*ea_shared, share);
         }
     }

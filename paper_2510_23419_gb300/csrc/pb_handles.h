@@ -199,5 +199,5 @@ void choose_form(const pb_instance* I, int R, int requested, int& form, int& wt)
 pb_status batch_start(int count, pb_instance* const* insts, const pb_schedule* scheds, const int32_t* replicas,
                       const uint64_t* seeds, const pb_anneal_opts* opts, cudaStream_t setup_st, bool join,
                       std::vector<double>* load_io, std::vector<std::unique_ptr<pb_run>>& runs_out,
-                      std::vector<double>* costs, std::vector<int>* stream_of);
+                      std::vector<double>* costs, std::vector<int>* stream_of, bool latency_first = false);
 }  // namespace pb

@@ -174,7 +174,7 @@ void pb_server::run_loop()
             {
                 TraceRange trace_("server: admission round");
                 ps = batch_start(m, insts.data(), scheds.data(), reps.data(), seeds.data(), os.data(), setup, false,
-                                 &load_copy, runs, &costs, &streams);
+                                 &load_copy, runs, &costs, &streams, /*latency_first=*/true);
             }
             const std::string err = ps == PB_OK ? std::string() : std::string(pb_last_error());
             lk.lock();
