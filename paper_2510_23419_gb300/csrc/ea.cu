@@ -423,6 +423,10 @@ __global__ void __launch_bounds__(kResidentThreads, 1)
                 ea_tile_fast<16, 4, PB_J_PM1_I8>(job, wk.tile, smem);
             else if (wk.path == kEaPathFast8)
                 ea_tile_fast<8, 16, PB_J_PM1_I8>(job, wk.tile, smem);
+            else if (wk.path == kEaPathGen24)  // compile-time shapes fold the index arithmetic
+                ea_tile<24, 1, PB_J_PM1_I8, false>(job, wk.tile, smem);
+            else if (wk.path == kEaPathGen12)
+                ea_tile<12, 4, PB_J_PM1_I8, false>(job, wk.tile, smem);
             else
                 ea_tile<0, 0, PB_J_PM1_I8, false>(job, wk.tile, smem);
         } else {
@@ -432,7 +436,7 @@ __global__ void __launch_bounds__(kResidentThreads, 1)
                 ea_tile_fast<16, 4, PB_J_F32>(job, wk.tile, smem);
             else if (wk.path == kEaPathFast8)
                 ea_tile_fast<8, 16, PB_J_F32>(job, wk.tile, smem);
-            else
+            else  // also kEaPathGen24 / kEaPathGen12: compile-time shapes here would spill
                 ea_tile<0, 0, PB_J_F32, false>(job, wk.tile, smem);
         }
     }

@@ -43,6 +43,8 @@ enum EaTilePath : int32_t {
     kEaPathFast16 = 2,         // L = 16, WT = 4
     kEaPathFast8 = 3,          // L = 8, WT = 16
     kEaPathGeneric = 4,        // any other even L <= 32
+    kEaPathGen24 = 5,          // generic tile with compile-time L = 24, WT = 1 (+-1 kernel; FP32: generic)
+    kEaPathGen12 = 6,          // generic tile with compile-time L = 12, WT = 4 (+-1 kernel; FP32: generic)
 };
 
 struct EaWork {
@@ -57,6 +59,8 @@ inline int32_t ea_tile_path(const EaJob& j)
     if (j.inst.L == 32 && j.WT == 1) return kEaPathFast32;
     if (j.inst.L == 16 && j.WT == 4) return kEaPathFast16;
     if (j.inst.L == 8 && j.WT == 16) return kEaPathFast8;
+    if (j.inst.L == 24 && j.WT == 1) return kEaPathGen24;
+    if (j.inst.L == 12 && j.WT == 4) return kEaPathGen12;
     return kEaPathGeneric;
 }
 
