@@ -3,11 +3,12 @@
 // Sec. 1.2.2 are the classes of a proper colouring, k >= 2 of them, updated in
 // turn).  One launch per colour class and sweep (the plain form).
 //
-// A thread owns one spin i of the class and one spin word (4 replicas):
-// F_r = sum_j J_ij m_j(r) + h_i (Eq. 3) over i's compressed row, then the p-bit
-// decision (Eq. 2) with the Philox word of (class rank of i, s, word, colour).
-// Spins of one class have no edge between them, so the class is updated in
-// place.
+// Spins carry class-contiguous labels (a class is a label range).  A thread
+// keeps one spin word (4 replicas) and walks its block's share of the class:
+// for each spin i, F_r = sum_j J_ij m_j(r) + h_i (Eq. 3) over i's row, then the
+// p-bit decision (Eq. 2) with the Philox word of (class rank of i, s, word,
+// colour).  Spins of one class have no edge between them, so the class is
+// updated in place.
 #include <algorithm>
 
 #include "csr_launch.h"
