@@ -396,6 +396,16 @@ pb_status pb_run_device_ms(pb_run* run, float* ms);
 pb_status pb_run_kernel_ms(pb_run* run, float* ms);
 void pb_run_destroy(pb_run* run);
 
+/* Measurement helper (no counterpart in the paper; it bounds the decision step of
+ * Eq. 2): the random-word ceiling of the EA update.  Runs a kernel that draws exactly
+ * the decision words an L = 32 resident tile draws (Philox4x32-10, the same counter
+ * layout, one 32-bit word per p-bit update) and does nothing else, on `blocks` CTAs of
+ * 1024 threads (0 = one per SM) for `sweeps` sweeps; blocks until done.  Outputs: ms,
+ * the kernel's duration (CUDA events on `stream`), and updates, the number of p-bit
+ * updates whose words it drew (blocks * 1024 * 128 * sweeps).  Errors: PB_EINVAL
+ * (null output, sweeps < 1), PB_EDEVICE. */
+pb_status pb_philox_ceiling(int32_t sweeps, int32_t blocks, void* stream, float* ms, double* updates);
+
 /* Local fields F_i = sum_j J_ij m_j + h_i (Eq. 3) of given states, computed on the
  * device with the same arithmetic the anneal kernels use for this instance
  * (integer for PM1; FP32 for EA F32).  states: host [R][N] int8 in {-1, +1};
@@ -415,22 +425,32 @@ pb_status pb_fields_ex(pb_instance* inst, const int8_t* states, int32_t R, int32
  * allocation and the synchronisation it can cause are not allowed.  It runs the
  * same resident kernel as pb_anneal (results are identical to pb_anneal with the
  * same arguments) but keeps every scratch buffer in one file-scope device array
- * of 16 MiB, which each GPU that loads this library holds until the process
- * exits.  Inputs and outputs are caller-owned DEVICE buffers:
+ * of 16 MiB, which each GPU holds until the process exits once the library's
+ * module holding it is loaded there.  CUDA may load modules lazily, so the first
+ * call on a device may be the one that loads the module and reserves the 16 MiB;
+ * callers that must not allocate later make one small warm-up call on each device
+ * first (outside their arena or real-time loop).  The first call on a device also
+ * looks up the array's device address (cudaGetSymbolAddress).
+ * Inputs and outputs are caller-owned DEVICE buffers:
  *   J_dev            [3][L^3] int8 +-1 couplings (same layout as pb_instance_desc.J), h = 0
  *   best_E_dev, final_E_dev     [replicas] double (exact int energies)
  *   best_sweep_dev   [replicas] int32
  *   best_states_dev, final_states_dev  [replicas][L^3] int8 +-1
- * The schedule is read from host memory during the call.  L must be even, in [2, 32].
- * A request whose scratch (about 2 * replicas * L^3 bytes plus the threshold
- * table of 52 bytes per beta level) exceeds 16 MiB is rejected with PB_EINVAL.
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * The schedule is read from host memory during the call.  L must be even
+ * (else PB_ECOLOUR) and in [2, 32] (else PB_EINVAL).  A request whose scratch
+ * (about 2 * replicas * L^3 bytes plus the threshold table of 52 bytes per beta
+ * level) exceeds 16 MiB is rejected with PB_EINVAL.  The call does not wait for
+ * earlier work on `stream`: it stages its small host-side descriptors and table
+ * (cudaMemcpyAsync from pageable host memory, which returns once the bytes are
+ * staged), queues the work and returns; results are ready when the stream
+ * reaches that point.  The couplings are checked on the GPU, so a J_dev
+ * holding a value other than +-1 is reported in the outputs, not by the return
+ * code: every best_sweep_dev entry is PB_NOALLOC_BAD_COUPLINGS and every energy
+ * is NaN (the states are then meaningless).
  * Every call uses the same array and leaves its contents behind: calls whose
  * work overlaps on the GPU (different streams, or threads without ordering)
- * race and corrupt each other -- order them on one stream.  The call returns
- * once the work is queued on `stream` (after a short synchronisation that
- * checks the couplings); results are ready when the stream reaches that point. */
+ * race and corrupt each other -- order them on one stream. */
+#define PB_NOALLOC_BAD_COUPLINGS (-2)
 pb_status pb_anneal_ea_noalloc(int32_t L, const int8_t* J_dev, const pb_schedule* sched, int32_t replicas,
                                uint64_t seed, double* best_E_dev, int32_t* best_sweep_dev, int8_t* best_states_dev,
                                double* final_E_dev, int8_t* final_states_dev, void* stream);

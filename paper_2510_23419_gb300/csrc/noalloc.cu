@@ -33,6 +33,9 @@ constexpr size_t kScratchBytes = 16u << 20;  // 16 MiB, held on every device tha
 
 // The scratch of pb_anneal_ea_noalloc.  In host code this name is only a
 // host-side stand-in; its device address comes from cudaGetSymbolAddress.
+// The library is built without relocatable device code and CUDA may load
+// modules lazily, so a device may reserve this array only when this file's
+// module is first used there -- normally inside the first call on that device.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
@@ -74,6 +77,19 @@ __global__ void __launch_bounds__(256) noalloc_jbits_kernel(const int8_t* __rest
         if (v < 0) bits |= (uint8_t)(1u << (2 + b));
     }
     jb[((x + y + z) & 1) * half + (i >> 1)] = bits;
+}
+
+// Couplings other than +-1 were seen (flag set by noalloc_jbits_kernel): mark every
+// replica's outputs so the caller can tell, without this call reading anything back.
+__global__ void __launch_bounds__(256) noalloc_mark_bad_kernel(const int* __restrict__ bad, int R, double* best_E,
+                                                               double* final_E, int32_t* best_sweep)
+{
+    if (*bad == 0) return;
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    best_E[r] = __longlong_as_double(0x7FF8000000000000LL);
+    final_E[r] = __longlong_as_double(0x7FF8000000000000LL);
+    best_sweep[r] = PB_NOALLOC_BAD_COUPLINGS;
 }
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
@@ -159,7 +175,7 @@ extern "C" pb_status pb_anneal_ea_noalloc(int32_t L, const int8_t* J_dev, const 
     for (int t = 0; t < n_tiles; ++t) work[t] = EaWork{0, t, ea_tile_path(j)};
 
     // Every call reuses the same array: reset what must start at zero (the tile
-    // counter); everything else is overwritten before it is read.
+    // counter and the bad-coupling flag); everything else is overwritten before it is read.
     int* bad = reinterpret_cast<int*>(S + o_ctr + 8);
     PB_CUDA_TRY(cudaMemsetAsync(S + o_ctr, 0, 16, st));
     PB_CUDA_TRY(cudaMemcpyAsync(S + o_job, &j, sizeof(EaJob), cudaMemcpyHostToDevice, st));
@@ -167,10 +183,6 @@ extern "C" pb_status pb_anneal_ea_noalloc(int32_t L, const int8_t* J_dev, const 
     PB_CUDA_TRY(cudaMemcpyAsync(S + o_tab, tab.data(), tab.size() * 4, cudaMemcpyHostToDevice, st));
     noalloc_jbits_kernel<<<(N + 255) / 256, 256, 0, st>>>(J_dev, L, S + o_jb, bad);
     PB_CUDA_TRY(cudaGetLastError());
-    int bad_h = 0;
-    PB_CUDA_TRY(cudaMemcpyAsync(&bad_h, bad, 4, cudaMemcpyDeviceToHost, st));
-    PB_CUDA_TRY(cudaStreamSynchronize(st));
-    if (bad_h) return fail(PB_EINVAL, "PM1 couplings must be +1 or -1");
 
     const size_t smem = ea_resident_smem(L, WT, PB_J_PM1_I8, 0, nF);
     PB_CUDA_TRY(ea_resident_set_smem(PB_J_PM1_I8, smem));
@@ -180,5 +192,9 @@ extern "C" pb_status pb_anneal_ea_noalloc(int32_t L, const int8_t* J_dev, const 
     PB_CUDA_TRY(ea_launch_readout(j, j.final_words, final_states_dev, final_E_dev, st));
     PB_CUDA_TRY(ea_launch_readout(j, j.best_words, best_states_dev, best_E_dev, st));
     PB_CUDA_TRY(cudaMemcpyAsync(best_sweep_dev, j.best_sweep, (size_t)replicas * 4, cudaMemcpyDeviceToDevice, st));
+    // the coupling check is reported in the outputs, so the call never waits for the GPU
+    noalloc_mark_bad_kernel<<<(replicas + 255) / 256, 256, 0, st>>>(bad, replicas, best_E_dev, final_E_dev,
+                                                                     best_sweep_dev);
+    PB_CUDA_TRY(cudaGetLastError());
     return PB_OK;
 }

@@ -23,6 +23,7 @@ PB_DIST_PM1, PB_DIST_GAUSS, PB_DIST_UNIF = 0, 1, 2
 PB_SCHED_LINEAR, PB_SCHED_GEOMETRIC, PB_SCHED_EXPLICIT = 0, 1, 2
 PB_FORM_AUTO, PB_FORM_PLAIN, PB_FORM_RESIDENT, PB_FORM_CUDACORE, PB_FORM_TENSOR = range(5)
 PB_FLAG_TEST_EXPIRE_WAITS = 0x40000000  # failure-path test hook (see include/pbit.h)
+PB_NOALLOC_BAD_COUPLINGS = -2  # best_sweep of pb_anneal_ea_noalloc when J_dev holds a value other than +-1
 
 _ERRNAMES = {0: "PB_OK", 1: "PB_EINVAL", 2: "PB_ECOLOUR", 3: "PB_ENOMEM", 4: "PB_EDEVICE", 5: "PB_ETIMEOUT",
              6: "PB_EBUSY", 7: "PB_EUNSUPPORTED"}
@@ -125,6 +126,7 @@ def load():
         "pb_fields": ([P, P, I32, P, I64, P], st),
         "pb_fields_ex": ([P, P, I32, I32, P, I64, P], st),
         "pb_anneal_ea_noalloc": ([I32, P, P, I32, U64, P, P, P, P, P, P], st),
+        "pb_philox_ceiling": ([I32, I32, P, P, P], st),
         "pb_create_graph_instance": ([P, P, P], st),
         "pb_greedy_colouring": ([I32, I64, P, P, P], I32),
         "pb_instance_colours": ([P], I32),
@@ -369,6 +371,14 @@ def pb_anneal_ea_noalloc(L: int, J_dev: int, sched: pb_schedule, replicas: int, 
                                        ctypes.c_void_p(best_E_dev), ctypes.c_void_p(best_sweep_dev),
                                        ctypes.c_void_p(best_states_dev), ctypes.c_void_p(final_E_dev),
                                        ctypes.c_void_p(final_states_dev), _stream(stream)))
+
+
+def pb_philox_ceiling(sweeps: int, blocks: int = 0, stream=None):
+    """(kernel ms, p-bit updates whose random words it drew) of the random-word ceiling kernel."""
+    ms = ctypes.c_float()
+    upd = ctypes.c_double()
+    _check(load().pb_philox_ceiling(sweeps, blocks, _stream(stream), ctypes.byref(ms), ctypes.byref(upd)))
+    return float(ms.value), float(upd.value)
 
 
 # ------------------------------------------------------- parallel tempering
