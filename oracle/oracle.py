@@ -13,6 +13,7 @@ What each function follows in the paper (arXiv 2510.23419):
   threshold         Eq. 2 p-bit, uint32 threshold reading (see the C file)
   schedule          Sec. 1.3.1 classical annealing, Algorithm 1's linear beta step
   anneal            Sec. 1.2.2 update groups + Sec. 1.3.1 classical annealing
+  class_step        one update-group step of that loop, from given states
   gen_ea/gen_biclique  Sec. 2 random cubic lattices / Sec. 3 random bicliques
   brute_force       exhaustive enumeration (Boltzmann law of Sec. 1.2.1)
 
@@ -80,6 +81,8 @@ def _load():
             lib.orc_anneal.argtypes = [i32, i64, P, P, P, P, P, i32, P, i32, i32, i32, u64,
                                        P, P, P, P, P, P, P]
             lib.orc_anneal.restype = ctypes.c_int
+            lib.orc_class_step.argtypes = [i32, i64, P, P, P, P, P, i32, i32, f64, i32, i32, i32, u64, P, P, P]
+            lib.orc_class_step.restype = ctypes.c_int
             lib.orc_pt.argtypes = [i32, i64, P, P, P, P, P, i32, P, i32, i32, i32, u64, P, P, P, P, P, P, P]
             lib.orc_pt.restype = ctypes.c_int
             _lib = lib
@@ -240,6 +243,33 @@ def anneal(eu, ev, J, h, colour, betas, R: int, seed: int, n_colours: int | None
     if trace:
         out["trace_E"] = tr
     return out
+
+
+def class_step(eu, ev, J, h, colour, c: int, beta: float, s: int, states, seed: int, r_first: int = 0,
+               n_colours: int | None = None) -> dict:
+    """One update-group step (Sec. 1.2.2) of sweep s at inverse temperature beta: colour class c of the
+    given states ([R, N] int8 +-1; row r is replica r_first + r) takes its decisions, every other spin
+    is kept.  Returns the new states, and per updated spin the FP64 probability P = 1/2 + tanh(beta F)/2
+    and the decision word w (NaN / 0 elsewhere)."""
+    colour = np.ascontiguousarray(colour, np.int32)
+    N = colour.size
+    m = np.array(states, dtype=np.int8, copy=True).reshape(-1, N)
+    R = m.shape[0]
+    eu = np.ascontiguousarray(eu, np.int32)
+    ev = np.ascontiguousarray(ev, np.int32)
+    J = np.ascontiguousarray(J, np.float64).reshape(-1)
+    hh = _h(h, N)
+    if n_colours is None:
+        n_colours = int(colour.max()) + 1
+    P = np.full((R, N), np.nan)
+    w = np.zeros((R, N), np.uint32)
+    rc = _load().orc_class_step(N, eu.size, _p(eu), _p(ev), _p(J), _p(hh), _p(colour), n_colours, c, float(beta), s,
+                                r_first, R, seed, _p(m), _p(P), _p(w))
+    if rc == -2:
+        raise ValueError("colouring has an edge inside a colour class")
+    if rc != 0:
+        raise ValueError(f"oracle class step failed ({rc})")
+    return dict(state=m, P=P, w=w)
 
 
 def anneal_ea(L: int, J, h, betas, R: int, seed: int, **kw) -> dict:

@@ -374,6 +374,56 @@ int orc_anneal(int32_t N, int64_t n_edges, const int32_t* eu, const int32_t* ev,
     return 0;
 }
 
+/* ------------------------------------------------------------------------ */
+/* One update-group step of the annealing loop above, from given states: the  */
+/* spins of colour class c of replicas r_first .. r_first+R-1 take their      */
+/* decisions of sweep s at inverse temperature beta (Eq. 3 field in FP64 from */
+/* the given state, Eq. 2 decision with the tag-0 word of counter             */
+/* (k, s, r >> 2, c), word r & 3); all other spins are left as they are.      */
+/* m is [R][N] in/out.  Optional outputs per updated spin: P_out [R][N] the   */
+/* FP64 probability 1/2 + tanh(beta F)/2 and w_out [R][N] the random word     */
+/* (other entries untouched).  Returns 0, -1 on bad arguments, -2 if the      */
+/* colouring has an internal edge, -3 on allocation failure.                  */
+/* ------------------------------------------------------------------------ */
+int orc_class_step(int32_t N, int64_t n_edges, const int32_t* eu, const int32_t* ev, const double* J,
+                   const double* h, const int32_t* colour, int32_t n_colours, int32_t c, double beta, int32_t s,
+                   int32_t r_first, int32_t R, uint64_t seed, int8_t* m, double* P_out, uint32_t* w_out)
+{
+    if (N < 1 || R < 0 || r_first < 0 || s < 0 || n_colours < 1 || n_colours > 255 || c < 0 || c >= n_colours)
+        return -1;
+    for (int32_t i = 0; i < N; ++i)
+        if (colour[i] < 0 || colour[i] >= n_colours) return -1;
+    if (orc_count_monochrome(n_edges, eu, ev, colour) != 0) return -2;
+    uint32_t* rank = (uint32_t*)malloc((size_t)N * sizeof(uint32_t));
+    double* F = (double*)malloc((size_t)N * sizeof(double));
+    if (!rank || !F) {
+        free(rank); free(F);
+        return -3;
+    }
+    for (int32_t cc = 0; cc < n_colours; ++cc) {
+        uint32_t k = 0;
+        for (int32_t i = 0; i < N; ++i)
+            if (colour[i] == cc) rank[i] = k++;
+    }
+    for (int32_t r = 0; r < R; ++r) {
+        const int32_t rg = r_first + r;
+        int8_t* mr = m + (int64_t)r * N;
+        /* fields of the given state; class c has no internal edge, so they do not
+           change while the class is updated */
+        orc_fields(N, n_edges, eu, ev, J, h, mr, F);
+        for (int32_t i = 0; i < N; ++i) {
+            if (colour[i] != c) continue;
+            uint32_t w = orc_rand_word(seed, rank[i], (uint32_t)s, (uint32_t)(rg >> 2),
+                                       (ORC_TAG_DECISION << 24) | (uint32_t)c, rg & 3);
+            mr[i] = (w < orc_threshold(beta, F[i])) ? 1 : -1;
+            if (P_out) P_out[(int64_t)r * N + i] = 0.5 + 0.5 * tanh(beta * F[i]);
+            if (w_out) w_out[(int64_t)r * N + i] = w;
+        }
+    }
+    free(rank); free(F);
+    return 0;
+}
+
 /* ------------------------------------------------------------------------
  * Parallel tempering (replica exchange; Hukushima & Nemoto, J. Phys. Soc. Jpn.
  * 65, 1604 (1996)), named by the paper as a better PC solving method

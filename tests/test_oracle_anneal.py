@@ -101,3 +101,61 @@ def test_bad_colouring_rejected(orc):
     col[0] = 1
     with pytest.raises(ValueError):
         orc.anneal(eu, ev, np.ones(9), None, col, np.zeros(1), 1, 1)
+
+
+def _iterate_class_steps(orc, eu, ev, J, h, col, betas, R, seed, r_first=0):
+    """Initial state of the anneal (zero sweeps), then every class of every sweep by class_step."""
+    k = int(col.max()) + 1
+    m = orc.anneal(eu, ev, J, h, col, np.zeros(0), R, seed, n_colours=k, r_first=r_first)["final_state"]
+    for s, beta in enumerate(betas):
+        for c in range(k):
+            m = orc.class_step(eu, ev, J, h, col, c, beta, s, m, seed, r_first=r_first, n_colours=k)["state"]
+    return m
+
+
+@pytest.mark.parametrize("kind", ["ea_pm1_h", "ea_gauss_h", "biclique_unif", "three_colour"])
+def test_class_steps_replay_the_anneal(orc, kind):
+    """The one-class step reproduces the annealing loop: iterating it over every class of
+    every sweep from the initial state gives the anneal's final state, replica for replica
+    (replicas offset by r_first so the counters' replica words are exercised)."""
+    rng = np.random.default_rng(5)
+    if kind.startswith("ea"):
+        L = 4
+        eu, ev, col = orc.ea_graph(L)
+        J = orc.gen_ea(L, orc.DIST_PM1 if "pm1" in kind else orc.DIST_GAUSS, 9).reshape(-1)
+        h = rng.integers(-2, 3, size=L ** 3).astype(float) if "pm1" in kind else rng.normal(size=L ** 3)
+    elif kind == "biclique_unif":
+        n = 6
+        eu, ev, col = orc.biclique_graph(n)
+        J = orc.gen_biclique(n, orc.DIST_UNIF, 4).reshape(-1)
+        h = None
+    else:  # 5-cycle with a chord: 3 colours
+        eu = np.array([0, 1, 2, 3, 4, 0], np.int32)
+        ev = np.array([1, 2, 3, 4, 0, 2], np.int32)
+        col = np.array([0, 1, 2, 0, 1], np.int32)
+        J = rng.normal(size=6)
+        h = rng.normal(size=5)
+    betas = orc.schedule(orc.SCHED_GEOMETRIC, 0.1, 4.0, 25)
+    R, seed, r0 = 6, 17, 5
+    ref = orc.anneal(eu, ev, J, h, col, betas, R, seed, n_colours=int(col.max()) + 1, r_first=r0)
+    got = _iterate_class_steps(orc, eu, ev, J, h, col, betas, R, seed, r_first=r0)
+    assert np.array_equal(got, ref["final_state"])
+
+
+def test_class_step_outputs(orc):
+    """Only the stepped class changes; P is the p-bit law of the spin's field and the
+    new spin is +1 exactly when the word is below floor(P 2^32)."""
+    L = 4
+    eu, ev, col = orc.ea_graph(L)
+    J = orc.gen_ea(L, orc.DIST_GAUSS, 2).reshape(-1)
+    m0 = np.random.default_rng(3).choice(np.array([-1, 1], np.int8), size=(3, L ** 3))
+    out = orc.class_step(eu, ev, J, None, col, 1, 0.7, 4, m0, 8)
+    assert np.array_equal(out["state"][:, col == 0], m0[:, col == 0])
+    assert np.all(np.isnan(out["P"][:, col == 0])) and np.all(out["w"][:, col == 0] == 0)
+    for r in range(3):
+        F = orc.fields(eu, ev, J, None, m0[r])
+        for i in np.flatnonzero(col == 1)[:20]:
+            P = 0.5 + 0.5 * np.tanh(0.7 * F[i])
+            assert out["P"][r, i] == pytest.approx(P, rel=0, abs=1e-15)  # libm vs numpy tanh: last ulps
+            T = min(int(np.floor(out["P"][r, i] * 2.0 ** 32)), 2 ** 32 - 1)
+            assert out["state"][r, i] == (1 if int(out["w"][r, i]) < T else -1)
