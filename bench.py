@@ -223,14 +223,89 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------- measured peaks
+def measure_dense_peaks(n: int = 8192, reps: int = 10):
+    """Dense tensor peaks of this GPU, measured the way the BF16 figure of the
+    driver's peak file is: n^3 products, best of `reps`, CUDA events.  FP8 e4m3 with
+    torch._scaled_mm (per-tensor unit scales, BF16 output); BF16 with torch.matmul.
+    TFLOP/s = 2 n^3 / time."""
+    import torch
+    out = {"n": n, "reps": reps}
+
+    def best_of(fn):
+        fn()
+        torch.cuda.synchronize()
+        best = math.inf
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        return 2.0 * n ** 3 / (best / 1e3) / 1e12
+
+    g = torch.Generator(device="cuda").manual_seed(0)
+    a16 = torch.randn(n, n, device="cuda", dtype=torch.bfloat16, generator=g)
+    b16 = torch.randn(n, n, device="cuda", dtype=torch.bfloat16, generator=g)
+    out["bf16_tflops"] = best_of(lambda: torch.matmul(a16, b16))
+    try:
+        a8 = a16.to(torch.float8_e4m3fn)
+        b8 = b16.t().contiguous().to(torch.float8_e4m3fn).t()   # column-major second operand
+        one = torch.ones((), device="cuda", dtype=torch.float32)
+        out["fp8_tflops"] = best_of(lambda: torch._scaled_mm(a8, b8, scale_a=one, scale_b=one,
+                                                             out_dtype=torch.bfloat16))
+        out["fp8_how"] = "torch._scaled_mm e4m3 x e4m3 -> bf16, unit per-tensor scales"
+    except Exception as e:  # noqa: BLE001 -- report why, keep the bench going
+        out["fp8_tflops"] = None
+        out["fp8_error"] = str(e)[:200]
+    del a16, b16
+    torch.cuda.empty_cache()
+    return out
+
+
+def philox_ceiling(pb, stream, sweeps: int = 200):
+    """Measured random-word ceiling of the EA update (one Philox4x32-10 word per update,
+    same counters as the resident tiles, nothing else): updates/s, best of 3."""
+    best = 0.0
+    for _ in range(3):
+        ms, upd = pb.pb_philox_ceiling(sweeps, 0, stream=stream)
+        best = max(best, upd / (ms / 1e3))
+    return best
+
+
 # ------------------------------------------------------------ biclique
+def split_field_error(pb, stream, n: int = 4096, states: int = 4):
+    """Error of the split hi + lo BF16 tensor-core field against FP64 (numpy) on the
+    bench's biclique size: N(0,1) and U(-1,1) couplings, random +-1 states and the
+    all-+1 state; |F - F64| relative to sum_j |J_ij| (max and mean over spins)."""
+    import synth_inputs as syn
+    out = {"n": n, "states": states, "unit": "|F_tensor - F_fp64| / sum_j |J_ij|"}
+    for law, dist in (("gauss", pb.PB_DIST_GAUSS), ("unif", pb.PB_DIST_UNIF)):
+        J = pb.pb_generate_biclique(n, dist, 11)
+        inst = pb.pb_create_instance(pb.PB_TOPO_BICLIQUE, J, None, n=n, stream=stream)
+        m = np.concatenate([syn.states(states - 1, 2 * n, 5), np.ones((1, 2 * n), np.int8)])
+        F = pb.pb_fields_ex(inst, m, pb.PB_FORM_TENSOR, stream=stream).astype(np.float64)
+        pb.pb_instance_destroy(inst)
+        Jd = J.astype(np.float64)
+        A = np.abs(Jd)
+        scale = np.concatenate([A.sum(axis=1), A.sum(axis=0)])
+        mf = m.astype(np.float64)
+        F64 = np.concatenate([mf[:, n:] @ Jd.T, mf[:, :n] @ Jd], axis=1)   # left: J m_right, right: J^T m_left
+        rel = np.abs(F - F64) / scale
+        out[law] = {"max": float(rel.max()), "mean": float(rel.mean()),
+                    "bound_per_coupling": 2.0 ** -16}
+    return out
+
+
 def biclique_block(pb, stream, peaks):
     """Biclique K_{n,n}, n = 4096, 4096 replicas, linear beta 0.35 -> 3.5: sweep-loop kernels of the
     tensor-core form (+-1 in FP8 e4m3, N(0,1) in split BF16) and of the FP32 CUDA-core form, timed with
     the library's events around the sweep loop.  Tensor roofline: 2n FLOP per update (e4m3) or 4n
     (two BF16 products) against the measured BF16 peak (x2 for FP8, the nominal dense ratio)."""
     n, R = 4096, 4096
-    bf16 = float(peaks.get("bf16_tflops", 1964.9))
+    bf16 = float(peaks.get("bf16_tflops", 1888.9))
+    fp8 = peaks.get("fp8_tflops_measured")
     out = {"workload": "biclique n=4096 (8192 spins), 4096 replicas, linear beta 0.35->3.5, h=0"}
     for law, form, S in (("pm1", "tensor", 200), ("gauss", "tensor", 100), ("pm1", "cudacore", 4)):
         J = pb.pb_generate_biclique(n, pb.PB_DIST_PM1 if law == "pm1" else pb.PB_DIST_GAUSS, 11)
@@ -247,10 +322,50 @@ def biclique_block(pb, stream, peaks):
         key = f"{law}_{form}"
         ent = {"sweeps": S, "ms": ms, "updates_per_s": upd / (ms / 1e3), "tflops": tf}
         if form == "tensor":
-            peak = 2 * bf16 if law == "pm1" else bf16
-            ent.update({"peak_tflops": peak, "frac": tf / peak,
-                        "peak_source": "measured bf16 burst" + (" x 2 (nominal fp8/bf16 ratio)" if law == "pm1" else "")})
+            if law == "pm1":
+                peak = fp8 if fp8 else 2 * bf16
+                src = ("measured fp8 dense (torch._scaled_mm e4m3, 8192^3, best of 10, this run)" if fp8
+                       else "measured bf16 burst x 2 (nominal fp8/bf16 ratio; fp8 measurement failed)")
+            else:
+                peak, src = bf16, "measured bf16 burst (peak file)"
+                # the method's own work is 2n FLOP per update; the split issues 4n
+                ent["method_tflops_2n"] = upd * 2 * n / (ms / 1e3) / 1e12
+                ent["method_frac_2n"] = ent["method_tflops_2n"] / peak
+            ent.update({"peak_tflops": peak, "frac": tf / peak, "peak_source": src})
         out[key] = ent
+    out["split_bf16_field_error"] = split_field_error(pb, stream)
+    return out
+
+
+# ------------------------------------------------------------ config 1
+def config1_block(pb, stream):
+    """The paper's small-cube run shape (Sec. 2): EA L = 6 (216 spins), +-1 bonds from seed 1,
+    h = 0, linear beta 0.1 -> 3.0 over 1000 sweeps, 64 replicas, seed 42.  Latency of one
+    whole anneal (create excluded; readout of energies included) in the plain form the
+    configuration names, and in the resident form; median of 5 after one warm-up."""
+    import torch
+    L, R, S = 6, 64, 1000
+    J = pb.pb_generate_ea(L, pb.PB_DIST_PM1, 1)
+    inst = pb.pb_create_instance(pb.PB_TOPO_EA3D, J, None, L=L, stream=stream)
+    sc = pb.make_schedule(pb.PB_SCHED_LINEAR, S, 0.1, 3.0)
+    out = {"workload": "EA L=6 +-J (seed 1), h=0, linear beta 0.1->3.0, 1000 sweeps, 64 replicas, seed 42",
+           "updates": L ** 3 * R * S}
+    for name, form in (("plain", pb.PB_FORM_PLAIN), ("resident", pb.PB_FORM_RESIDENT)):
+        ts = []
+        for it in range(6):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            run = pb.pb_anneal(inst, sc, R, 42, pb.make_opts(form), stream=stream)
+            pb.pb_energy(run, R)
+            e1.record(stream)
+            e1.synchronize()
+            pb.pb_run_destroy(run)
+            if it:
+                ts.append(e0.elapsed_time(e1))
+        ms = statistics.median(ts)
+        out[name] = {"ms": ms, "updates_per_s": L ** 3 * R * S / (ms / 1e3)}
+    pb.pb_instance_destroy(inst)
     return out
 
 
@@ -693,7 +808,7 @@ def main():
     h2d = sum(J.nbytes for J in Js)
     d2h = 0
     e2e_ms = []
-    for _ in range(max(1, min(2, args.steps))):
+    for _ in range(max(1, min(3, args.steps))):
         flush.zero_()
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -726,19 +841,33 @@ def main():
     k_ms = statistics.mean(kern_ms)
     achieved = updates_per_step() / (k_ms / 1e3) / 1e9          # Gupdate/s per launch
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    # ALU ceiling: Philox4x32-10 takes 20 32x32->64 multiplies per 4 updates; with
-    # the high and low halves as two IMAD issues at 64 IMAD/clk/SM: 6.4 updates/clk/SM
-    alu_peak = 152 * 64.0 / 10.0 * sm_max * 1e6 / 1e9          # Gupdate/s
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    # measured ALU ceiling: a kernel that draws exactly the tiles' random words (one
+    # Philox4x32-10 word per update, same counters) and nothing else
+    ceil_gups = philox_ceiling(pb, stream) / 1e9
+    # derived IMAD bound, for context: 20 32x32->64 multiplies per 4 updates, the high
+    # and low halves as two IMAD issues at 64 IMAD/clk/SM -> 6.4 updates/clk/SM
+    imad_peak = n_sm * 64.0 / 10.0 * sm_max * 1e6 / 1e9           # Gupdate/s
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     traffic = profiled_traffic()
-    roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Gupdate/s",
-                "frac": achieved / alu_peak, "traffic": traffic,
+    roofline = {"bound": "alu", "achieved": achieved, "peak": ceil_gups, "unit": "Gupdate/s",
+                "frac": achieved / ceil_gups, "traffic": traffic,
                 "traffic_source": "profiles/ea_resident_batch_dram.md (ncu dram__bytes_read+write, both kernels of one step)",
-                "peak_source": "derived: 152 SMs x 64 IMAD/clk x max SM clock / 10 IMAD per update (Philox)",
+                "peak_source": "measured: Philox-only ceiling kernel (pb_philox_ceiling: the tiles' decision words, "
+                               "one per update, nothing else), best of 3, this run",
                 "kernel": "ea_resident_kernel<f32> then ea_resident_kernel<+-1> (chained; events around both)",
                 "kernel_ms": k_ms,
+                "imad_bound": {"peak": imad_peak, "frac": achieved / imad_peak, "sms": n_sm,
+                               "source": f"derived: {n_sm} SMs (device query) x 64 IMAD/clk x max SM clock / "
+                                         "10 IMAD per update"},
                 "hbm_equiv": {"bytes_per_update": 2, "achieved_gbs": achieved * 2, "peak_gbs": hbm,
-                              "frac": achieved * 2 / hbm, "peak_source": "measured"}}
+                              "frac": achieved * 2 / hbm, "peak_source": "measured (peak file)"}}
+    dense = measure_dense_peaks()
+    peaks = dict(peaks)
+    peaks["fp8_tflops_measured"] = dense.get("fp8_tflops")
+    line_peaks = {"fp8_tflops": dense.get("fp8_tflops"), "bf16_tflops_this_run": dense.get("bf16_tflops"),
+                  "bf16_tflops_peak_file": peaks.get("bf16_tflops"), "how": dense.get("fp8_how", dense.get("fp8_error")),
+                  "n": dense["n"], "reps": dense["reps"]}
 
     # ---- time to target (p = 0.99 of the best warm-up energy, 90% of replicas) ----
     ttt = []
@@ -757,7 +886,7 @@ def main():
             "clocks": clocks,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": args.steps * (len({j[1] for j in JOBS}) + 4 * len(JOBS)),
-            "roofline": roofline, "time_to_target": ttt}
+            "roofline": roofline, "time_to_target": ttt, "measured_peaks": line_peaks}
 
     # ---- plain per-instance form on the same inputs (one pass) ----
     if not args.no_plain and rank == 0:
@@ -775,6 +904,8 @@ def main():
         pv = updates_per_step() / (pms / 1e3)
         line["plain_form"] = {"value": pv, "unit": UNIT, "ms_per_step": pms, "speedup_of_batched": value / world / pv}
 
+    if rank == 0:
+        line["config1"] = config1_block(pb, stream)
     if rank == 0 and not args.no_biclique:
         line["biclique"] = biclique_block(pb, stream, peaks)
     if rank == 0 and not args.no_extensions:

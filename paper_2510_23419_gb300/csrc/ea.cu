@@ -443,6 +443,38 @@ __global__ void __launch_bounds__(kResidentThreads, 1)
 }
 
 // ---------------------------------------------------------------------------
+// Random-word ceiling of the EA update: the decision words of an L = 32 tile
+// (same counters, round keys and first-round hoisting as the fast tile: one
+// Philox4x32-10 call per site and 4 replicas, i.e. one word per update) and
+// nothing else -- no field, no threshold, no state.  Each thread takes the
+// sites of one column of both colours, two sites per iteration as the +-1
+// tile does; the words are folded into one xor per thread so none is dead.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kResidentThreads, 1)
+    ea_philox_ceiling_kernel(uint32_t key0, uint32_t key1, int sweeps, uint32_t* __restrict__ sink)
+{
+    constexpr int L = 32, h2 = L / 2;
+    const RoundKeys rk = round_keys(key0, key1);
+    const int t = threadIdx.x;
+    const int cw = t % (kResidentThreads / 2), zp = t / (kResidentThreads / 2);
+    const int q = cw % h2, y = cw / h2;
+    const uint32_t tq = blockIdx.x;
+    uint32_t acc = 0;
+    for (int s = 0; s < sweeps; ++s) {
+#pragma unroll 1
+        for (int c = 0; c < 2; ++c) {
+            const PhiloxPre pre = philox_pre((uint32_t)s, tq, (kTagDecision << 24) | (uint32_t)c, rk);
+#pragma unroll 2
+            for (int z = zp; z < L; z += 2) {
+                const U4 r = philox_c0((uint32_t)(q + h2 * (y + L * z)), pre, rk);
+                acc ^= r.x ^ r.y ^ r.z ^ r.w;
+            }
+        }
+    }
+    sink[(size_t)blockIdx.x * kResidentThreads + t] = acc;
+}
+
+// ---------------------------------------------------------------------------
 // Plain form (global memory state, one tile with WT = Rw)
 // ---------------------------------------------------------------------------
 struct SiteGeom {
@@ -835,6 +867,12 @@ cudaError_t ea_launch_resident(int jtype, const EaJob* d_jobs, const EaWork* d_w
     return jtype == PB_J_F32 ? cudaLaunchKernelEx(&cfg, ea_resident_kernel<PB_J_F32>, d_jobs, d_work, n_work, d_counter)
                              : cudaLaunchKernelEx(&cfg, ea_resident_kernel<PB_J_PM1_I8>, d_jobs, d_work, n_work,
                                                   d_counter);
+}
+
+cudaError_t ea_launch_philox_ceiling(uint64_t seed, int sweeps, int blocks, uint32_t* sink, cudaStream_t st)
+{
+    ea_philox_ceiling_kernel<<<blocks, kResidentThreads, 0, st>>>((uint32_t)seed, (uint32_t)(seed >> 32), sweeps, sink);
+    return cudaGetLastError();
 }
 
 static unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }

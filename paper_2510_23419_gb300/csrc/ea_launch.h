@@ -106,6 +106,10 @@ cudaError_t ea_resident_set_smem(int jtype, size_t smem);
 // caller orders any later consumer after both).
 cudaError_t ea_launch_resident(int jtype, const EaJob* d_jobs, const EaWork* d_work, int n_work, int* d_counter,
                                size_t smem, int grid, bool after_previous, cudaStream_t st);
+// Random-word ceiling: `blocks` CTAs of kResidentThreads threads, each thread drawing the
+// decision words of 32 sites (one L = 32 column, both colours) per sweep; sink holds
+// blocks * kResidentThreads words.  Updates counted: blocks * kResidentThreads * 32 * 4 per sweep.
+cudaError_t ea_launch_philox_ceiling(uint64_t seed, int sweeps, int blocks, uint32_t* sink, cudaStream_t st);
 cudaError_t ea_launch_plain_init(const EaJob& job, cudaStream_t st);
 cudaError_t ea_launch_plain_sweep(const EaJob& job, int s, cudaStream_t st);
 cudaError_t ea_launch_plain_energy(const EaJob& job, int s, bool init, cudaStream_t st);

@@ -834,6 +834,34 @@ pb_status pb_run_device_ms(pb_run* run, float* ms)
     return PB_OK;
 }
 
+pb_status pb_philox_ceiling(int32_t sweeps, int32_t blocks, void* stream, float* ms, double* updates)
+{
+    pb::TraceRange trace_("pb_philox_ceiling");
+    if (!ms || !updates || sweeps < 1) return fail(PB_EINVAL, "pb_philox_ceiling: null output or sweeps < 1");
+    if (blocks <= 0) blocks = sm_count();
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    uint32_t* sink = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto cleanup = [&]() {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (sink) cudaFree(sink);
+    };
+    cudaError_t e = cudaMalloc(&sink, (size_t)blocks * kResidentThreads * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = ea_launch_philox_ceiling(0x5EEDu, 2, blocks, sink, st);  // warm-up
+    if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+    if (e == cudaSuccess) e = ea_launch_philox_ceiling(0x5EEDu, sweeps, blocks, sink, st);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+    cleanup();
+    if (e != cudaSuccess) return cuda_fail(e, "pb_philox_ceiling");
+    *updates = (double)blocks * kResidentThreads * 32.0 * 4.0 * sweeps;
+    return PB_OK;
+}
+
 pb_status pb_run_kernel_ms(pb_run* run, float* ms)
 {
     if (!run || !ms) return fail(PB_EINVAL, "null argument");
