@@ -95,6 +95,31 @@ def test_f32_fields(pb, orc, form, n):
         assert np.all(np.abs(F[r] - F64) <= 1e-5 * scale)
 
 
+@pytest.mark.parametrize("law", ["gauss", "unif"])
+@pytest.mark.parametrize("n", [2048, 4096])
+def test_split_bf16_fields_full_size(pb, orc, n, law):
+    """Split hi + lo BF16 products with FP32 accumulation in tensor memory (K = n, many
+    K stages and tile rounds) against the FP64 field of the same states, at the
+    benchmark's sizes: within 1e-5 of sum_j |J_ij| for every spin, on random +-1
+    states and on a fully aligned state (all +1)."""
+    dist = pb.PB_DIST_GAUSS if law == "gauss" else pb.PB_DIST_UNIF
+    J = pb.pb_generate_biclique(n, dist, 17 + n)
+    inst = pb.pb_create_instance(pb.PB_TOPO_BICLIQUE, J, None, n=n)
+    m = np.concatenate([syn.states(3, 2 * n, 19), np.ones((1, 2 * n), np.int8)])
+    try:
+        F = pb.pb_fields_ex(inst, m, pb.PB_FORM_TENSOR)
+    finally:
+        pb.pb_instance_destroy(inst)
+    eu, ev, _ = orc.biclique_graph(n)
+    Jd = J.astype(np.float64).reshape(-1)
+    scale = orc.fields(eu, ev, np.abs(Jd), None, np.ones(2 * n, np.int8))
+    worst = 0.0
+    for r in range(m.shape[0]):
+        F64 = orc.fields(eu, ev, Jd, None, m[r])
+        worst = max(worst, float(np.max(np.abs(F[r] - F64) / scale)))
+    assert worst <= 1e-5, worst
+
+
 @pytest.mark.parametrize("form", FORMS)
 def test_f32_energies_and_ensemble(pb, orc, form):
     n, R, S = 48, 128, 80
@@ -127,6 +152,33 @@ def test_pm1_fields_exact(pb, orc, form):
     eu, ev, _ = orc.biclique_graph(n)
     for r in range(3):
         assert np.array_equal(F[r].astype(np.float64), orc.fields(eu, ev, J.astype(float).reshape(-1), h.astype(float), m[r]))
+
+
+def test_tensor_multi_tile_ensemble(pb, orc):
+    """Split-BF16 tensor form at n = 1024 with 512 replicas (four 256-row tiles per side,
+    two replica tiles, persistent rounds) against the oracle's law: final and best energy
+    per spin, means within 3 standard errors, two-sample KS p >= 0.001."""
+    stats = pytest.importorskip("scipy.stats")
+    from concurrent.futures import ThreadPoolExecutor
+    n, R, S, R_orc = 1024, 512, 30, 96
+    J = pb.pb_generate_biclique(n, pb.PB_DIST_GAUSS, 23)
+    sc = pb.make_schedule(pb.PB_SCHED_LINEAR, S, 0.35, 3.5)
+    g = _gpu(pb, n, J, None, sc, R, 29, "tensor")
+    ob = orc.schedule(orc.SCHED_LINEAR, 0.35, 3.5, S)
+    eu, ev, col = orc.biclique_graph(n)
+    Jd = J.astype(np.float64).reshape(-1)
+
+    def part(r0):
+        return orc.anneal(eu, ev, Jd, None, col, ob, 6, 29, r_first=r0)
+
+    with ThreadPoolExecutor(max_workers=16) as ex:
+        parts = list(ex.map(part, range(0, R_orc, 6)))
+    for key in ("final_E", "best_E"):
+        eg = g[key] / (2 * n)
+        eo = np.concatenate([p[key] for p in parts]) / (2 * n)
+        se = math.sqrt(eg.var(ddof=1) / eg.size + eo.var(ddof=1) / eo.size)
+        assert abs(eg.mean() - eo.mean()) <= 3 * se, (key, eg.mean(), eo.mean(), se)
+        assert float(stats.ks_2samp(eg, eo).pvalue) >= 1e-3, key
 
 
 def test_tensor_sampled_large(pb, orc):
