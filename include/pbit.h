@@ -125,9 +125,21 @@ typedef enum pb_form {
  * waits and ignore the flag. */
 #define PB_FLAG_TEST_EXPIRE_WAITS 0x40000000
 
+/* pb_anneal_opts.flags: stop at the target (the quality criterion of Sec. 1.3.1 /
+ * Fig. 1: a run is done once it reaches a given fraction of the ground-state
+ * energy).  With a finite target_energy, each replica's running best stops
+ * changing at the first sweep whose energy is <= target (its best energy, state
+ * and sweep are then those of that sweep, the recorded target sweep), and the
+ * run ends early once every replica has reached the target; otherwise after all
+ * sweeps.  The best results of a replica depend only on its own trajectory, so
+ * they are the same in every form, alone or in a batch.  The final state and
+ * energy are those of the sweep at which the replica's block of the run stopped,
+ * which depends on the form. */
+#define PB_FLAG_STOP_AT_TARGET 0x1
+
 typedef struct pb_anneal_opts {
     int32_t form;          /* pb_form */
-    int32_t flags;         /* 0, or PB_FLAG_TEST_EXPIRE_WAITS (tests of the failure path only) */
+    int32_t flags;         /* 0, PB_FLAG_STOP_AT_TARGET, or PB_FLAG_TEST_EXPIRE_WAITS (failure-path tests only) */
     double target_energy;  /* record, per replica, the first sweep whose energy is <= target;
                               NaN disables the record */
 } pb_anneal_opts;

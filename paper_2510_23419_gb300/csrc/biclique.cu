@@ -245,7 +245,9 @@ __global__ void __launch_bounds__(256) bq_sweep_end_kernel(BqJob job, int s_arg,
                                                           int32_t* sp_write)
 {
     const int s = sp_read ? *sp_read : s_arg;
-    if (sp_write && blockIdx.x == 0 && threadIdx.x == 0) *sp_write = s + 1;  // read by the next sweep's launches
+    // read by the next sweep's launches; a max, because in stop mode the block that sees the
+    // last replica reach the target raises it to S
+    if (sp_write && blockIdx.x == 0 && threadIdx.x == 0) atomicMax(sp_write, s + 1);
     if (!init && s >= job.S) return;
     __shared__ int s_copy[kEndReps];
     constexpr int kSub = 8;  // partial-row subsets, one per warp
@@ -274,22 +276,31 @@ __global__ void __launch_bounds__(256) bq_sweep_end_kernel(BqJob job, int s_arg,
     __syncthreads();
     if (threadIdx.x < kEndReps) {
         const int r = r0 + threadIdx.x;
-        bool imp;
+        bool imp, hit_now = false;
         const int prev = init ? -2 : job.best_sweep[r];
+        const bool live = init || job.has_target != 2 || job.hit_sweep[r] < 0;  // stop mode: best frozen at the target
         if (pm1) {
             int32_t E = 0;
 #pragma unroll
             for (int k = 0; k < kSub; ++k) E += s_pi[k][threadIdx.x];
-            imp = init || E < job.E_best_i[r];
+            imp = init || (live && E < job.E_best_i[r]);
             if (imp) job.E_best_i[r] = E;
-            if (!init && job.has_target && job.hit_sweep[r] < 0 && E <= job.target_i) job.hit_sweep[r] = s;
+            hit_now = !init && job.has_target && job.hit_sweep[r] < 0 && E <= job.target_i;
         } else {
             float E = 0.0f;
 #pragma unroll
             for (int k = 0; k < kSub; ++k) E += s_pf[k][threadIdx.x];
-            imp = init || E < job.E_best_f[r];
+            imp = init || (live && E < job.E_best_f[r]);
             if (imp) job.E_best_f[r] = E;
-            if (!init && job.has_target && job.hit_sweep[r] < 0 && E <= job.target_f) job.hit_sweep[r] = s;
+            hit_now = !init && job.has_target && job.hit_sweep[r] < 0 && E <= job.target_f;
+        }
+        if (hit_now) {
+            job.hit_sweep[r] = s;
+            // stop mode: the last replica to reach the target ends the run after this sweep
+            if (job.has_target == 2 && r < job.R && atomicAdd(job.stop, 1) + 1 == job.R) {
+                job.stop[1] = s;
+                if (sp_write) atomicMax(sp_write, job.S);
+            }
         }
         if (init) job.hit_sweep[r] = -1;
         if (imp) job.best_sweep[r] = init ? -1 : s;
@@ -300,13 +311,30 @@ __global__ void __launch_bounds__(256) bq_sweep_end_kernel(BqJob job, int s_arg,
     if (!init) bq_copy_flagged(job, r0, s_copy, (s - 1) & 1);
 }
 
+// The sweep whose state the live buffers end with: S - 1, or the sweep after
+// which a stop-mode run ended.
+__device__ __forceinline__ int bq_last_sweep(const BqJob& job)
+{
+    return (job.has_target == 2 && job.stop[1] >= 0) ? job.stop[1] : job.S - 1;
+}
+
+// End of a captured chunk of sweeps: keep looping (the condition of the graph's
+// while node) while the next sweep index, which every sweep end raises, is
+// below S -- a stop-mode run that has reached its target raised it to S.
+// One thread: the condition has a single writer.
+__global__ void bq_chunk_cond_kernel(cudaGraphConditionalHandle h, const int32_t* __restrict__ next, int32_t S)
+{
+    cudaGraphSetConditional(h, *next < S ? 1u : 0u);
+}
+
 __global__ void __launch_bounds__(256) bq_best_flush_kernel(BqJob job)
 {
     __shared__ int s_copy[kEndReps];
     const int r0 = blockIdx.x * kEndReps;
-    if (threadIdx.x < kEndReps) s_copy[threadIdx.x] = job.best_sweep[r0 + threadIdx.x] == job.S - 1 ? 1 : 0;
+    const int last = bq_last_sweep(job);
+    if (threadIdx.x < kEndReps) s_copy[threadIdx.x] = job.best_sweep[r0 + threadIdx.x] == last ? 1 : 0;
     __syncthreads();
-    bq_copy_flagged(job, r0, s_copy, (job.S - 1) & 1);
+    bq_copy_flagged(job, r0, s_copy, last & 1);
 }
 
 __global__ void __launch_bounds__(256) bq_readout_kernel(BqJob job, int which, int8_t* __restrict__ out)
@@ -318,12 +346,18 @@ __global__ void __launch_bounds__(256) bq_readout_kernel(BqJob job, int which, i
     const int c = (int)(j - (long long)r * 2 * n);
     const int side = c >= n ? 1 : 0;
     const int i = c - side * n;
-    void* const* src = which ? job.best : job.spins;
+    const void* src_side;
+    if (which)
+        src_side = job.best[side];
+    else if (job.has_target == 2 && job.stop[1] >= 0)  // stopped early: the live buffers of that sweep
+        src_side = job.buf[side][job.stop[1] & 1];
+    else
+        src_side = job.spins[side];
     bool minus;
     if (job.inst.jtype == PB_J_PM1_I8)
-        minus = static_cast<const uint8_t*>(src[side])[(size_t)r * job.ld + i] & 0x80u;
+        minus = static_cast<const uint8_t*>(src_side)[(size_t)r * job.ld + i] & 0x80u;
     else
-        minus = static_cast<const uint16_t*>(src[side])[(size_t)r * job.ld + i] & 0x8000u;
+        minus = static_cast<const uint16_t*>(src_side)[(size_t)r * job.ld + i] & 0x8000u;
     out[j] = minus ? (int8_t)-1 : (int8_t)1;
 }
 
@@ -501,6 +535,12 @@ cudaError_t bq_launch_sweep_end(const BqJob& job, int s, int init, const int32_t
                                 cudaStream_t st)
 {
     bq_sweep_end_kernel<<<job.Rpad / kEndReps, 256, 0, st>>>(job, s, init, sp_read, sp_write);
+    return cudaGetLastError();
+}
+
+cudaError_t bq_launch_chunk_cond(cudaGraphConditionalHandle h, const int32_t* next, int32_t S, cudaStream_t st)
+{
+    bq_chunk_cond_kernel<<<1, 1, 0, st>>>(h, next, S);
     return cudaGetLastError();
 }
 

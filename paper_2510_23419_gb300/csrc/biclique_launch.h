@@ -49,8 +49,10 @@ struct BqJob {
     float* E_best_f;
     int32_t* best_sweep;
     int32_t* hit_sweep;
-    int32_t has_target, target_i;
+    int32_t has_target, target_i;  // has_target: 0 none, 1 record the target sweep, 2 also stop there (see pbit.h)
     float target_f;
+    int32_t* stop;          // has_target == 2: [0] replicas that reached the target, [1] the sweep after which all
+                            // had (-1 while running); the sweep counters jump to S then
     double* epart;          // [ceil(n/64)][R] row-tile parts of the exact readout energy
     const int32_t* win;     // PM1 [levels][3]: threshold window (lo, width, off) of each beta level
     int32_t tabmode;        // tensor form: where the decisions read the windows (widest level decides)
@@ -88,6 +90,8 @@ cudaError_t bq_launch_cc_half(const BqJob& job, int side, int s, const int32_t* 
 // s + 1 overwrites them), so a run of improving sweeps costs one copy.
 cudaError_t bq_launch_sweep_end(const BqJob& job, int s, int init, const int32_t* sp_read, int32_t* sp_write,
                                 cudaStream_t st);
+// Inside the body of a graph's while node: continue while *next < S (one thread).
+cudaError_t bq_launch_chunk_cond(cudaGraphConditionalHandle h, const int32_t* next, int32_t S, cudaStream_t st);
 // After the last sweep (S): copy the replicas whose best is state S - 1.
 cudaError_t bq_launch_best_flush(const BqJob& job, cudaStream_t st);
 cudaError_t bq_launch_readout(const BqJob& job, int which /*0 final, 1 best*/, int8_t* out_pm, double* out_E,

@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(kThreads, 1) bq_res_kernel(BqJob job, int tab_
         half(1, s, true, win, cexp);
         reduce_energy(&E);  // its barrier ends side B
         if (t < kRB) {
-            if (E < Ebest) {
+            if ((job.has_target != 2 || hit < 0) && E < Ebest) {  // stop mode: the best is frozen at the target
                 Ebest = E;
                 bsweep = s;
                 atomicOr(&s_flag, 1u << t);
@@ -281,6 +281,9 @@ __global__ void __launch_bounds__(kThreads, 1) bq_res_kernel(BqJob job, int tab_
         }
         __syncthreads();
         copy_best();
+        // stop mode: the block ends once its replicas (padding included) have reached the target; its
+        // final state still goes to the buffers of the last sweep's parity, where the readout looks
+        if (job.has_target == 2 && __syncthreads_and(t >= kRB || hit >= 0 || rb + t >= job.R)) break;
     }
     // ---- outputs: final state (in the buffers of the last sweep's parity), best energies and sweeps
     __syncthreads();

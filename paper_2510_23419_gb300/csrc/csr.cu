@@ -127,6 +127,7 @@ template <int JT, bool TEMP, bool ELL>
 __global__ void __launch_bounds__(kCsrLanesQ* kCsrLanesV) csr_class_kernel(CsrJob job, int c, int s)
 {
     constexpr bool PM1 = JT == PB_J_PM1_I8;
+    if (job.has_target == 2 && job.stop[1] >= 0) return;  // stop mode: every replica has reached the target
     __shared__ int32_t red_i[kCsrLanesV][kCsrLanesQ][4];
     __shared__ float red_f[kCsrLanesV][kCsrLanesQ][4];
     __shared__ uint32_t s_win[kCsrWinSmem];
@@ -293,6 +294,8 @@ constexpr int kSweepEndWarps = 32;
 __global__ void __launch_bounds__(kSweepEndWarps * 32) csr_sweep_end_kernel(CsrJob job, int s, int init)
 {
     __shared__ double acc[kSweepEndWarps][32];
+    // stop mode: nothing changes after the sweep at which every replica had reached the target
+    if (!init && job.has_target == 2 && job.stop[1] >= 0) return;
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     const int r = blockIdx.x * 32 + lane;
     const bool live = r < 4 * job.Rw;
@@ -328,12 +331,15 @@ __global__ void __launch_bounds__(kSweepEndWarps * 32) csr_sweep_end_kernel(CsrJ
         imp = false;  // resumed: the given best stays
         job.hit_sweep[r] = -1;
     } else {
-        imp = E < job.E_best[r];
+        imp = (job.has_target != 2 || job.hit_sweep[r] < 0) && E < job.E_best[r];  // stop mode: frozen at the target
         if (imp) {
             job.E_best[r] = E;
             job.best_sweep[r] = s;
         }
-        if (job.has_target && job.hit_sweep[r] < 0 && E <= job.target) job.hit_sweep[r] = s;
+        if (job.has_target && job.hit_sweep[r] < 0 && E <= job.target) {
+            job.hit_sweep[r] = s;
+            if (job.has_target == 2 && r < job.R && atomicAdd(job.stop, 1) + 1 == job.R) job.stop[1] = s;
+        }
     }
     job.improved[r] = imp ? 1 : 0;
 }
@@ -359,30 +365,34 @@ __global__ void __launch_bounds__(256) csr_snapshot_kernel(CsrJob job)
 // Replica exchange after sweep s (tempering): one thread per chain, pairs of
 // the sweep's parity in increasing order; accepted with probability
 // min(1, exp((beta_{t+1} - beta_t)(E_b - E_a))) by the word of counter
-// (t, s, r >> 2, 3 << 24), index r & 3.
+// (t, s, r >> 2, 3 << 24), index r & 3.  +-1: the host's FP64 threshold table
+// (bit-exact with the oracle); real couplings: an FP32 rule like the p-bit
+// decision's -- the exponent in FP32 (energies rounded to FP32, the pair's
+// beta step times log2 e from the host), one exp2, and the uniform
+// u = ((w >> 9) + 1/2) 2^-23 -- so no FP64 arithmetic runs on the device here.
 __global__ void __launch_bounds__(128) csr_exchange_kernel(CsrJob job, int s)
 {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= job.C) return;
     for (int t = s & 1; t + 1 < job.M; t += 2) {
         const int a = job.slot_of[t * job.C + r], b = job.slot_of[(t + 1) * job.C + r];
-        const double dE = job.E_cur[b] - job.E_cur[a];
         const U4 rw = philox10((uint32_t)t, (uint32_t)s, (uint32_t)(r >> 2), 3u << 24, job.key0, job.key1);
         const uint32_t ws[4] = {rw.x, rw.y, rw.z, rw.w};
         const uint32_t w = ws[r & 3];
         bool accept;
         if (job.g.jtype == PB_J_PM1_I8) {
-            // integer energies: the host's FP64 table of floor(exp(dbeta (-d)) 2^32), d = 1, 2, ...
-            if (dE >= 0.0) {
+            // integer energies (held exactly): the host's FP64 table of floor(exp(dbeta (-d)) 2^32), d = 1, 2, ...
+            const long long d = __double2ll_rn(job.E_cur[a]) - __double2ll_rn(job.E_cur[b]);
+            if (d <= 0) {
                 accept = true;
             } else {
-                const long long d = (long long)(-dE);
                 const int len = job.xwin[2 * t], off = job.xwin[2 * t + 1];
                 accept = d <= len && w < job.xtab[off + (int)(d - 1)];
             }
         } else {
-            const double x = (job.ladder[t + 1] - job.ladder[t]) * dE;
-            accept = x >= 0.0 || (double)w < floor(exp(x) * 4294967296.0);
+            const float y = job.xdb[t] * ((float)job.E_cur[b] - (float)job.E_cur[a]);  // x log2 e
+            const float u = __uint_as_float(0x3F800000u | (w >> 9)) - 0.99999994f;
+            accept = y >= 0.0f || u < ex2_ftz(y);
         }
         if (accept) {
             job.temp[a] = (uint8_t)(t + 1);

@@ -258,9 +258,17 @@ static pb_status csr_prepare(pb_run* run, pb_instance* I, const std::vector<doub
         j.betaf = run->betaf.as<float>();
     }
     PB_CUDA_TRY(cudaStreamSynchronize(st));
+    j.stop = nullptr;
     if (opts && !std::isnan(opts->target_energy)) {
-        j.has_target = 1;
+        j.has_target = (opts->flags & PB_FLAG_STOP_AT_TARGET) ? 2 : 1;
         j.target = opts->target_energy;
+    }
+    if (j.has_target == 2) {
+        const int32_t init_stop[2] = {0, -1};
+        PB_ALLOC(run->n_hit, sizeof(init_stop));
+        PB_CUDA_TRY(cudaMemcpyAsync(run->n_hit.p, init_stop, sizeof(init_stop), cudaMemcpyHostToDevice, st));
+        PB_CUDA_TRY(cudaStreamSynchronize(st));
+        j.stop = run->n_hit.as<int32_t>();
     }
     const size_t words = (size_t)I->N * j.Rw;
     j.nchunk = (int)((I->N + kCsrChunk - 1) / kCsrChunk);
@@ -346,13 +354,16 @@ static pb_status csr_setup_pt(pb_run* run, pb_instance* I, const double* ladder,
         temp[(size_t)g] = (uint8_t)(g / C);
         slot_of[(size_t)g] = g;
     }
-    DevBuf* P = run->pt;  // 0 temp, 1 slot_of, 2 ladder, 3 xtab, 4 xwin, 5 n_accept
+    DevBuf* P = run->pt;  // 0 temp, 1 slot_of, 2 xdb, 3 xtab, 4 xwin, 5 n_accept
     PB_ALLOC(P[0], temp.size());
     PB_CUDA_TRY(cudaMemcpyAsync(P[0].p, temp.data(), temp.size(), cudaMemcpyHostToDevice, st));
     PB_ALLOC(P[1], slot_of.size() * 4);
     PB_CUDA_TRY(cudaMemcpyAsync(P[1].p, slot_of.data(), slot_of.size() * 4, cudaMemcpyHostToDevice, st));
-    PB_ALLOC(P[2], (size_t)M * 8);
-    PB_CUDA_TRY(cudaMemcpyAsync(P[2].p, ladder, (size_t)M * 8, cudaMemcpyHostToDevice, st));
+    // real couplings: the exponent's beta step per pair, times log2 e, in FP32 for the device rule
+    std::vector<float> xdb((size_t)std::max(1, M - 1), 0.0f);
+    for (int t = 0; t + 1 < M; ++t) xdb[(size_t)t] = (float)((ladder[t + 1] - ladder[t]) * 1.4426950408889634);
+    PB_ALLOC(P[2], xdb.size() * 4);
+    PB_CUDA_TRY(cudaMemcpyAsync(P[2].p, xdb.data(), xdb.size() * 4, cudaMemcpyHostToDevice, st));
     std::vector<uint32_t> xtab;
     std::vector<int32_t> xwin((size_t)2 * std::max(1, M - 1), 0);
     if (I->jtype == PB_J_PM1_I8) {
@@ -378,7 +389,7 @@ static pb_status csr_setup_pt(pb_run* run, pb_instance* I, const double* ladder,
     PB_CUDA_TRY(cudaStreamSynchronize(st));
     j.temp = P[0].as<uint8_t>();
     j.slot_of = P[1].as<int32_t>();
-    j.ladder = P[2].as<double>();
+    j.xdb = P[2].as<float>();
     j.xtab = P[3].as<uint32_t>();
     j.xwin = P[4].as<int32_t>();
     j.n_accept = P[5].as<unsigned long long>();

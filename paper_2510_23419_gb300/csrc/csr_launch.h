@@ -58,14 +58,16 @@ struct CsrJob {
     int32_t* best_sweep;     // [4 Rw]
     int32_t* hit_sweep;      // [4 Rw]
     uint8_t* improved;       // [4 Rw] + 1 "any" flag at [4 Rw]
-    int32_t has_target;
+    int32_t has_target;        // 0 none, 1 record the target sweep, 2 also stop there (see pbit.h)
+    int32_t* stop;             // has_target == 2: [0] replicas that reached the target, [1] the sweep after
+                               // which all had (-1 while running); later launches return at once
     double target;
     double* E_cur;             // [4 Rw] energy after the last sweep
     // parallel tempering (null temp: annealing with the schedule)
     uint8_t* temp;             // [4 Rw] temperature index of every slot (= replica)
     int32_t* slot_of;          // [M][C] slot holding temperature t of chain r
     int32_t M, C;              // temperatures, chains; slot g = k C + r starts at temperature k
-    const double* ladder;      // [M] inverse temperatures (real couplings)
+    const float* xdb;          // [M-1] (beta_{t+1} - beta_t) log2 e, rounded to FP32 (real couplings)
     const uint32_t* xtab;      // +-1: exchange thresholds floor(exp(dbeta_t * (-d)) 2^32), d = 1, 2, ...
     const int32_t* xwin;       // +-1: [M-1][2] (length, offset) of pair t's thresholds in xtab
     unsigned long long* n_accept;  // [M-1] accepted exchanges per pair

@@ -271,8 +271,7 @@ __device__ void ea_tile(const EaJob& job, int tile, unsigned char* smem)
                     for (int b = 0; b < 4; ++b) F[b] = ea_field_f32(jv, hv, nb, b);
                     if (decide) {
                         const U4 r = philox10((uint32_t)k, (uint32_t)s, g.tq, c3, key0, key1);
-                        snew = f32_word(decide_f32(r.x, F[0], cexp), decide_f32(r.y, F[1], cexp),
-                                        decide_f32(r.z, F[2], cexp), decide_f32(r.w, F[3], cexp));
+                        snew = decide_f32_word(r.x, r.y, r.z, r.w, F[0], F[1], F[2], F[3], cexp);
                         own[kw] = snew;
                     } else {
                         snew = own[kw];
@@ -360,13 +359,14 @@ __device__ void ea_tile(const EaJob& job, int tile, unsigned char* smem)
             int32_t Ei = 0;
             float Ef = 0.0f;
             energy_of(t, Ei, Ef);
+            const bool live = job.has_target != 2 || hit < 0;  // stop mode: the best is frozen at the target
             bool imp;
             if (JT == PB_J_PM1_I8) {
-                imp = Ei < bestEi;
+                imp = live && Ei < bestEi;
                 if (imp) bestEi = Ei;
                 if (job.has_target && hit < 0 && Ei <= job.target_i) hit = s;
             } else {
-                imp = Ef < bestEf;
+                imp = live && Ef < bestEf;
                 if (imp) bestEf = Ef;
                 if (job.has_target && hit < 0 && Ef <= job.target_f) hit = s;
             }
@@ -376,6 +376,8 @@ __device__ void ea_tile(const EaJob& job, int tile, unsigned char* smem)
         __syncthreads();
         const uint32_t f = reinterpret_cast<const uint32_t*>(sflag)[g.w];
         tile_store_words<LT, WTT>(g, sp, job.best_words, tile, f * 0xFFu);
+        // stop mode: the tile ends once all its replicas (padding included) have reached the target
+        if (job.has_target == 2 && __syncthreads_and(t >= nrep || hit >= 0 || tile * nrep + t >= job.R)) break;
     }
 
     // ---- results ----
@@ -508,9 +510,17 @@ __device__ __forceinline__ void neighbour_ranks(int L, const SiteGeom& s, int (&
     kn[5] = s.q + h2 * (s.y + L * zm);
 }
 
+// Plain form in stop mode: every replica has reached the target, the launches
+// of the remaining sweeps return at once.
+__device__ __forceinline__ bool ea_plain_stopped(const EaJob& job)
+{
+    return job.has_target == 2 && *reinterpret_cast<const volatile int32_t*>(job.n_hit) >= job.R;
+}
+
 template <int JT, bool HH>
 __global__ void __launch_bounds__(256) ea_plain_half_kernel(EaJob job, int c, int s)
 {
+    if (ea_plain_stopped(job)) return;
     __shared__ uint32_t stab[256];
     const int L = job.inst.L;
     const int half = job.inst.half;
@@ -559,8 +569,8 @@ __global__ void __launch_bounds__(256) ea_plain_half_kernel(EaJob job, int c, in
         const float jv[6] = {ja.x, ja.y, ja.z, ja.w, jb.x, jb.y};
         const float hv = __ldg(job.inst.hf + site);
         const float cexp = f32_cexp(job.betaf[s / job.step]);
-        snew = f32_word(decide_f32(r.x, ea_field_f32(jv, hv, nb, 0), cexp), decide_f32(r.y, ea_field_f32(jv, hv, nb, 1), cexp),
-                        decide_f32(r.z, ea_field_f32(jv, hv, nb, 2), cexp), decide_f32(r.w, ea_field_f32(jv, hv, nb, 3), cexp));
+        snew = decide_f32_word(r.x, r.y, r.z, r.w, ea_field_f32(jv, hv, nb, 0), ea_field_f32(jv, hv, nb, 1),
+                               ea_field_f32(jv, hv, nb, 2), ea_field_f32(jv, hv, nb, 3), cexp);
     }
     job.final_words[(size_t)c * half * WT + j] = snew;
 }
@@ -586,6 +596,7 @@ __global__ void __launch_bounds__(256) ea_plain_init_kernel(EaJob job)
 template <int JT, bool HH>
 __global__ void __launch_bounds__(256) ea_plain_energy_kernel(EaJob job, int s, int init)
 {
+    if (!init && ea_plain_stopped(job)) return;
     __shared__ int32_t red_i[8][256 / 32];
     __shared__ float red_f[4][256 / 32];
     __shared__ uint32_t s_mask;
@@ -671,15 +682,21 @@ __global__ void __launch_bounds__(256) ea_plain_energy_kernel(EaJob job, int s, 
                 H += red_i[4 + t][q];
             }
             const int32_t E = -(3 * N - 2 * U) - H;
-            imp = init || E < job.E_best_i[r];
+            imp = init || ((job.has_target != 2 || job.hit_sweep[r] < 0) && E < job.E_best_i[r]);
             if (imp) job.E_best_i[r] = E;
-            if (!init && job.has_target && job.hit_sweep[r] < 0 && E <= job.target_i) job.hit_sweep[r] = s;
+            if (!init && job.has_target && job.hit_sweep[r] < 0 && E <= job.target_i) {
+                job.hit_sweep[r] = s;
+                if (job.has_target == 2 && r < job.R) atomicAdd(job.n_hit, 1);
+            }
         } else {
             float E = 0.0f;
             for (int q = 0; q < 8; ++q) E += red_f[t][q];
-            imp = init || E < job.E_best_f[r];
+            imp = init || ((job.has_target != 2 || job.hit_sweep[r] < 0) && E < job.E_best_f[r]);
             if (imp) job.E_best_f[r] = E;
-            if (!init && job.has_target && job.hit_sweep[r] < 0 && E <= job.target_f) job.hit_sweep[r] = s;
+            if (!init && job.has_target && job.hit_sweep[r] < 0 && E <= job.target_f) {
+                job.hit_sweep[r] = s;
+                if (job.has_target == 2 && r < job.R) atomicAdd(job.n_hit, 1);
+            }
         }
         if (init) job.hit_sweep[r] = -1;
         if (imp) job.best_sweep[r] = init ? -1 : s;

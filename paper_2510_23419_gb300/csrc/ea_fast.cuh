@@ -244,8 +244,7 @@ struct EaFastTile {
             for (int b = 0; b < 4; ++b) F[b] = ea_field_f32(jv, hv, nb, b);
             if constexpr (DECIDE) {
                 const U4 r = philox_c0((uint32_t)k, pre, rk);
-                snew = f32_word(decide_f32(r.x, F[0], cexp), decide_f32(r.y, F[1], cexp), decide_f32(r.z, F[2], cexp),
-                                decide_f32(r.w, F[3], cexp));
+                snew = decide_f32_word(r.x, r.y, r.z, r.w, F[0], F[1], F[2], F[3], cexp);
                 own[base0 + z * SZ] = snew;
             } else {
                 snew = own[base0 + z * SZ];
@@ -378,13 +377,14 @@ struct EaFastTile {
                 int32_t Ei = 0;
                 float Ef = 0.0f;
                 energy_of(t, Ei, Ef);
+                const bool live = job.has_target != 2 || hit < 0;  // stop mode: the best is frozen at the target
                 bool imp;
                 if constexpr (PM1) {
-                    imp = Ei < bestEi;
+                    imp = live && Ei < bestEi;
                     if (imp) bestEi = Ei;
                     if (job.has_target && hit < 0 && Ei <= job.target_i) hit = s;
                 } else {
-                    imp = Ef < bestEf;
+                    imp = live && Ef < bestEf;
                     if (imp) bestEf = Ef;
                     if (job.has_target && hit < 0 && Ef <= job.target_f) hit = s;
                 }
@@ -395,6 +395,8 @@ struct EaFastTile {
             __syncthreads();
             const uint32_t f = reinterpret_cast<const uint32_t*>(sflag)[w];
             store_words(job.best_words, f * 0xFFu);
+            // stop mode: the tile ends once all its replicas (padding included) have reached the target
+            if (job.has_target == 2 && __syncthreads_and(t >= NREP || hit >= 0 || tile * NREP + t >= job.R)) break;
         }
 
         store_words(job.final_words, 0xFFFFFFFFu);

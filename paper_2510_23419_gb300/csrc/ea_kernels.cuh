@@ -53,13 +53,35 @@ __device__ __forceinline__ float ex2_ftz(float x)
 // P = 1/2 + tanh(beta F)/2 = 1 / (1 + e^{-2 beta F}).  The word r gives
 // u = ((r >> 9) + 1/2) 2^-23, the comparison u < P is evaluated as
 // u (1 + e^{-2 beta F}) < 1, so it needs one exp2 and no reciprocal or
-// float->int conversion.  Returns the new spin bit (1 <=> m = -1).
-// cexp = -2 beta log2(e).
+// float->int conversion.  It is computed on 2u (exact), whose product
+// 2u (1 + e) is >= 2 exactly when u (1 + e) >= 1: the outcome is then bit 30
+// of the (positive) result, with no compare.  cexp = -2 beta log2(e).
+__device__ __forceinline__ float uniform2_f32(uint32_t r)
+{
+    return __uint_as_float(0x40000000u | (r >> 9)) - __uint_as_float(0x3FFFFFFFu);  // 2u, exactly
+}
+// Bits of 2u (1 + e^{-2 beta F}); bit 30 set <=> m = -1.
+__device__ __forceinline__ uint32_t decide_f32_bits(uint32_t r, float F, float cexp)
+{
+    const float u2 = uniform2_f32(r);
+    const float e = ex2_ftz(cexp * F);
+    return __float_as_uint(fmaf(u2, e, u2));
+}
+// The new spin bit (1 <=> m = -1).
 __device__ __forceinline__ uint32_t decide_f32(uint32_t r, float F, float cexp)
 {
-    const float u = __uint_as_float(0x3F800000u | (r >> 9)) - 0.99999994f;
-    const float e = ex2_ftz(cexp * F);
-    return fmaf(u, e, u) >= 1.0f ? 1u : 0u;
+    return decide_f32_bits(r, F, cexp) >> 30;
+}
+// Four decisions as one F32 spin word (byte b = 0x3F for m = +1, 0xBF for
+// m = -1, see below): the top bytes of the four results gathered, their bit 6
+// (bit 30 of the result) moved to bit 7.
+__device__ __forceinline__ uint32_t decide_f32_word(uint32_t r0, uint32_t r1, uint32_t r2, uint32_t r3, float F0,
+                                                    float F1, float F2, float F3, float cexp)
+{
+    const uint32_t v0 = decide_f32_bits(r0, F0, cexp), v1 = decide_f32_bits(r1, F1, cexp);
+    const uint32_t v2 = decide_f32_bits(r2, F2, cexp), v3 = decide_f32_bits(r3, F3, cexp);
+    const uint32_t g = (__byte_perm(v0, v1, 0x7373u) & 0x0000FFFFu) | (__byte_perm(v2, v3, 0x7373u) & 0xFFFF0000u);
+    return 0x3F3F3F3Fu | ((g << 1) & 0x80808080u);
 }
 
 __device__ __forceinline__ float f32_cexp(float beta) { return -2.0f * beta * 1.4426950408889634f; }

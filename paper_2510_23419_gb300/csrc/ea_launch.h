@@ -21,7 +21,8 @@ struct EaJob {
     int32_t R;                // replicas requested
     int32_t WT;               // words (4 replicas each) per site in one tile
     int32_t n_tiles;
-    int32_t has_target;
+    int32_t has_target;       // 0: none; 1: record the first sweep at the target; 2: also freeze the
+                              // running best there and stop once every replica has reached it
     int32_t target_i;         // PM1 target energy (integer)
     float target_f;           // F32 target energy
     uint32_t* best_words;     // tile layout
@@ -30,6 +31,7 @@ struct EaJob {
     float* E_best_f;          // F32 running-best energy
     int32_t* best_sweep;      // [n_tiles*4*WT]
     int32_t* hit_sweep;       // [n_tiles*4*WT]
+    int32_t* n_hit;           // plain form, has_target == 2: replicas that reached the target (device counter)
     int32_t s0;               // first sweep (resident form: > 0 only for a resumed run)
     int32_t resume;           // resident form: the initial state is final_words, the running best
                               // (best_words, E_best_*, best_sweep) is given

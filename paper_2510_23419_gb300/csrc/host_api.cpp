@@ -335,7 +335,7 @@ pb_status ea_prepare_run(pb_run* run, pb_instance* I, const pb_schedule* sc, int
     }
     j.has_target = 0;
     if (opts && !std::isnan(opts->target_energy)) {
-        j.has_target = 1;
+        j.has_target = (opts->flags & PB_FLAG_STOP_AT_TARGET) ? 2 : 1;
         const double tg = opts->target_energy;
         j.target_i = (int32_t)std::max(-2.0e9, std::min(2.0e9, std::floor(tg)));
         j.target_f = (float)tg;
@@ -348,6 +348,12 @@ pb_status ea_prepare_run(pb_run* run, pb_instance* I, const pb_schedule* sc, int
     j.final_words = run->final_words.as<uint32_t>();
     j.best_sweep = run->best_sweep.as<int32_t>();
     j.hit_sweep = run->hit_sweep.as<int32_t>();
+    j.n_hit = nullptr;
+    if (j.has_target == 2 && form == PB_FORM_PLAIN) {
+        PB_ALLOC(run->n_hit, 16);
+        PB_CUDA_TRY(cudaMemsetAsync(run->n_hit.p, 0, 16, st));
+        j.n_hit = run->n_hit.as<int32_t>();
+    }
     PB_ALLOC(run->best_pm, (size_t)R * I->N);
     PB_ALLOC(run->final_pm, (size_t)R * I->N);
     PB_ALLOC(run->E_out, (size_t)2 * R * 8);

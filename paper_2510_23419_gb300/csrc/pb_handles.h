@@ -138,6 +138,7 @@ struct pb_run {
     pb::BqTcMaps maps{};
     int* dev_err = nullptr;  // device error word of bounded waits (null if the form has none)
     pb::DevBuf table, betaf, best_words, final_words, E_best_i, E_best_f, best_sweep, hit_sweep;
+    pb::DevBuf n_hit;      // stop-at-target counters (replicas that reached the target; biclique: + sweep word)
     pb::DevBuf best_pm, final_pm, E_out;  // readout: [R][N] x2, [2R] doubles
     pb::DevBuf extra[8];
     pb::DevBuf pt[6];      // parallel tempering buffers of a general-graph run

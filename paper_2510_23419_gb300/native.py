@@ -23,6 +23,7 @@ PB_DIST_PM1, PB_DIST_GAUSS, PB_DIST_UNIF = 0, 1, 2
 PB_SCHED_LINEAR, PB_SCHED_GEOMETRIC, PB_SCHED_EXPLICIT = 0, 1, 2
 PB_FORM_AUTO, PB_FORM_PLAIN, PB_FORM_RESIDENT, PB_FORM_CUDACORE, PB_FORM_TENSOR = range(5)
 PB_FLAG_TEST_EXPIRE_WAITS = 0x40000000  # failure-path test hook (see include/pbit.h)
+PB_FLAG_STOP_AT_TARGET = 0x1  # freeze each replica's best at the target, end the run once all reached it
 PB_NOALLOC_BAD_COUPLINGS = -2  # best_sweep of pb_anneal_ea_noalloc when J_dev holds a value other than +-1
 
 _ERRNAMES = {0: "PB_OK", 1: "PB_EINVAL", 2: "PB_ECOLOUR", 3: "PB_ENOMEM", 4: "PB_EDEVICE", 5: "PB_ETIMEOUT",
