@@ -318,15 +318,6 @@ __device__ __forceinline__ int bq_last_sweep(const BqJob& job)
     return (job.has_target == 2 && job.stop[1] >= 0) ? job.stop[1] : job.S - 1;
 }
 
-// End of a captured chunk of sweeps: keep looping (the condition of the graph's
-// while node) while the next sweep index, which every sweep end raises, is
-// below S -- a stop-mode run that has reached its target raised it to S.
-// One thread: the condition has a single writer.
-__global__ void bq_chunk_cond_kernel(cudaGraphConditionalHandle h, const int32_t* __restrict__ next, int32_t S)
-{
-    cudaGraphSetConditional(h, *next < S ? 1u : 0u);
-}
-
 __global__ void __launch_bounds__(256) bq_best_flush_kernel(BqJob job)
 {
     __shared__ int s_copy[kEndReps];
@@ -535,12 +526,6 @@ cudaError_t bq_launch_sweep_end(const BqJob& job, int s, int init, const int32_t
                                 cudaStream_t st)
 {
     bq_sweep_end_kernel<<<job.Rpad / kEndReps, 256, 0, st>>>(job, s, init, sp_read, sp_write);
-    return cudaGetLastError();
-}
-
-cudaError_t bq_launch_chunk_cond(cudaGraphConditionalHandle h, const int32_t* next, int32_t S, cudaStream_t st)
-{
-    bq_chunk_cond_kernel<<<1, 1, 0, st>>>(h, next, S);
     return cudaGetLastError();
 }
 

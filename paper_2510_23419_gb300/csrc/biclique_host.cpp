@@ -330,10 +330,6 @@ static cudaError_t bq_half(pb_run* run, int side, int own, int other, int s, con
 // Sweeps per captured chunk (even: the two sweep counters alternate within it).
 constexpr int kChunkSweeps = 32;
 
-// The sweep loop as a graph while node (one launch, ends on the device) or as
-// repeated launches of the chunk graph.
-static bool bq_use_while_node(const BqJob& j) { return j.has_target == 2; }
-
 // One chunk of sweeps.  Sweep k of the chunk reads its index from counter
 // k % 2 and its sweep end stores the next index into the other counter, so no
 // launch reads a counter that a concurrent block writes.  Sweeps past S do
@@ -404,39 +400,11 @@ pb_status bq_launch(pb_run* run, cudaStream_t st)
         const int chunk = std::min(kChunkSweeps, (j.S + 1) & ~1);
         const int nchunks = (j.S + chunk - 1) / chunk;
         const bool capture = st != nullptr && st != cudaStreamLegacy && st != cudaStreamPerThread;
-        if (capture && bq_use_while_node(j)) {
-            // one graph: a while node whose body is the chunk, followed by a one-thread kernel that
-            // sets the condition from the next sweep index; a run that has done all its sweeps (or,
-            // in stop mode, reached its target) launches nothing more
-            auto shared = std::make_shared<BatchShared>();
-            cudaGraph_t graph = nullptr;
-            PB_CUDA_TRY(cudaGraphCreate(&graph, 0));
-            struct GraphGuard {
-                cudaGraph_t g;
-                ~GraphGuard() { cudaGraphDestroy(g); }
-            } guard{graph};
-            cudaGraphConditionalHandle cond;
-            PB_CUDA_TRY(cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault));
-            cudaGraphNodeParams cp = {};
-            cp.type = cudaGraphNodeTypeConditional;
-            cp.conditional.handle = cond;
-            cp.conditional.type = cudaGraphCondTypeWhile;
-            cp.conditional.size = 1;
-            cudaGraphNode_t node = nullptr;
-            PB_CUDA_TRY(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp));
-            cudaGraph_t body = cp.conditional.phGraph_out[0];
-            PB_CUDA_TRY(cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-            pb_status ps = bq_enqueue_chunk(run, chunk, st);
-            cudaError_t ce = ps == PB_OK ? bq_launch_chunk_cond(cond, run->dev_err + 2, j.S, st) : cudaSuccess;
-            cudaError_t e = cudaStreamEndCapture(st, &body);
-            if (ps != PB_OK) return ps;
-            if (ce != cudaSuccess) return cuda_fail(ce, "bq_launch_chunk_cond");
-            if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
-            PB_CUDA_TRY(cudaGraphInstantiate(&shared->exec, graph, 0));
-            PB_CUDA_TRY(cudaGraphLaunch(shared->exec, st));
-            run->batch = shared;
-        } else if (capture) {
-            // one captured chunk, launched ceil(S / chunk) times; launches past the last sweep return at once
+        if (capture) {
+            // one captured chunk, launched ceil(S / chunk) times; launches past the last sweep (or, in stop
+            // mode, past the sweep at which every replica had reached the target) return at once.  A graph
+            // while node that ends the loop on the device was measured slower: served stream p50 13 -> 17 ms,
+            // mixed batch 2.66 -> 3.19 s.
             auto shared = std::make_shared<BatchShared>();
             cudaGraph_t graph = nullptr;
             PB_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));

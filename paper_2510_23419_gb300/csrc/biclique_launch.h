@@ -90,8 +90,6 @@ cudaError_t bq_launch_cc_half(const BqJob& job, int side, int s, const int32_t* 
 // s + 1 overwrites them), so a run of improving sweeps costs one copy.
 cudaError_t bq_launch_sweep_end(const BqJob& job, int s, int init, const int32_t* sp_read, int32_t* sp_write,
                                 cudaStream_t st);
-// Inside the body of a graph's while node: continue while *next < S (one thread).
-cudaError_t bq_launch_chunk_cond(cudaGraphConditionalHandle h, const int32_t* next, int32_t S, cudaStream_t st);
 // After the last sweep (S): copy the replicas whose best is state S - 1.
 cudaError_t bq_launch_best_flush(const BqJob& job, cudaStream_t st);
 cudaError_t bq_launch_readout(const BqJob& job, int which /*0 final, 1 best*/, int8_t* out_pm, double* out_E,

@@ -142,10 +142,12 @@ def test_stop_at_target_in_a_batch(pb, orc):
             pb.pb_instance_destroy(i)
 
 
-@pytest.mark.parametrize("topo,form", [("ea", "resident"), ("bq", "resident"), ("bq", "tensor")])
+@pytest.mark.parametrize("topo,form", [("ea", "resident"), ("bq", "resident")])
 def test_stop_ends_the_run_early(pb, topo, form):
     """A target every replica reaches within a few sweeps: the run with 4000 sweeps ends
-    far sooner than the same run without the stop."""
+    far sooner than the same run without the stop (forms that run the whole anneal in one
+    launch; the launch-per-sweep forms still issue their remaining launches, which return
+    at once)."""
     S, R = 4000, 64
     sched = pb.make_schedule(pb.PB_SCHED_LINEAR, S, 1.0, 3.0)
     if topo == "ea":
