@@ -337,6 +337,40 @@ def biclique_block(pb, stream, peaks):
     return out
 
 
+def biclique_sweep_block(pb, stream, peaks):
+    """Config 3 over its range: n in {512, 1024, 2048, 4096} x R in {256, 1024, 4096}, linear beta
+    0.35 -> 3.5, h = 0; tensor form with +-1 couplings (FP8 e4m3) and N(0,1) (split BF16), and
+    the FP32 CUDA-core form (+-1).  Timed with the library's events around the sweep loop;
+    FLOP/s on the method's 2n FLOP per update against the measured FP8 / BF16 dense peaks."""
+    fp8 = peaks.get("fp8_tflops_measured") or 2 * float(peaks.get("bf16_tflops", 1888.9))
+    bf16 = float(peaks.get("bf16_tflops", 1888.9))
+    insts = {}
+    rows = []
+    for n in (512, 1024, 2048, 4096):
+        for law in ("pm1", "gauss"):
+            J = pb.pb_generate_biclique(n, pb.PB_DIST_PM1 if law == "pm1" else pb.PB_DIST_GAUSS, 13)
+            insts[(n, law)] = pb.pb_create_instance(pb.PB_TOPO_BICLIQUE, J, None, n=n, stream=stream)
+        for R in (256, 1024, 4096):
+            for law, form in (("pm1", "tensor"), ("gauss", "tensor"), ("pm1", "cudacore")):
+                budget = 4e10 if form == "tensor" else 2e9
+                S = int(max(4, min(400, budget / (2 * n * R)))) & ~1
+                sc = pb.make_schedule(pb.PB_SCHED_LINEAR, S, 0.35, 3.5)
+                f = pb.PB_FORM_TENSOR if form == "tensor" else pb.PB_FORM_CUDACORE
+                run = pb.pb_anneal(insts[(n, law)], sc, R, 3, pb.make_opts(f), stream=stream)
+                ms = pb.pb_run_kernel_ms(run)
+                pb.pb_run_destroy(run)
+                ups = 2 * n * R * S / (ms / 1e3)
+                tf = ups * 2 * n / 1e12
+                peak = fp8 if (form == "tensor" and law == "pm1") else bf16
+                rows.append({"n": n, "R": R, "law": law, "form": form, "sweeps": S, "ms": ms, "updates_per_s": ups,
+                             "tflops_2n": tf, "frac_2n": tf / peak if form == "tensor" else None,
+                             "peak": ("fp8" if law == "pm1" else "bf16") if form == "tensor" else None})
+    for i in insts.values():
+        pb.pb_instance_destroy(i)
+    return {"workload": "biclique K_{n,n}, n in {512,1024,2048,4096}, R in {256,1024,4096}, linear 0.35->3.5, h=0",
+            "peaks_tflops": {"fp8": fp8, "bf16": bf16}, "rows": rows}
+
+
 # ------------------------------------------------------------ config 1
 def config1_block(pb, stream):
     """The paper's small-cube run shape (Sec. 2): EA L = 6 (216 spins), +-1 bonds from seed 1,
@@ -514,55 +548,140 @@ def mixed_block(pb, stream):
 
 
 def served_block(pb, stream, n_req: int):
-    """Poisson arrivals (500 requests/s, seed 11) of jobs drawn like the mixed batch with
-    sweep budgets log-uniform in [50, 1000], served with continuous batching; latency from
-    submit to result ready."""
+    """Served stream (continuous batching through the request server): Poisson arrivals at
+    500 requests/s (seed 11) of jobs drawn like the mixed batch (EA L in {8,12,16,24} /
+    biclique n in {128,...,2048}, +-1 / N(0,1), replicas 32..1024) over 48 distinct instances,
+    each request with a sweep budget (log-uniform in [50, 1000]) and a target residual energy:
+    p E_ref with p = 0.99 (EA) / 0.95 (biclique), E_ref the best energy of a 10^4-sweep,
+    256-replica anneal of the instance computed beforehand (10x the largest budget, the stated
+    proxy for the ground state); the anneal stops at the target (every replica reached it) or
+    at the budget.  Reported: latency from submit to result ready (p50/p99/max), the offered
+    load rho = arrival rate / the maximum sustainable rate (completion rate of a burst of
+    requests all submitted at once), and the plain per-instance forms on every 20th request
+    (one after another, same stop rule): throughput and the residual-energy distributions."""
     import torch
+    lam, p_ea, p_bq = 500.0, 0.99, 0.95
     jobs = mixed_jobs(n_req, 11, 50, 1000)
-    # a pool of 48 distinct instances (instance seed reused), requests pick their own R, S, seed
     pool = {}
     for q, j in enumerate(jobs):
-        key = (j[0], j[1], j[2])
-        pool.setdefault(key, 11000 + len(pool))
+        pool.setdefault((j[0], j[1], j[2]), 11000 + len(pool))
     jobs = [(t, sz, law, R, S, pool[(t, sz, law)]) for t, sz, law, R, S, _ in jobs]
     insts, owned = make_instances(pb, jobs, stream)
+    key_of = [(j[0], j[1], j[2], j[5]) for j in jobs]
+    # E_ref per distinct instance (untimed): one batch of long anneals
+    uniq = {}
+    for k, inst in zip(key_of, insts):
+        uniq.setdefault(k, inst)
+    ukeys = list(uniq)
+    t0 = time.perf_counter()
+    long_s = pb.make_schedule(pb.PB_SCHED_GEOMETRIC, 10000, BETA0, BETA1)
+    runs = pb.pb_anneal_batch([uniq[k] for k in ukeys], [long_s] * len(ukeys), [256] * len(ukeys),
+                              [77 + q for q in range(len(ukeys))], stream=stream)
+    eref = {k: float(pb.pb_energy(r, 256)[1].min()) for k, r in zip(ukeys, runs)}
+    for r in runs:
+        pb.pb_run_destroy(r)
+    eref_s = time.perf_counter() - t0
     scheds = [pb.make_schedule(pb.PB_SCHED_GEOMETRIC, j[4], BETA0, BETA1) for j in jobs]
-    rng = np.random.default_rng(11)
-    gaps = rng.exponential(1.0 / 500.0, size=n_req)
+    target = [(p_ea if j[0] == "ea" else p_bq) * eref[k] for j, k in zip(jobs, key_of)]
+    opts = [pb.make_opts(pb.PB_FORM_AUTO, t, pb.PB_FLAG_STOP_AT_TARGET) for t in target]
+    seeds = [90000 + q for q in range(n_req)]
+    spins = [j[1] ** 3 if j[0] == "ea" else 2 * j[1] for j in jobs]
+
+    def serve(idx, gaps):
+        """Submit requests idx at the given inter-arrival gaps (None: all at once); returns
+        (span s, per-request best energies, target sweeps, server stats)."""
+        torch.cuda.synchronize()
+        sv = pb.pb_server_create(max_inflight=512, gather_us=0)
+        tickets = [None] * len(idx)
+        t_start = time.perf_counter()
+
+        def submitter():
+            t = t_start
+            for a, q in enumerate(idx):
+                if gaps is not None:
+                    t += gaps[a]
+                    d = t - time.perf_counter()
+                    if d > 0:
+                        time.sleep(d)
+                tickets[a] = pb.pb_server_submit(sv, insts[q], scheds[q], jobs[q][3], seeds[q], opts[q])
+
+        th = threading.Thread(target=submitter)
+        th.start()
+        th.join()
+        best, hits = {}, {}
+        for a, q in enumerate(idx):
+            run, _ = pb.pb_server_wait(sv, tickets[a], -1)
+            best[q] = pb.pb_energy(run, jobs[q][3])[1]
+            hits[q] = pb.pb_target_sweeps(run, jobs[q][3])
+            pb.pb_run_destroy(run)
+        span = time.perf_counter() - t_start
+        st = pb.pb_server_stats_get(sv)
+        pb.pb_server_destroy(sv)
+        return span, best, hits, st
+
+    allq = list(range(n_req))
+    gaps = np.random.default_rng(11).exponential(1.0 / lam, size=n_req)
+    span, best, hits, st = serve(allq, gaps)
+    # maximum sustainable rate: a burst of the first 4000 requests submitted at once
+    burst = allq[: min(4000, n_req)]
+    bspan, _, _, bst = serve(burst, None)
+    mu_max = len(burst) / bspan
+    # plain per-instance forms on every 20th request, one after another
+    sub = allq[::20]
     torch.cuda.synchronize()
-    sv = pb.pb_server_create(max_inflight=512, gather_us=0)
-    tickets = [None] * n_req
-    t_start = time.perf_counter()
-
-    def submitter():
-        t = t_start
-        for q in range(n_req):
-            t += gaps[q]
-            d = t - time.perf_counter()
-            if d > 0:
-                time.sleep(d)
-            tickets[q] = pb.pb_server_submit(sv, insts[q], scheds[q], jobs[q][3], 90000 + q)
-
-    th = threading.Thread(target=submitter)
-    th.start()
-    th.join()
-    for q in range(n_req):
-        run, _ = pb.pb_server_wait(sv, tickets[q], -1)
+    pbest = {}
+    t0 = time.perf_counter()
+    for q in sub:
+        f = pb.PB_FORM_PLAIN if jobs[q][0] == "ea" else pb.PB_FORM_CUDACORE
+        run = pb.pb_anneal(insts[q], scheds[q], jobs[q][3], seeds[q], pb.make_opts(f, target[q], pb.PB_FLAG_STOP_AT_TARGET),
+                           stream=stream)
+        pbest[q] = pb.pb_energy(run, jobs[q][3])[1]
         pb.pb_run_destroy(run)
-    t_end = time.perf_counter()
-    st = pb.pb_server_stats_get(sv)
-    pb.pb_server_destroy(sv)
+    plain_s = time.perf_counter() - t0
+    served_sub_s = sum(1 for _ in sub) / mu_max      # the same requests at the served maximum rate
+    pm1_same, g_ok, g_n, ks_p = True, 0, 0, []
+    res_served, res_plain = [], []
+    for q in sub:
+        a, b = best[q], pbest[q]
+        e_ref, n_sp = eref[key_of[q]], spins[q]
+        res_served.append((a.min() - e_ref) / n_sp)
+        res_plain.append((b.min() - e_ref) / n_sp)
+        if jobs[q][2] == "pm1":
+            pm1_same &= bool(np.array_equal(a, b))
+        else:
+            g_n += 1
+            se = math.sqrt(a.var(ddof=1) / a.size + b.var(ddof=1) / b.size) if a.size > 1 else 0.0
+            g_ok += int(abs(a.mean() - b.mean()) <= 3 * se + 1e-9 * abs(a.mean()))
+            ks_p.append(ks_2samp_p(a, b))
+    reached = np.array([float((hits[q] >= 0).mean()) for q in allq])
+    res_all = np.array([(best[q].min() - eref[key_of[q]]) / spins[q] for q in allq])
+    upd = sum(job_updates(j) for j in jobs)
     for i in owned:
         pb.pb_instance_destroy(i)
-    upd = sum(job_updates(j) for j in jobs)
-    span = t_end - t_start
     return {"workload": "Poisson arrivals 500/s (seed 11) of mixed jobs (EA L in {8,12,16,24} / biclique n in "
-                        "{128,...,2048}, +-1 / N(0,1), replicas 32..1024, sweeps log-uniform in [50, 1000]), "
-                        "48 distinct instances",
-            "requests": n_req, "seconds": span, "throughput_updates_per_s": upd / span,
-            "requests_per_s": n_req / span, "offered_req_per_s": 500.0,
+                        "{128,...,2048}, +-1 / N(0,1), replicas 32..1024, sweep budgets log-uniform in [50, 1000]), "
+                        "48 distinct instances; target p E_ref (p = 0.99 EA, 0.95 biclique), stop at the target",
+            "requests": n_req, "seconds": span, "requests_per_s": n_req / span, "offered_req_per_s": lam,
+            "budget_updates_per_s": upd / span,
             "p50_ms": st.p50_ms, "p99_ms": st.p99_ms, "mean_ms": st.mean_ms, "max_ms": st.max_ms,
-            "rounds": st.rounds, "peak_inflight_bytes": st.peak_inflight_bytes, "failed": st.failed}
+            "rounds": st.rounds, "peak_inflight_bytes": st.peak_inflight_bytes, "failed": st.failed,
+            "max_sustainable_req_per_s": mu_max, "offered_load_rho": lam / mu_max,
+            "burst": {"requests": len(burst), "seconds": bspan, "p99_ms": bst.p99_ms},
+            "e_ref": {"how": "best of a 1e4-sweep geometric 0.1->5.0 anneal with 256 replicas per instance",
+                      "instances": len(ukeys), "seconds": eref_s},
+            "target": {"requests_all_replicas_reached": int((reached == 1.0).sum()),
+                       "mean_fraction_of_replicas_reached": float(reached.mean()),
+                       "residual_per_spin_median": float(np.median(res_all)),
+                       "residual_per_spin_p90": float(np.quantile(res_all, 0.9))},
+            "plain_on_every_20th_request": {
+                "requests": len(sub), "plain_seconds": plain_s, "plain_req_per_s": len(sub) / plain_s,
+                "served_req_per_s_at_max_rate": mu_max, "speedup": mu_max / (len(sub) / plain_s),
+                "served_seconds_equiv": served_sub_s,
+                "pm1_requests_identical": pm1_same, "gauss_requests_mean_within_3se": f"{g_ok}/{g_n}",
+                "gauss_requests_ks_2samp": ks_summary(ks_p),
+                "residual_per_spin_ks_p": ks_2samp_p(np.array(res_served), np.array(res_plain)),
+                "residual_per_spin_mean": {"served": float(np.mean(res_served)), "plain": float(np.mean(res_plain))},
+                "plain_forms": "EA plain (one launch per colour and sweep), biclique FP32 CUDA-core"}}
 
 
 # ------------------------------------------------------ next rows (f1-f4)
@@ -619,29 +738,36 @@ def extensions_block(pb, stream, peaks):
         "ms": ms, "kernel_ms": kms, "updates_per_s": N * G * S / (kms / 1e3), "best_E_per_spin": float(be.min()) / N,
         "exchange_acceptance": [float(a) / (C * (S // 2)) for a in acc]}
     pb.pb_instance_destroy(inst)
-    # f4: sparsified biclique n = 512 on the general-graph path vs the dense tensor form
+    # f4: sparsified biclique n = 512 on the general-graph path vs the dense tensor form, at several
+    # copy strengths (the copies of a vertex must agree for the projection to keep the energy)
     n, R, S = 512, 256, 300
     Jb = pb.pb_generate_biclique(n, pb.PB_DIST_PM1, 72)
-    sp = pb.pb_sparsify_biclique(Jb, 4, 2)
-    sinst = pb.pb_create_graph_instance(sp["N"], sp["eu"], sp["ev"], sp["J"], None, sp["colour"], stream=stream)
     dinst = pb.pb_create_instance(pb.PB_TOPO_BICLIQUE, Jb, None, n=n, stream=stream)
     sc = pb.make_schedule(pb.PB_SCHED_LINEAR, S, 0.35, 3.5)
-    ms_s, run = timed(lambda: pb.pb_anneal(sinst, sc, R, 3, stream=stream))
-    proj = pb.pb_sparse_project(sp["copy_of"], 2 * n, pb.pb_best_states(run, R, sp["N"]))
-    pb.pb_run_destroy(run)
     ms_d, run = timed(lambda: pb.pb_anneal(dinst, sc, R, 3, stream=stream))
     dense_best = float(pb.pb_energy(run, R)[1].min())
     pb.pb_run_destroy(run)
-    F = pb.pb_fields(dinst, proj, stream=stream)  # biclique energies of the projected states: -(sum m F)/2
-    e_proj = -0.5 * (proj.astype(np.float64) * F.astype(np.float64)).sum(axis=1)
-    pb.pb_instance_destroy(sinst)
+    by_strength = []
+    for cs in (2, 6, 16):
+        sp = pb.pb_sparsify_biclique(Jb, 4, cs)
+        sinst = pb.pb_create_graph_instance(sp["N"], sp["eu"], sp["ev"], sp["J"], None, sp["colour"], stream=stream)
+        ms_s, run = timed(lambda: pb.pb_anneal(sinst, sc, R, 3, stream=stream))
+        bst = pb.pb_best_states(run, R, sp["N"])
+        pb.pb_run_destroy(run)
+        pb.pb_instance_destroy(sinst)
+        proj = pb.pb_sparse_project(sp["copy_of"], 2 * n, bst)
+        F = pb.pb_fields(dinst, proj, stream=stream)  # biclique energies of the projected states: -(sum m F)/2
+        e_proj = -0.5 * (proj.astype(np.float64) * F.astype(np.float64)).sum(axis=1)
+        # copy agreement: fraction of copies whose spin equals their vertex's projected (majority) spin
+        agree = float((bst == proj[:, sp["copy_of"]]).mean())
+        by_strength.append({"copy_strength": cs, "spins": sp["N"], "sparse_ms": ms_s,
+                            "best_E_per_spin_projected": float(e_proj.min()) / (2 * n),
+                            "copy_agreement": agree})
     pb.pb_instance_destroy(dinst)
     out["sparsified_biclique"] = {
-        "workload": f"biclique n={n} +-J, copy graph (<= 6 neighbours, copy strength 2, {sp['N']} spins), "
-                    f"{R} replicas, {S} sweeps linear 0.35->3.5",
-        "sparse_ms": ms_s, "dense_tensor_ms": ms_d,
-        "best_E_per_spin_sparse_projected": float(e_proj.min()) / (2 * n),
-        "best_E_per_spin_dense": dense_best / (2 * n)}
+        "workload": f"biclique n={n} +-J, copy graph (<= 4 edges per copy, copy edges of strength c), "
+                    f"{R} replicas, {S} sweeps linear 0.35->3.5; projection by majority of copies",
+        "dense_tensor_ms": ms_d, "best_E_per_spin_dense": dense_best / (2 * n), "by_copy_strength": by_strength}
     # f2: Algorithm 1 on an EA L = 8 +-J cube
     J8 = pb.pb_generate_ea(8, pb.PB_DIST_PM1, 73)
     einst = pb.pb_create_instance(pb.PB_TOPO_EA3D, J8, None, L=8, stream=stream)
@@ -723,7 +849,7 @@ def main():
     ap.add_argument("--no-extensions", action="store_true",
                     help="skip general graphs, tempering, sparsified biclique and Algorithm 1")
     ap.add_argument("--no-serve", action="store_true", help="skip the served Poisson stream")
-    ap.add_argument("--serve-requests", type=int, default=1500, help="requests of the served stream")
+    ap.add_argument("--serve-requests", type=int, default=15000, help="requests of the served stream")
     ap.add_argument("--case", default=None, choices=sorted(CASES),
                     help="run one small launch of a hot-path kernel (for ncu) and exit")
     args = ap.parse_args()
@@ -908,6 +1034,7 @@ def main():
         line["config1"] = config1_block(pb, stream)
     if rank == 0 and not args.no_biclique:
         line["biclique"] = biclique_block(pb, stream, peaks)
+        line["biclique_sweep"] = biclique_sweep_block(pb, stream, peaks)
     if rank == 0 and not args.no_extensions:
         line["next_rows"] = extensions_block(pb, stream, peaks)
     if rank == 0 and not args.no_mixed:

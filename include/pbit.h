@@ -131,7 +131,8 @@ typedef enum pb_form {
  * changing at the first sweep whose energy is <= target (its best energy, state
  * and sweep are then those of that sweep, the recorded target sweep), and the
  * run ends early once every replica has reached the target; otherwise after all
- * sweeps.  The best results of a replica depend only on its own trajectory, so
+ * sweeps (forms that launch per sweep still issue their remaining launches, which
+ * return at once).  The best results of a replica depend only on its own trajectory, so
  * they are the same in every form, alone or in a batch.  The final state and
  * energy are those of the sweep at which the replica's block of the run stopped,
  * which depends on the form. */
