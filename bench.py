@@ -792,6 +792,7 @@ CASES = {
     "ea-L32-pm1-small": ("ea", 32, "pm1", 608, 50, "resident"),
     "ea-L32-gauss-small": ("ea", 32, "gauss", 608, 50, "resident"),
     "ea-L16-pm1-small": ("ea", 16, "pm1", 2432, 50, "resident"),
+    "ea-L16-gauss-small": ("ea", 16, "gauss", 2432, 50, "resident"),
     "ea-L24-pm1-small": ("ea", 24, "pm1", 608, 50, "resident"),      # generic tile (WT = 1)
     "ea-L12-pm1-small": ("ea", 12, "pm1", 2432, 50, "resident"),     # generic tile (WT = 4)
     "ea-L24-gauss-small": ("ea", 24, "gauss", 608, 50, "resident"),  # generic tile, FP32
@@ -805,13 +806,16 @@ CASES = {
 }
 
 
-def run_case(name):
-    """One launch of the hot-path kernel on a small case (152 tiles: one wave), for ncu."""
+def run_case(name, sweeps=None):
+    """One launch of the hot-path kernel on a small case (152 tiles: one wave), for ncu;
+    `sweeps` overrides the case's sweep count."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
     from paper_2510_23419_gb300 import native as pb
     topo, size, law, R, S, form = CASES[name]
+    if sweeps:
+        S = sweeps
     dist = {"pm1": pb.PB_DIST_PM1, "gauss": pb.PB_DIST_GAUSS, "unif": pb.PB_DIST_UNIF}[law]
     forms = {"resident": pb.PB_FORM_RESIDENT, "plain": pb.PB_FORM_PLAIN, "cudacore": pb.PB_FORM_CUDACORE,
              "tensor": pb.PB_FORM_TENSOR}
@@ -852,9 +856,10 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=15000, help="requests of the served stream")
     ap.add_argument("--case", default=None, choices=sorted(CASES),
                     help="run one small launch of a hot-path kernel (for ncu) and exit")
+    ap.add_argument("--case-sweeps", type=int, default=None, help="sweeps of the --case run")
     args = ap.parse_args()
     if args.case:
-        run_case(args.case)
+        run_case(args.case, args.case_sweeps)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
