@@ -274,7 +274,9 @@ __global__ void __launch_bounds__(256) bq_sweep_end_kernel(BqJob job, int s_arg,
         }
     }
     __syncthreads();
-    if (threadIdx.x < kEndReps) {
+    if (threadIdx.x < kEndReps && r0 + (int)threadIdx.x >= job.R) {
+        s_copy[threadIdx.x] = 0;  // padding replicas: nothing to record (the tensor form leaves them as they are)
+    } else if (threadIdx.x < kEndReps) {
         const int r = r0 + threadIdx.x;
         bool imp, hit_now = false;
         const int prev = init ? -2 : job.best_sweep[r];
@@ -323,7 +325,8 @@ __global__ void __launch_bounds__(256) bq_best_flush_kernel(BqJob job)
     __shared__ int s_copy[kEndReps];
     const int r0 = blockIdx.x * kEndReps;
     const int last = bq_last_sweep(job);
-    if (threadIdx.x < kEndReps) s_copy[threadIdx.x] = job.best_sweep[r0 + threadIdx.x] == last ? 1 : 0;
+    if (threadIdx.x < kEndReps)
+        s_copy[threadIdx.x] = (r0 + (int)threadIdx.x < job.R && job.best_sweep[r0 + threadIdx.x] == last) ? 1 : 0;
     __syncthreads();
     bq_copy_flagged(job, r0, s_copy, last & 1);
 }

@@ -495,9 +495,20 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                                                 job.key1);
             for (int cc = 0; cc < kEpiCols / 32; ++cc) {
                 const int c = slot * (kEpiCols / 32) + cc;
+                const bool last = cc == kEpiCols / 32 - 1;
+                if (r0 + c * 32 >= job.R) {
+                    // 32 replicas of the tile's padding: nothing to decide, store or sum (their
+                    // columns of the product depend only on their own spins, which stay as set)
+                    if (last) {
+                        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive_cluster(buf ? acce_r1 : acce_r0);
+                    }
+                    continue;
+                }
                 float v[32];
                 tmem_ld32(taddr + (uint32_t)(c * 32), v);
-                if (cc == kEpiCols / 32 - 1) {
+                if (last) {
                     // this warp has read its part of the accumulator: release the buffer
                     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                     __syncwarp();

@@ -475,7 +475,7 @@ pb_status ea_batch_launch(std::vector<pb_run*>& runs, const std::shared_ptr<Batc
     // the kernels simply run one after the other.
     const bool capture = st != nullptr && st != cudaStreamLegacy && st != cudaStreamPerThread;
     cudaGraph_t graph = nullptr;
-    PB_CUDA_TRY(cudaEventRecord(runs[0]->ev_start, st));
+    for (pb_run* r : runs) PB_CUDA_TRY(cudaEventRecord(r->ev_start, st));  // every run spans the shared launch
     if (capture) PB_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     auto body = [&]() -> pb_status {
         PB_CUDA_TRY(cudaMemsetAsync(shared->counter.p, 0, 16, st));
@@ -513,11 +513,7 @@ pb_status ea_batch_launch(std::vector<pb_run*>& runs, const std::shared_ptr<Batc
     } else if (ps != PB_OK) {
         return ps;
     }
-    PB_CUDA_TRY(cudaEventRecord(runs[0]->ev_stop, st));
-    for (size_t q = 1; q < runs.size(); ++q) {
-        PB_CUDA_TRY(cudaEventRecord(runs[q]->ev_start, st));
-        PB_CUDA_TRY(cudaEventRecord(runs[q]->ev_stop, st));
-    }
+    for (pb_run* r : runs) PB_CUDA_TRY(cudaEventRecord(r->ev_stop, st));
     for (pb_run* r : runs) r->batch = shared;
     return PB_OK;
 }
