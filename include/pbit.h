@@ -328,7 +328,9 @@ pb_status pb_find_imin(pb_instance* inst, const pb_imin_opts* opts, void* stream
 /* Autotuner.  Times each candidate launch choice for `inst` with `replicas`
  * replicas on a short probe anneal of `probe_sweeps` sweeps (linear beta
  * 0.1 -> 3.0) on `stream`: EA resident form with every valid tile width (replica
- * words per tile) and the plain form; biclique tensor and CUDA-core forms.  The
+ * words per tile) and the plain form; biclique tensor form with whole tiles and
+ * with a sparse last round split into half-width tiles, the CUDA-core form and,
+ * where it fits, the resident form.  The
  * cost of a candidate is its sweep-loop time times the SMs it keeps busy (a
  * batch fills the SMs that a small job leaves idle); the cheapest is returned
  * and stored in a process-wide table keyed by (topology, L or n, coupling type,
@@ -336,7 +338,10 @@ pb_status pb_find_imin(pb_instance* inst, const pb_imin_opts* opts, void* stream
  * and pb_anneal_batch then use.  Synchronous. */
 typedef struct pb_tune_result {
     int32_t form;              /* chosen pb_form */
-    int32_t tile_width;        /* EA resident: replica words (4 replicas each) per tile; else 0 */
+    int32_t tile_width;        /* EA resident: replica words (4 replicas each) per tile; biclique tensor
+                                  form: 1 = a sparse last round of 256-replica tiles is split into
+                                  128-replica tiles (shorter latency, more SM-time), 0 = whole tiles;
+                                  else 0 */
     int32_t n_candidates;
     int32_t candidate_form[8];
     int32_t candidate_wt[8];

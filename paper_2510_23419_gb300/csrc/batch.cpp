@@ -136,7 +136,11 @@ void choose_form(const pb_instance* I, int R, int requested, int& form, int& wt)
     } else if (I->topo == PB_TOPO_CSR) {
         if (form == PB_FORM_AUTO) form = PB_FORM_PLAIN;
     } else {
-        if (tuned) form = te.form;
+        wt = 1;  // tensor form: split a sparse last round of tiles (lowest latency) unless tuned otherwise
+        if (tuned) {
+            form = te.form;
+            wt = te.wt;
+        }
         // small instances: the resident form (no launch per half-sweep); else tensor cores
         if (form == PB_FORM_AUTO) form = bq_resident_fits(I) ? PB_FORM_RESIDENT : PB_FORM_TENSOR;
     }
@@ -210,7 +214,7 @@ pb_status batch_start(int count, pb_instance* const* insts, const pb_schedule* s
         } else {
             pb_anneal_opts oo = o ? *o : pb_anneal_opts{PB_FORM_AUTO, 0, NAN};
             oo.form = j.form;
-            ps = bq_setup(r, j.I, &scheds[j.q], j.R, seeds[j.q], &oo, st);
+            ps = bq_setup(r, j.I, &scheds[j.q], j.R, seeds[j.q], &oo, st, j.wt);
         }
         if (ps != PB_OK) return ps;
     }
@@ -360,6 +364,8 @@ pb_status pb_autotune(pb_instance* I, int32_t R, int32_t probe_sweeps, void* str
     } else if (I->topo == PB_TOPO_CSR) {
         cand.push_back({PB_FORM_PLAIN, 0});
     } else {
+        // tensor form with a sparse last round of tiles split into 128-replica tiles (wt 1) or not (wt 0)
+        cand.push_back({PB_FORM_TENSOR, 1});
         cand.push_back({PB_FORM_TENSOR, 0});
         cand.push_back({PB_FORM_CUDACORE, 0});
         if (bq_resident_fits(I)) cand.push_back({PB_FORM_RESIDENT, 0});
@@ -396,11 +402,11 @@ pb_status pb_autotune(pb_instance* I, int32_t R, int32_t probe_sweeps, void* str
             ps = csr_setup(run.get(), I, &sc, R, 1, &o, st);
             if (ps == PB_OK) ps = csr_launch(run.get(), st);
         } else {
-            ps = bq_setup(run.get(), I, &sc, R, 1, &o, st);
+            ps = bq_setup(run.get(), I, &sc, R, 1, &o, st, wt);
             if (ps == PB_OK) ps = bq_launch(run.get(), st);
             if (form == PB_FORM_TENSOR) {
-                const int nrp = ((I->n + 127) / 128 + 1) / 2;
-                units = std::min(sms, 2 * nrp * ((R + 255) / 256));
+                units = std::min(sms, 2 * bq_tc_clusters(I->n, run->bjob.Rpad, I->jtype == PB_J_PM1_I8 ? 0 : 1,
+                                                         wt != 0));
             } else if (form == PB_FORM_RESIDENT) {
                 units = std::min(sms, (R + 31) / 32);
             } else {

@@ -177,7 +177,7 @@ bool bq_resident_fits(const pb_instance* I)
 }
 
 static pb_status bq_prepare(pb_run* run, pb_instance* I, const pb_schedule* sc, int R, uint64_t seed,
-                            const pb_anneal_opts* opts, int form, cudaStream_t st)
+                            const pb_anneal_opts* opts, int form, int tile_split, cudaStream_t st)
 {
     std::vector<double> betas;
     int step = 1;
@@ -203,6 +203,7 @@ static pb_status bq_prepare(pb_run* run, pb_instance* I, const pb_schedule* sc, 
     j.S = sc->n_sweeps;
     j.step = step;
     j.R = R;
+    j.tile_split = tile_split;
     const bool tensor = form == PB_FORM_TENSOR;
     const bool resident = form == PB_FORM_RESIDENT;
     run->form = form;
@@ -351,7 +352,7 @@ static pb_status bq_enqueue_chunk(pb_run* run, int nsweeps, cudaStream_t st)
 }
 
 pb_status bq_setup(pb_run* run, pb_instance* I, const pb_schedule* sc, int R, uint64_t seed,
-                   const pb_anneal_opts* opts, cudaStream_t st)
+                   const pb_anneal_opts* opts, cudaStream_t st, int tile_split)
 {
     int form = opts ? opts->form : PB_FORM_AUTO;
     if (form == PB_FORM_AUTO) form = PB_FORM_TENSOR;
@@ -359,7 +360,7 @@ pb_status bq_setup(pb_run* run, pb_instance* I, const pb_schedule* sc, int R, ui
         return fail(PB_EUNSUPPORTED, "form not available for biclique instances");
     if (form == PB_FORM_RESIDENT && !bq_resident_fits(I))
         return fail(PB_EUNSUPPORTED, "biclique too large for the resident form (n <= 256 for +-1, n <= 128 for F32)");
-    return bq_prepare(run, I, sc, R, seed, opts, form, st);
+    return bq_prepare(run, I, sc, R, seed, opts, form, tile_split, st);
 }
 
 // The anneal on `st`: initial state and its energy, the sweeps as repeated
@@ -437,9 +438,9 @@ pb_status bq_launch(pb_run* run, cudaStream_t st)
 }
 
 pb_status bq_anneal(pb_run* run, pb_instance* I, const pb_schedule* sc, int R, uint64_t seed,
-                    const pb_anneal_opts* opts, cudaStream_t st)
+                    const pb_anneal_opts* opts, cudaStream_t st, int tile_split)
 {
-    pb_status ps = bq_setup(run, I, sc, R, seed, opts, st);
+    pb_status ps = bq_setup(run, I, sc, R, seed, opts, st, tile_split);
     if (ps != PB_OK) return ps;
     return bq_launch(run, st);
 }
@@ -455,7 +456,7 @@ pb_status bq_fields(pb_instance* I, const int8_t* d_states, int R, int form, flo
     sc.n_sweeps = 1;
     sc.step_duration = 1;
     sc.beta0 = sc.beta1 = 0.0;
-    pb_status ps = bq_prepare(&run, I, &sc, R, 0, nullptr, form, st);
+    pb_status ps = bq_prepare(&run, I, &sc, R, 0, nullptr, form, 1, st);
     if (ps != PB_OK) return ps;
     PB_CUDA_TRY(bq_launch_encode(run.bjob, d_states, st));
     PB_CUDA_TRY(bq_half(&run, 0, 0, 0, 0, nullptr, 0, d_out, st));

@@ -275,7 +275,35 @@ __device__ __forceinline__ float warp_transpose_sum(float (&e)[32], int lane)
     return e[0];
 }
 
-// Persistent kernel over CTA pairs (clusters of two).  Cluster c processes
+// Cluster-tile vt of a launch: row pair p, first replica rb and replica count.
+// The tiles of a side are (row pair, 256-replica block) pairs, T of them; when
+// the last round of the persistent loop would keep at most half the clusters
+// busy (L = T mod clusters tiles, 2L <= clusters, including the case of a
+// single round), those L tiles are split into 2L tiles of 128 replicas (an
+// N = 128 MMA chain each), so that the last round takes about half as long.
+// Each half still loads its full J rows, so the split trades SM-time for
+// latency: a lone run gains, a crowded batch loses; the run's tile_split flag
+// (the autotuner's choice per shape, on by default) decides.
+struct TcTile {
+    int p, rb, ncols;
+};
+
+__host__ __device__ __forceinline__ void tc_tile_split(int T, int nclus, bool allow, int& nfull, int& nvirt)
+{
+    const int L = T % nclus;
+    const bool split = allow && L > 0 && 2 * L <= nclus;
+    nfull = split ? T - L : T;
+    nvirt = split ? T + L : T;
+}
+
+__device__ __forceinline__ TcTile tc_tile(int vt, int nrp, int nfull)
+{
+    if (vt < nfull) return TcTile{vt % nrp, (vt / nrp) * TBN, TBN};
+    const int h = vt - nfull, t = nfull + (h >> 1);
+    return TcTile{t % nrp, (t / nrp) * TBN + (h & 1) * (TBN / 2), TBN / 2};
+}
+
+// Persistent kernel over CTA pairs (clusters of two).  Cluster c processes// Persistent kernel over CTA pairs (clusters of two).  Cluster c processes
 // the cluster-tiles ct = c, c + nclusters, ...; cluster-tile ct is (row pair
 // p = ct % nrp, replica block b = ct / nrp), a 256-row x 256-replica tile
 // computed by one M=256, N=256 MMA chain over the pair: the CTA of rank k
@@ -324,8 +352,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     const int n = job.inst.n;
     const int nkb = (n + Cfg::KELEM - 1) / Cfg::KELEM;
     const int nrp = (((n + TBM - 1) / TBM) + 1) / 2;
-    const int nct = nrp * (job.Rpad / TBN);
     const int clus = blockIdx.x >> 1, nclus = gridDim.x >> 1;
+    int nfull, nct;  // whole tiles, and all tiles of the launch (whole + halves of the last round)
+    tc_tile_split(nrp * (job.Rpad / TBN), nclus, job.tile_split != 0, nfull, nct);
     const uint32_t crank = cluster_rank();
 
     if (threadIdx.x == 0) {
@@ -362,8 +391,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
             const uint32_t fb0 = map_rank(&full_bar[0], 0);
             bool ok = true;
             for (int ct = clus; ct < nct && ok; ct += nclus) {
-                const int i0 = (2 * (ct % nrp) + (int)crank) * TBM;
-                const int r0 = (ct / nrp) * TBN + (int)crank * (TBN / 2);
+                // (a 128-replica tile still loads a 128-row box per CTA; its MMA reads the first 64)
+                const TcTile tl = tc_tile(ct, nrp, nfull);
+                const int i0 = (2 * tl.p + (int)crank) * TBM;
+                const int r0 = tl.rb + (int)crank * (tl.ncols / 2);
                 for (int kb = 0; kb < nkb; ++kb) {
                     if (!mbar_wait(&empty_bar[st], ph ^ 1u, job.wait_ns)) {
                         atomicOr(err, 1);
@@ -387,7 +418,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     } else if (warp == 1) {
         // ---------------- MMA issuer (even CTA only) ----------------
         if (lane == 0 && crank == 0) {
-            constexpr uint32_t idesc = instr_desc(KIND == 0 ? 0u : 1u, 2 * TBM, TBN);
+            constexpr uint32_t idesc_full = instr_desc(KIND == 0 ? 0u : 1u, 2 * TBM, TBN);
+            constexpr uint32_t idesc_half = instr_desc(KIND == 0 ? 0u : 1u, 2 * TBM, TBN / 2);
             // descriptor of the ring's first byte; a stage or K offset only adds to
             // the start-address field (shared addresses stay below 2^18, so the
             // 14-bit field of addr >> 4 never carries)
@@ -396,6 +428,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
             uint32_t ph = 0, j = 0;
             bool ok = true;
             for (int ct = clus; ct < nct && ok; ct += nclus, ++j) {
+                const uint32_t idesc = ct < nfull ? idesc_full : idesc_half;
                 const uint32_t buf = j & 1u, aph = (j >> 1) & 1u;
                 if (!mbar_wait(&acce_bar[buf], aph ^ 1u, job.wait_ns)) {
                     atomicOr(err, 8);
@@ -473,9 +506,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
         bool ok = true;
         for (int ct = clus; ct < nct; ct += nclus, ++j) {
             const uint32_t buf = j & 1u, aph = (j >> 1) & 1u;
-            const int rt = 2 * (ct % nrp) + (int)crank;
+            const TcTile tl = tc_tile(ct, nrp, nfull);
+            const bool half_tile = tl.ncols != TBN;  // 128 replicas: one 32-column chunk per epilogue warp
+            const int rt = 2 * tl.p + (int)crank;
             const int i = rt * TBM + row;
-            const int r0 = (ct / nrp) * TBN;
+            const int r0 = tl.rb;
             if (ok && !mbar_wait(&accf_bar[buf], aph, job.wait_ns)) {
                 atomicOr(err, 4);
                 ok = false;
@@ -494,11 +529,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
             const PhiloxFixed pf = philox_fixed((uint32_t)i, (uint32_t)s, (kTagDecision << 24) | (uint32_t)side, job.key0,
                                                 job.key1);
             for (int cc = 0; cc < kEpiCols / 32; ++cc) {
-                const int c = slot * (kEpiCols / 32) + cc;
+                const int c = half_tile ? slot : slot * (kEpiCols / 32) + cc;
                 const bool last = cc == kEpiCols / 32 - 1;
-                if (r0 + c * 32 >= job.R) {
+                if ((half_tile && cc > 0) || r0 + c * 32 >= job.R) {
                     // 32 replicas of the tile's padding: nothing to decide, store or sum (their
-                    // columns of the product depend only on their own spins, which stay as set)
+                    // columns of the product depend only on their own spins, which stay as set);
+                    // a 128-replica tile has only one chunk per warp
                     if (last) {
                         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                         __syncwarp();
@@ -712,8 +748,10 @@ cudaError_t bq_launch_tc_half(const BqTcMaps& maps, int bsel, const BqJob& job, 
     const int kind = job.inst.jtype == PB_J_PM1_I8 ? 0 : 1;
     const size_t smem = bq_tc_smem_bytes(kind);
     const int nrp = (((job.inst.n + TBM - 1) / TBM) + 1) / 2;
-    const int nct = nrp * (job.Rpad / TBN);
-    const int nclus = std::max(1, std::min(nct, tc_active_clusters(kind)));
+    const int active = tc_active_clusters(kind);
+    int nfull = 0, nvirt = 0;  // the kernel makes the same split from the grid it gets
+    tc_tile_split(nrp * (job.Rpad / TBN), active, job.tile_split != 0, nfull, nvirt);
+    const int nclus = std::max(1, std::min(nvirt, active));
     dim3 grid((unsigned)(2 * nclus));  // persistent clusters of two CTAs
     const CUtensorMap& A = side == 0 ? maps.a[0] : maps.a[2];
     const CUtensorMap& A2 = side == 0 ? maps.a[1] : maps.a[3];
@@ -727,6 +765,15 @@ cudaError_t bq_launch_tc_half(const BqTcMaps& maps, int bsel, const BqJob& job, 
     else
         bq_tc_half_kernel<1, 0><<<grid, kThreads, smem, st>>>(A, A2, B, job, side, s, sp, decide, fields_out, err);
     return cudaGetLastError();
+}
+
+int bq_tc_clusters(int n, int Rpad, int kind, bool split)
+{
+    const int nrp = (((n + TBM - 1) / TBM) + 1) / 2;
+    const int active = tc_active_clusters(kind);
+    int nfull = 0, nvirt = 0;
+    tc_tile_split(nrp * (Rpad / TBN), active, split, nfull, nvirt);
+    return std::max(1, std::min(nvirt, active));
 }
 
 }  // namespace pb

@@ -30,5 +30,8 @@ cudaError_t bq_tc_make_map(CUtensorMap* map, const void* base, int elem_bytes, u
 // must name the matching buffers.
 cudaError_t bq_launch_tc_half(const BqTcMaps& maps, int bsel, const BqJob& job, int side, int s, const int32_t* sp,
                               int decide, float* fields_out, int* err, cudaStream_t st);
+// CTA pairs a half-sweep launch of an n x n biclique with Rpad replicas occupies
+// (kind 0 e4m3, 1 split BF16; split: the last round's tiles halved).
+int bq_tc_clusters(int n, int Rpad, int kind, bool split);
 
 }  // namespace pb

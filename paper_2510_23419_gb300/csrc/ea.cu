@@ -345,6 +345,7 @@ __device__ void ea_tile(const EaJob& job, int tile, unsigned char* smem)
     }
 
     // ---- sweeps ----
+    const bool stop_mode = job.has_target == 2;
     for (int s = job.s0; s < job.S; ++s) {
         uint32_t uacc = 0;
         int32_t hm[4] = {0, 0, 0, 0};
@@ -377,7 +378,7 @@ __device__ void ea_tile(const EaJob& job, int tile, unsigned char* smem)
         const uint32_t f = reinterpret_cast<const uint32_t*>(sflag)[g.w];
         tile_store_words<LT, WTT>(g, sp, job.best_words, tile, f * 0xFFu);
         // stop mode: the tile ends once all its replicas (padding included) have reached the target
-        if (job.has_target == 2 && __syncthreads_and(t >= nrep || hit >= 0 || tile * nrep + t >= job.R)) break;
+        if (stop_mode && __syncthreads_and(t >= nrep || hit >= 0 || tile * nrep + t >= job.R)) break;
     }
 
     // ---- results ----

@@ -365,6 +365,7 @@ struct EaFastTile {
             store_words(job.best_words, 0xFFFFFFFFu);
         }
 
+        const bool stop_mode = job.has_target == 2;
         for (int s = job.s0; s < job.S; ++s) {
             uint32_t uacc = 0;
             float ef[4] = {0.f, 0.f, 0.f, 0.f};
@@ -396,7 +397,7 @@ struct EaFastTile {
             const uint32_t f = reinterpret_cast<const uint32_t*>(sflag)[w];
             store_words(job.best_words, f * 0xFFu);
             // stop mode: the tile ends once all its replicas (padding included) have reached the target
-            if (job.has_target == 2 && __syncthreads_and(t >= NREP || hit >= 0 || tile * NREP + t >= job.R)) break;
+            if (stop_mode && __syncthreads_and(t >= NREP || hit >= 0 || tile * NREP + t >= job.R)) break;
         }
 
         store_words(job.final_words, 0xFFFFFFFFu);

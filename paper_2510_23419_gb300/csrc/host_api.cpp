@@ -667,7 +667,7 @@ pb_status pb_anneal_ex(pb_instance* I, const pb_schedule* sc, int32_t R, uint64_
         choose_form(I, R, form, f, wt);
         pb_anneal_opts o = opts ? *opts : pb_anneal_opts{PB_FORM_AUTO, 0, NAN};
         o.form = f;
-        pb_status ps = bq_anneal(run.get(), I, sc, R, seed, &o, st);
+        pb_status ps = bq_anneal(run.get(), I, sc, R, seed, &o, st, wt);
         if (ps != PB_OK) return ps;
     }
     *out = run.release();

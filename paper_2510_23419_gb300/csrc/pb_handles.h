@@ -165,8 +165,9 @@ uint32_t threshold_u32(double beta, double F);
 pb_status bq_build(pb_instance* I, const pb_instance_desc* d, cudaStream_t st);
 void threshold_windows(const std::vector<double>& betas, int nF, int fmin, std::vector<uint32_t>& tab,
                        std::vector<int32_t>& win);
+// tile_split: tensor form, halve the tiles of a sparse last round (BqJob::tile_split)
 pb_status bq_anneal(pb_run* run, pb_instance* I, const pb_schedule* sc, int R, uint64_t seed,
-                    const pb_anneal_opts* opts, cudaStream_t st);
+                    const pb_anneal_opts* opts, cudaStream_t st, int tile_split = 1);
 pb_status bq_fields(pb_instance* I, const int8_t* d_states, int R, int form, float* d_out, cudaStream_t st);
 // Split forms of the anneal: set-up (allocations, tables, copies; may synchronise
 // `st`) and launch (graph capture and launch on `st`, no synchronisation).
@@ -184,7 +185,7 @@ pb_status csr_anneal_resume(pb_instance* I, const pb_schedule* sched, int32_t re
                             const int32_t* best_sweep, cudaStream_t st, pb_run** out);
 int ea_choose_wt(const pb_instance* I, int R, int nF);
 pb_status bq_setup(pb_run* run, pb_instance* I, const pb_schedule* sc, int R, uint64_t seed,
-                   const pb_anneal_opts* opts, cudaStream_t st);
+                   const pb_anneal_opts* opts, cudaStream_t st, int tile_split = 1);
 pb_status bq_launch(pb_run* run, cudaStream_t st);
 bool bq_resident_fits(const pb_instance* I);
 pb_status csr_build(pb_instance* I, int32_t N, int64_t n_edges, const int32_t* eu, const int32_t* ev, int jtype,
@@ -196,6 +197,7 @@ pb_status csr_fields(pb_instance* I, const int8_t* d_states, int R, float* d_out
 pb_status wait_run(pb_run* run, int32_t timeout_ms);
 // Form (and EA tile width) for a job: the caller's choice, else the autotuner's
 // table entry for the job's shape, else the built-in rule.
+// wt: EA resident tile width; biclique tensor form: 1 = split a sparse last round of tiles, 0 = whole tiles.
 void choose_form(const pb_instance* I, int R, int requested, int& form, int& wt);
 pb_status batch_start(int count, pb_instance* const* insts, const pb_schedule* scheds, const int32_t* replicas,
                       const uint64_t* seeds, const pb_anneal_opts* opts, cudaStream_t setup_st, bool join,

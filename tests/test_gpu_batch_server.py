@@ -139,7 +139,15 @@ def test_autotune_records_choice(pb):
     binst, bsc, bR, bseed, _ = _make(pb, JOBS[2])
     try:
         t = pb.pb_autotune(binst, bR, 4)
-        assert t.form in (pb.PB_FORM_TENSOR, pb.PB_FORM_CUDACORE, pb.PB_FORM_RESIDENT) and t.n_candidates == 3
+        assert t.form in (pb.PB_FORM_TENSOR, pb.PB_FORM_CUDACORE, pb.PB_FORM_RESIDENT) and t.n_candidates == 4
+        # the tensor form is tried with whole tiles and with the last round split into half-width tiles
+        tensor_wt = sorted(t.candidate_wt[c] for c in range(t.n_candidates) if t.candidate_form[c] == pb.PB_FORM_TENSOR)
+        assert tensor_wt == [0, 1]
+        # a PB_FORM_AUTO anneal follows the table (form and tile choice) and gives the same result as the
+        # explicit tensor form (both tile choices give identical trajectories)
+        a = _alone(pb, binst, bsc, bR, bseed, pb.make_opts(pb.PB_FORM_AUTO))
+        b = _alone(pb, binst, bsc, bR, bseed, pb.make_opts(pb.PB_FORM_TENSOR))
+        _same(a, b)
     finally:
         pb.pb_autotune_clear()
         pb.pb_instance_destroy(binst)
