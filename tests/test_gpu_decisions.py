@@ -102,7 +102,9 @@ EA_CASES = [
     (32, 64, "resident", True, None),
     (16, 2432, "resident", False, [(0, 96), (1200, 96), (2336, 96)]),
     (16, 2432, "resident", True, [(0, 64), (2368, 64)]),
-    (24, 40, "resident", False, None),      # generic tile, FP32
+    (24, 40, "resident", False, None),      # generic tile, compile-time shape L = 24, WT = 1
+    (12, 64, "resident", True, None),       # generic tile, compile-time shape L = 12, WT = 4, with fields
+    (10, 32, "resident", False, None),      # generic tile of runtime shape
     (8, 24, "plain", True, None),           # plain form
 ]
 
