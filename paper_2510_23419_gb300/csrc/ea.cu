@@ -98,12 +98,13 @@ __device__ __forceinline__ void warp_partials_bytes(const TileCtx& g, uint32_t a
 }
 
 // Merge the thread's words of both colours into a global state buffer for the
-// replicas whose byte mask is set (same word partition as the half-sweeps).
+// replicas that `flags` selects (byte b = 1: replica 4w + b of each word;
+// 0x01010101: all), with the same word partition as the half-sweeps.
 template <int LT, int WTT>
 __device__ __forceinline__ void tile_store_words(const TileCtx& g, const uint32_t* sp, uint32_t* gdst, int tile,
-                                                 uint32_t mask)
+                                                 uint32_t flags)
 {
-    if (!g.active || mask == 0u) return;
+    if (!g.active || flags == 0u) return;
     const int L = LT ? LT : g.L;
     const int WT = WTT ? WTT : g.WT;
     const int h2 = L >> 1;
@@ -114,11 +115,10 @@ __device__ __forceinline__ void tile_store_words(const TileCtx& g, const uint32_
         uint32_t* dst = gdst + ((size_t)tile * 2 + c) * half * WT;
         for (int z = g.zfirst; z < L; z += g.zstep) {
             const int kw = (g.q + h2 * (g.y + L * z)) * WT + g.w;
-            const uint32_t v = src[kw];
-            if (mask == 0xFFFFFFFFu)
-                dst[kw] = v;
+            if (WT == 1)
+                snapshot_word<true>(dst + kw, src[kw], flags);
             else
-                dst[kw] = (dst[kw] & ~mask) | (v & mask);
+                snapshot_word<false>(dst + kw, src[kw], flags);
         }
     }
 }
@@ -341,7 +341,7 @@ __device__ void ea_tile(const EaJob& job, int tile, unsigned char* smem)
             bsweep = job.best_sweep[r];
         }
     } else {
-        tile_store_words<LT, WTT>(g, sp, job.best_words, tile, 0xFFFFFFFFu);
+        tile_store_words<LT, WTT>(g, sp, job.best_words, tile, 0x01010101u);
     }
 
     // ---- sweeps ----
@@ -376,13 +376,13 @@ __device__ void ea_tile(const EaJob& job, int tile, unsigned char* smem)
         }
         __syncthreads();
         const uint32_t f = reinterpret_cast<const uint32_t*>(sflag)[g.w];
-        tile_store_words<LT, WTT>(g, sp, job.best_words, tile, f * 0xFFu);
+        tile_store_words<LT, WTT>(g, sp, job.best_words, tile, f);
         // stop mode: the tile ends once all its replicas (padding included) have reached the target
         if (stop_mode && __syncthreads_and(t >= nrep || hit >= 0 || tile * nrep + t >= job.R)) break;
     }
 
     // ---- results ----
-    tile_store_words<LT, WTT>(g, sp, job.final_words, tile, 0xFFFFFFFFu);
+    tile_store_words<LT, WTT>(g, sp, job.final_words, tile, 0x01010101u);
     if (t < nrep) {
         const int r = tile * nrep + t;
         if (JT == PB_J_PM1_I8)

@@ -317,22 +317,17 @@ struct EaFastTile {
         }
     }
 
-    // merge the thread's words of both colours into a global state buffer
-    __device__ __forceinline__ void store_words(uint32_t* gdst, uint32_t mask) const
+    // the thread's words of both colours into a global state buffer, the replicas
+    // that `flags` selects (byte b = 1: replica 4w + b; 0x01010101: all four)
+    __device__ __forceinline__ void store_words(uint32_t* gdst, uint32_t flags) const
     {
-        if (mask == 0u) return;
+        if (flags == 0u) return;
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
             uint32_t* dst = gdst + ((size_t)tile * 2 + c) * CLS + base0;
             const uint32_t* src = sp + c * CLS + base0;
 #pragma unroll 4
-            for (int z = zp; z < L; z += 2) {
-                const uint32_t v = src[z * SZ];
-                if (mask == 0xFFFFFFFFu)
-                    dst[z * SZ] = v;
-                else
-                    dst[z * SZ] = (dst[z * SZ] & ~mask) | (v & mask);
-            }
+            for (int z = zp; z < L; z += 2) snapshot_word<WT == 1>(dst + z * SZ, src[z * SZ], flags);
         }
     }
 
@@ -362,7 +357,7 @@ struct EaFastTile {
                 bsweep = job.best_sweep[r];
             }
         } else {
-            store_words(job.best_words, 0xFFFFFFFFu);
+            store_words(job.best_words, 0x01010101u);
         }
 
         const bool stop_mode = job.has_target == 2;
@@ -395,12 +390,12 @@ struct EaFastTile {
             if (s + 1 < job.S) load_table(s + 1);  // row s was last read before the barrier above
             __syncthreads();
             const uint32_t f = reinterpret_cast<const uint32_t*>(sflag)[w];
-            store_words(job.best_words, f * 0xFFu);
+            store_words(job.best_words, f);
             // stop mode: the tile ends once all its replicas (padding included) have reached the target
             if (stop_mode && __syncthreads_and(t >= NREP || hit >= 0 || tile * NREP + t >= job.R)) break;
         }
 
-        store_words(job.final_words, 0xFFFFFFFFu);
+        store_words(job.final_words, 0x01010101u);
         if (t < NREP) {
             const int r = tile * NREP + t;
             if constexpr (PM1)

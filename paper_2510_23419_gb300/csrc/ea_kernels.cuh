@@ -84,6 +84,31 @@ __device__ __forceinline__ uint32_t decide_f32_word(uint32_t r0, uint32_t r1, ui
     return 0x3F3F3F3Fu | ((g << 1) & 0x80808080u);
 }
 
+// Merge the replicas of one spin word that `flags` selects (byte b = 1: replica b)
+// into a global snapshot word: the whole word when all four are selected.
+// Otherwise, with BYTES, a byte store per selected replica: the destination is
+// never read, so the snapshot does not wait on global memory (the
+// read-modify-write did, with every warp of the tile snapshotting after the same
+// barrier).  Tiles with one replica word per column (WT = 1) take it: all lanes
+// of a warp then hold the same four replicas and take the same branch.  With
+// several words per column neighbouring lanes hold different replicas, their
+// byte stores diverge, and the read-modify-write measured faster.
+template <bool BYTES>
+__device__ __forceinline__ void snapshot_word(uint32_t* dst, uint32_t v, uint32_t flags)
+{
+    if (flags == 0x01010101u) {
+        *dst = v;
+    } else if constexpr (BYTES) {
+        unsigned char* d = reinterpret_cast<unsigned char*>(dst);
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+            if ((flags >> (8 * b)) & 1u) d[b] = (unsigned char)(v >> (8 * b));
+    } else {
+        const uint32_t mask = flags * 0xFFu;
+        *dst = (*dst & ~mask) | (v & mask);
+    }
+}
+
 __device__ __forceinline__ float f32_cexp(float beta) { return -2.0f * beta * 1.4426950408889634f; }
 
 // F32 spin words: byte b is the top byte of the float +-1.0 of replica b

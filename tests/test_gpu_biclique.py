@@ -223,6 +223,21 @@ def test_tensor_full_size_sampled(pb, orc):
         assert abs(g["best_E"][r] - e) <= 1e-9 * abs(e)
 
 
+def test_tensor_largest_biclique(pb):
+    """n = 16384 per side, the largest biclique the library takes, on tensor cores with
+    300 replicas (a ragged replica tile): a ferromagnet (J = +1) at beta = 2 from random
+    starts reaches one of its two ground states, E0 = -n^2 (all spins aligned), within
+    the first two sweeps in every replica.  (Side A aligns with side B's majority; in
+    the rare replica whose random side B sums to 0, the second sweep aligns it.)"""
+    n, R, S = 16384, 300, 4
+    J = np.ones((n, n), np.int8)
+    sc = pb.make_schedule(pb.PB_SCHED_LINEAR, S, 2.0, 2.0)
+    g = _gpu(pb, n, J, None, sc, R, 5, "tensor")
+    assert np.all(g["best_E"] == -float(n) * n)
+    assert np.all(g["best_sweep"] <= 1)
+    assert np.all(np.abs(g["best_state"].astype(np.int64).sum(axis=1)) == 2 * n)
+
+
 def test_tensor_threshold_row_in_global_memory(pb, orc):
     """n = 4300 at small beta: the threshold row (2n + 1 entries) is larger than the
     shared-memory table region and its unsaturated window is wider than 256, so the

@@ -193,6 +193,24 @@ def test_pm1_fields_exact(pb, orc):
         assert np.array_equal(F[r].astype(np.float64), orc.fields(eu, ev, J.astype(float).reshape(-1), h.astype(float), m[r]))
 
 
+def test_largest_cube(pb, orc):
+    """L = 64, the largest cube the library takes (the resident form stops at L = 32, so
+    the library's own choice is the plain form), with 5 replicas (a ragged replica
+    word): +-1 bit-exact with the oracle; N(0, 1): the returned states' energies,
+    recomputed by the oracle in FP64, within 1e-9 relative."""
+    L, R, S = 64, 5, 3
+    J = syn.ea_couplings(L, "pm1", 21)
+    sc, ob = _sched(pb, orc, pb.PB_SCHED_LINEAR, S, 0.3, 2.0)
+    _assert_same(_gpu(pb, L, J, None, sc, R, 23, pb.PB_FORM_AUTO), _orc(orc, L, J, None, ob, R, 23))
+    Jg = syn.ea_couplings(L, "gauss", 25)
+    g = _gpu(pb, L, Jg, None, sc, R, 27, pb.PB_FORM_AUTO)
+    eu, ev, _ = orc.ea_graph(L)
+    for key_s, key_e in (("final_state", "final_E"), ("best_state", "best_E")):
+        for r in range(R):
+            e = orc.energy(eu, ev, Jg.astype(np.float64).reshape(-1), None, g[key_s][r])
+            assert abs(g[key_e][r] - e) <= 1e-9 * abs(e)
+
+
 @pytest.mark.parametrize("form", ["plain", "resident"])
 def test_f32_energies_fp64(pb, orc, form):
     L, R, S = 8, 16, 100
