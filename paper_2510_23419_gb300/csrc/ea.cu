@@ -402,7 +402,7 @@ __device__ void ea_tile(const EaJob& job, int tile, unsigned char* smem)
 // Every CTA lets a programmatically dependent launch (the other type's kernel
 // of the same batch) start at once, so that kernel's CTAs take the SMs this
 // one leaves as its list runs out.
-template <int JT>
+template <int K>
 __global__ void __launch_bounds__(kResidentThreads, 1)
     ea_resident_kernel(const EaJob* __restrict__ jobs, const EaWork* __restrict__ work, int n_work, int* counter)
 {
@@ -417,7 +417,7 @@ __global__ void __launch_bounds__(kResidentThreads, 1)
         if (item >= n_work) break;
         const EaWork wk = work[item];
         const EaJob& job = jobs[wk.job];
-        if constexpr (JT == PB_J_PM1_I8) {
+        if constexpr (K == kEaKernelPm1) {
             if (wk.path == kEaPathFieldsGeneric)
                 ea_tile<0, 0, PB_J_PM1_I8, true>(job, wk.tile, smem);
             else if (wk.path == kEaPathFast32)
@@ -426,20 +426,24 @@ __global__ void __launch_bounds__(kResidentThreads, 1)
                 ea_tile_fast<16, 4, PB_J_PM1_I8>(job, wk.tile, smem);
             else if (wk.path == kEaPathFast8)
                 ea_tile_fast<8, 16, PB_J_PM1_I8>(job, wk.tile, smem);
-            else if (wk.path == kEaPathGen24)  // compile-time shapes fold the index arithmetic
-                ea_tile<24, 1, PB_J_PM1_I8, false>(job, wk.tile, smem);
+            else if (wk.path == kEaPathFast24)
+                ea_tile_fast<24, 1, PB_J_PM1_I8>(job, wk.tile, smem);
             else if (wk.path == kEaPathGen12)
                 ea_tile<12, 4, PB_J_PM1_I8, false>(job, wk.tile, smem);
             else
                 ea_tile<0, 0, PB_J_PM1_I8, false>(job, wk.tile, smem);
         } else {
-            if (wk.path == kEaPathFast32)
+            // the compile-time L = 12 shape in either FP32 kernel makes it spill: its tiles
+            // run the generic tile, as do L = 24 tiles in the first kernel
+            if (K == kEaKernelF32 && wk.path == kEaPathFast32)
                 ea_tile_fast<32, 1, PB_J_F32>(job, wk.tile, smem);
+            else if (K == kEaKernelF32L24 && wk.path == kEaPathFast24)
+                ea_tile_fast<24, 1, PB_J_F32>(job, wk.tile, smem);
             else if (wk.path == kEaPathFast16)
                 ea_tile_fast<16, 4, PB_J_F32>(job, wk.tile, smem);
             else if (wk.path == kEaPathFast8)
                 ea_tile_fast<8, 16, PB_J_F32>(job, wk.tile, smem);
-            else  // also kEaPathGen24 / kEaPathGen12: compile-time shapes here would spill
+            else
                 ea_tile<0, 0, PB_J_F32, false>(job, wk.tile, smem);
         }
     }
@@ -850,26 +854,33 @@ int ea_resident_pick_wt(int L, int jtype, int has_h, int nF, int cap_words)
 // The limit is a property of the kernel, shared by every run of the process
 // on a device: it only grows, so preparing a run never lowers the limit that
 // another prepared run will launch with.
-cudaError_t ea_resident_set_smem(int jtype, size_t smem)
+template <int K>
+static cudaError_t ea_resident_attr(size_t smem)
+{
+    return cudaFuncSetAttribute(ea_resident_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t ea_resident_set_smem(int kernel, size_t smem)
 {
     static std::mutex mu;
-    static size_t current[2][64] = {};
+    static size_t current[kEaKernels][64] = {};
+    if (kernel < 0 || kernel >= kEaKernels) return cudaErrorInvalidValue;
     int dev = 0;
     cudaGetDevice(&dev);
-    const int t = jtype == PB_J_F32 ? 1 : 0;
     std::lock_guard<std::mutex> lock(mu);
-    size_t* cur = (dev >= 0 && dev < 64) ? &current[t][dev] : nullptr;
+    size_t* cur = (dev >= 0 && dev < 64) ? &current[kernel][dev] : nullptr;
     if (cur && smem <= *cur) return cudaSuccess;
-    const cudaError_t e =
-        t ? cudaFuncSetAttribute(ea_resident_kernel<PB_J_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-          : cudaFuncSetAttribute(ea_resident_kernel<PB_J_PM1_I8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const cudaError_t e = kernel == kEaKernelPm1   ? ea_resident_attr<kEaKernelPm1>(smem)
+                          : kernel == kEaKernelF32 ? ea_resident_attr<kEaKernelF32>(smem)
+                                                   : ea_resident_attr<kEaKernelF32L24>(smem);
     if (e == cudaSuccess && cur) *cur = smem;
     return e;
 }
 
-cudaError_t ea_launch_resident(int jtype, const EaJob* d_jobs, const EaWork* d_work, int n_work, int* d_counter,
+cudaError_t ea_launch_resident(int kernel, const EaJob* d_jobs, const EaWork* d_work, int n_work, int* d_counter,
                                size_t smem, int grid, bool after_previous, cudaStream_t st)
 {
+    if (kernel < 0 || kernel >= kEaKernels) return cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3(kResidentThreads);
@@ -882,9 +893,11 @@ cudaError_t ea_launch_resident(int jtype, const EaJob* d_jobs, const EaWork* d_w
         cfg.attrs = attr;
         cfg.numAttrs = 1;
     }
-    return jtype == PB_J_F32 ? cudaLaunchKernelEx(&cfg, ea_resident_kernel<PB_J_F32>, d_jobs, d_work, n_work, d_counter)
-                             : cudaLaunchKernelEx(&cfg, ea_resident_kernel<PB_J_PM1_I8>, d_jobs, d_work, n_work,
-                                                  d_counter);
+    if (kernel == kEaKernelPm1)
+        return cudaLaunchKernelEx(&cfg, ea_resident_kernel<kEaKernelPm1>, d_jobs, d_work, n_work, d_counter);
+    if (kernel == kEaKernelF32)
+        return cudaLaunchKernelEx(&cfg, ea_resident_kernel<kEaKernelF32>, d_jobs, d_work, n_work, d_counter);
+    return cudaLaunchKernelEx(&cfg, ea_resident_kernel<kEaKernelF32L24>, d_jobs, d_work, n_work, d_counter);
 }
 
 cudaError_t ea_launch_philox_ceiling(uint64_t seed, int sweeps, int blocks, uint32_t* sink, cudaStream_t st)

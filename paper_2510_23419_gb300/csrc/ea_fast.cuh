@@ -5,6 +5,10 @@
 // both colours, i.e. the sites x = 2q + parity, fixed y, every other z, for 4
 // replicas.
 //
+// Shapes whose columns fill fewer than half the CTA (L = 24: 288 column-words,
+// 576 of the 1024 threads) leave the remaining warps without sites: they take
+// part in the barriers and add zero energy partials.
+//
 // Same arithmetic, random words and outputs as the generic tile; what changes
 // is only the instruction budget:
 //  * x and y neighbours (and their periodic wrap) are per-thread bases, the
@@ -76,11 +80,13 @@ constexpr int kResidentWarps = kResidentThreads / 32;
 template <int L, int WT, int JT>
 struct EaFastTile {
     static constexpr int T = kResidentThreads;
-    static constexpr int CWN = kResidentThreads / 2;  // column-words: two threads (z parities) per column
     static constexpr int h2 = L / 2;
+    static constexpr int CWN = h2 * L * WT;  // column-words: two threads (z parities) per column
+    static constexpr int TB = 2 * CWN;       // threads with sites; the others only join the barriers
+    static constexpr bool kAllBusy = TB == kResidentThreads;
     static constexpr int half = h2 * L * L;
     static constexpr int N = 2 * half;
-    static_assert(h2 * L * WT == CWN, "fast tile: one column-word per thread pair");
+    static_assert(TB <= T && TB % 32 == 0 && L % 8 == 0, "fast tile: whole warps of column-word pairs");
     static constexpr int SZ = L * h2 * WT;  // words between z planes of a class array
     static constexpr int CLS = half * WT;   // words of one class array
     static constexpr int NREP = 4 * WT;
@@ -89,6 +95,7 @@ struct EaFastTile {
 
     const EaJob& job;
     int tile, t, lane, warp, w, q, y, zp, base0, oyp, oym;
+    bool busy;  // the thread owns a column-word (always, when the columns fill the CTA)
     uint32_t tq;
     uint32_t* sp;
     int32_t* spart_i;
@@ -104,6 +111,7 @@ struct EaFastTile {
         t = threadIdx.x;
         lane = t & 31;
         warp = t >> 5;
+        busy = kAllBusy || t < TB;
         const int cw = t % CWN;
         zp = t / CWN;
         w = cw % WT;
@@ -120,7 +128,7 @@ struct EaFastTile {
         oym = ((y == 0) ? (L - 1) * h2 : -h2) * WT;
         uint32_t* jw = reinterpret_cast<uint32_t*>(sflag + 128);
         sjb4 = jw;
-        if constexpr (PM1) {
+        if (PM1 && (kAllBusy || busy)) {
 #pragma unroll 1
             for (int c = 0; c < 2; ++c)
 #pragma unroll 1
@@ -138,6 +146,8 @@ struct EaFastTile {
 
     __device__ __forceinline__ void init_state()
     {
+        if constexpr (!kAllBusy)
+            if (!busy) return;
         if (job.resume) {  // resumed run: the given state, in the tile layout of final_words
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
@@ -172,6 +182,8 @@ struct EaFastTile {
     template <int C, bool DECIDE>
     __device__ __forceinline__ void half_sweep(int s, uint32_t& uacc, float (&ef)[4])
     {
+        if constexpr (!kAllBusy)
+            if (!busy) return;
         const uint32_t* o = sp + (1 - C) * CLS;
         uint32_t* own = sp + C * CLS;
         const int zp = this->zp;
@@ -321,7 +333,7 @@ struct EaFastTile {
     // that `flags` selects (byte b = 1: replica 4w + b; 0x01010101: all four)
     __device__ __forceinline__ void store_words(uint32_t* gdst, uint32_t flags) const
     {
-        if (flags == 0u) return;
+        if (flags == 0u || (!kAllBusy && !busy)) return;
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
             uint32_t* dst = gdst + ((size_t)tile * 2 + c) * CLS + base0;
@@ -417,10 +429,11 @@ __device__ __forceinline__ void ea_tile_fast(const EaJob& job, int tile, unsigne
     tl.run();
 }
 
-// Fast-tile shapes: (L, WT) with (L/2) L WT == kResidentThreads / 2.
+// Fast-tile shapes: (L, WT) with (L/2) L WT == kResidentThreads / 2, and L = 24,
+// WT = 1 (its 288 column-words fill 576 of the threads).
 __host__ __device__ constexpr bool ea_fast_shape(int L, int WT)
 {
-    return (L == 32 && WT == 1) || (L == 16 && WT == 4) || (L == 8 && WT == 16);
+    return (L == 32 && WT == 1) || (L == 16 && WT == 4) || (L == 8 && WT == 16) || (L == 24 && WT == 1);
 }
 
 }  // namespace pb

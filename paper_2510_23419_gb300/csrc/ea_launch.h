@@ -45,8 +45,9 @@ enum EaTilePath : int32_t {
     kEaPathFast16 = 2,         // L = 16, WT = 4
     kEaPathFast8 = 3,          // L = 8, WT = 16
     kEaPathGeneric = 4,        // any other even L <= 32
-    kEaPathGen24 = 5,          // generic tile with compile-time L = 24, WT = 1 (+-1 kernel; FP32: generic)
+    kEaPathGen24 = 5,          // (unused: L = 24, WT = 1 takes the compile-time tile kEaPathFast24)
     kEaPathGen12 = 6,          // generic tile with compile-time L = 12, WT = 4 (+-1 kernel; FP32: generic)
+    kEaPathFast24 = 7,         // compile-time tile L = 24, WT = 1 (576 of the CTA's threads hold sites)
 };
 
 struct EaWork {
@@ -61,10 +62,19 @@ inline int32_t ea_tile_path(const EaJob& j)
     if (j.inst.L == 32 && j.WT == 1) return kEaPathFast32;
     if (j.inst.L == 16 && j.WT == 4) return kEaPathFast16;
     if (j.inst.L == 8 && j.WT == 16) return kEaPathFast8;
-    if (j.inst.L == 24 && j.WT == 1) return kEaPathGen24;
+    if (j.inst.L == 24 && j.WT == 1) return kEaPathFast24;
     if (j.inst.L == 12 && j.WT == 4) return kEaPathGen12;
     return kEaPathGeneric;
 }
+
+// Persistent resident kernels: one for +-1 couplings and two for FP32, which
+// differ in their compile-time tiles -- the L = 32 tile, or the L = 24 tile,
+// beside L = 16, L = 8 and the runtime-shaped generic tile.  With both the
+// L = 32 and the L = 24 tile in one kernel, the register allocation they share
+// slowed the L = 32 tile by 8%.  A batch takes the L = 24 kernel when its FP32
+// tiles include L = 24 ones and no L = 32 ones; otherwise L = 24 FP32 tiles
+// run the generic tile of the first kernel.
+enum EaKernel : int32_t { kEaKernelPm1 = 0, kEaKernelF32 = 1, kEaKernelF32L24 = 2, kEaKernels = 3 };
 
 // Shared memory of one resident tile, in bytes.
 __host__ __device__ inline size_t ea_resident_smem(int L, int WT, int jtype, int has_h, int nF)
@@ -81,7 +91,8 @@ __host__ __device__ inline size_t ea_resident_smem(int L, int WT, int jtype, int
     if (jtype == PB_J_PM1_I8 && has_h) b += (size_t)(1024 / 32) * 4 * WT * 4;  // per-warp h.m partials
     b += (size_t)4 * WT;                                 // improved flags
     // compile-time-shaped tiles keep their bond bytes as [2][L/8][threads] words
-    const bool fast = !has_h && ((L == 32 && WT == 1) || (L == 16 && WT == 4) || (L == 8 && WT == 16));
+    const bool fast =
+        !has_h && ((L == 32 && WT == 1) || (L == 16 && WT == 4) || (L == 8 && WT == 16) || (L == 24 && WT == 1));
     if (fast && jtype == PB_J_PM1_I8) {
         const size_t f = N * (size_t)WT * 4 + (size_t)(1024 / 32) * 4 * WT * 4 + 128 + (size_t)2 * (L / 8) * 1024 * 4;
         if (f > b) b = f;
@@ -99,14 +110,14 @@ constexpr size_t kResidentSmemLimit = 227 * 1024;
 // z parity, per column) and the tile fits shared memory; 0 if none.
 int ea_resident_pick_wt(int L, int jtype, int has_h, int nF, int cap_words);
 
-// Opt the persistent kernel of coupling type `jtype` into `smem` bytes of
-// dynamic shared memory (outside any capture).
-cudaError_t ea_resident_set_smem(int jtype, size_t smem);
-// Persistent kernel of coupling type `jtype` over n_work items (all of that
-// type).  after_previous: programmatic dependent launch on the kernel launched
+// Opt the persistent kernel `kernel` (EaKernel) into `smem` bytes of dynamic
+// shared memory (outside any capture).
+cudaError_t ea_resident_set_smem(int kernel, size_t smem);
+// Persistent kernel `kernel` (EaKernel) over n_work items of its coupling
+// type.  after_previous: programmatic dependent launch on the kernel launched
 // just before it on `st` (its CTAs start as that kernel's CTAs leave; the
 // caller orders any later consumer after both).
-cudaError_t ea_launch_resident(int jtype, const EaJob* d_jobs, const EaWork* d_work, int n_work, int* d_counter,
+cudaError_t ea_launch_resident(int kernel, const EaJob* d_jobs, const EaWork* d_work, int n_work, int* d_counter,
                                size_t smem, int grid, bool after_previous, cudaStream_t st);
 // Random-word ceiling: `blocks` CTAs of kResidentThreads threads, each thread drawing the
 // decision words of 32 sites (one L = 32 column, both colours) per sweep; sink holds

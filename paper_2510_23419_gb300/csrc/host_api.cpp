@@ -408,11 +408,19 @@ pb_status ea_batch_setup(std::vector<pb_run*>& runs, cudaStream_t st, std::share
     std::vector<EaJob> jobs;
     std::vector<TileCost> tiles[2];
     EaGroup grp[2];
+    // FP32 kernel: the one with the L = 24 tile if the batch has L = 24 FP32 tiles and no L = 32 ones
+    bool f32_l24 = false, f32_l32 = false;
+    for (const pb_run* r : runs) {
+        if (r->job.inst.jtype != PB_J_F32) continue;
+        f32_l24 |= ea_tile_path(r->job) == kEaPathFast24;
+        f32_l32 |= ea_tile_path(r->job) == kEaPathFast32;
+    }
+    grp[0].kernel = kEaKernelPm1;
+    grp[1].kernel = f32_l24 && !f32_l32 ? kEaKernelF32L24 : kEaKernelF32;
     for (size_t q = 0; q < runs.size(); ++q) {
         const EaJob& j = runs[q]->job;
         jobs.push_back(j);
         const int t = j.inst.jtype == PB_J_F32 ? 1 : 0;
-        grp[t].jtype = j.inst.jtype;
         grp[t].smem = std::max(grp[t].smem, ea_resident_smem(j.inst.L, j.WT, j.inst.jtype, j.inst.has_h, j.nF));
         const double per = (double)j.inst.N * 4.0 * j.WT * std::max(1, j.S) * (t ? 1.8 : 1.0);
         for (int k = 0; k < j.n_tiles; ++k) tiles[t].push_back({(int)q, k, per});
@@ -444,7 +452,7 @@ pb_status ea_batch_setup(std::vector<pb_run*>& runs, cudaStream_t st, std::share
     PB_CUDA_TRY(cudaMemcpyAsync(shared->work.p, work.data(), work.size() * sizeof(EaWork), cudaMemcpyHostToDevice, st));
     PB_CUDA_TRY(cudaStreamSynchronize(st));
     shared->n_work = (int)work.size();
-    for (const EaGroup& g : shared->groups) PB_CUDA_TRY(ea_resident_set_smem(g.jtype, g.smem));
+    for (const EaGroup& g : shared->groups) PB_CUDA_TRY(ea_resident_set_smem(g.kernel, g.smem));
     out = shared;
     return PB_OK;
 }
@@ -484,7 +492,7 @@ pb_status ea_batch_launch(std::vector<pb_run*>& runs, const std::shared_ptr<Batc
         PB_CUDA_TRY(cudaEventRecordWithFlags(shared->ev_k0, st, evf));
         for (size_t k = 0; k < shared->groups.size(); ++k) {
             const EaGroup& g = shared->groups[k];
-            PB_CUDA_TRY(ea_launch_resident(g.jtype, shared->jobs.as<EaJob>(), shared->work.as<EaWork>() + g.offset, g.n,
+            PB_CUDA_TRY(ea_launch_resident(g.kernel, shared->jobs.as<EaJob>(), shared->work.as<EaWork>() + g.offset, g.n,
                                            shared->counter.as<int>() + k, g.smem, g.grid, capture && k > 0, st));
             if (capture) PB_CUDA_TRY(cudaEventRecord(shared->ev_group[k], st));
         }

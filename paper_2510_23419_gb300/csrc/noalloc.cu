@@ -185,8 +185,8 @@ extern "C" pb_status pb_anneal_ea_noalloc(int32_t L, const int8_t* J_dev, const 
     PB_CUDA_TRY(cudaGetLastError());
 
     const size_t smem = ea_resident_smem(L, WT, PB_J_PM1_I8, 0, nF);
-    PB_CUDA_TRY(ea_resident_set_smem(PB_J_PM1_I8, smem));
-    PB_CUDA_TRY(ea_launch_resident(PB_J_PM1_I8, reinterpret_cast<const EaJob*>(S + o_job),
+    PB_CUDA_TRY(ea_resident_set_smem(kEaKernelPm1, smem));
+    PB_CUDA_TRY(ea_launch_resident(kEaKernelPm1, reinterpret_cast<const EaJob*>(S + o_job),
                                    reinterpret_cast<const EaWork*>(S + o_work), n_tiles, reinterpret_cast<int*>(S + o_ctr),
                                    smem, std::min(n_tiles, sms), false, st));
     PB_CUDA_TRY(ea_launch_readout(j, j.final_words, final_states_dev, final_E_dev, st));

@@ -94,9 +94,9 @@ struct pb_instance {
 
 namespace pb {
 // Tiles of one coupling type in a shared EA launch: work[offset, offset + n),
-// counter word `group`, one persistent kernel of `grid` CTAs.
+// the group's own counter word, one persistent kernel (EaKernel) of `grid` CTAs.
 struct EaGroup {
-    int jtype = 0, offset = 0, n = 0, grid = 0;
+    int kernel = 0, offset = 0, n = 0, grid = 0;
     size_t smem = 0;
     double cost = 0.0, longest = 0.0;  // estimated SM-time of all tiles / of the longest tile
 };

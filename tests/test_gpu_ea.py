@@ -81,6 +81,7 @@ CASES = [
     (12, 70, 5, 1, 0.1, 5.0, 1, 0, 8),
     (16, 40, 12, 1, 0.1, 5.0, 1, 0, 9),
     (32, 8, 4, 0, 0.3, 0.9, 1, 0, 10),
+    (24, 13, 6, 1, 0.1, 3.0, 1, 0, 14),   # compile-time L = 24 tile (576 of the CTA's threads), ragged replicas
     (4, 8, 30, 0, 0.1, 3.0, 1, 2, 11),
     (6, 6, 20, 0, 0.05, 2.0, 2, 5, 12),
     (8, 12, 15, 1, 0.1, 5.0, 1, 64, 13),
@@ -191,6 +192,34 @@ def test_pm1_fields_exact(pb, orc):
     eu, ev, _ = orc.ea_graph(L)
     for r in range(3):
         assert np.array_equal(F[r].astype(np.float64), orc.fields(eu, ev, J.astype(float).reshape(-1), h.astype(float), m[r]))
+
+
+def test_l24_tile_and_generic_tile_agree(pb):
+    """An FP32 L = 24 job runs the compile-time L = 24 tile alone, and the generic tile
+    in a batch with an FP32 L = 32 job (whose kernel holds the L = 32 tile instead):
+    the same arithmetic and random words, so bit-identical states, energies and best
+    sweeps either way."""
+    L, R, S, seed = 24, 12, 30, 33
+    J = syn.ea_couplings(L, "gauss", 31)
+    sc = pb.make_schedule(pb.PB_SCHED_GEOMETRIC, S, 0.1, 5.0)
+    alone = _gpu(pb, L, J, None, sc, R, seed, pb.PB_FORM_RESIDENT)
+    J32 = syn.ea_couplings(32, "gauss", 35)
+    insts = [pb.pb_create_instance(pb.PB_TOPO_EA3D, J, None, L=L), pb.pb_create_instance(pb.PB_TOPO_EA3D, J32, None, L=32)]
+    import torch
+    side = torch.cuda.Stream()
+    runs = pb.pb_anneal_batch(insts, [sc, pb.make_schedule(pb.PB_SCHED_GEOMETRIC, 5, 0.1, 5.0)], [R, 4], [seed, 37],
+                              stream=side)
+    try:
+        fe, be, bs = pb.pb_energy(runs[0], R)
+        assert np.array_equal(pb.pb_final_states(runs[0], R, L ** 3), alone["final_state"])
+        assert np.array_equal(pb.pb_best_states(runs[0], R, L ** 3), alone["best_state"])
+        assert np.array_equal(fe, alone["final_E"]) and np.array_equal(be, alone["best_E"])
+        assert np.array_equal(bs, alone["best_sweep"])
+    finally:
+        for r in runs:
+            pb.pb_run_destroy(r)
+        for i in insts:
+            pb.pb_instance_destroy(i)
 
 
 def test_largest_cube(pb, orc):
