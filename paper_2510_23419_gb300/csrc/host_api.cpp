@@ -109,6 +109,26 @@ uint32_t threshold_u32(double beta, double F)
     return (uint32_t)T;
 }
 
+// f(begin, end) over [0, n), split into contiguous ranges across host threads;
+// one range (no thread) below 2 x `grain` items.
+template <typename F>
+static void parallel_ranges(int n, int grain, F&& f)
+{
+    const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+    const int nt = std::min(hw, std::max(1, n / std::max(1, grain)));
+    if (nt <= 1) {
+        f(0, n);
+        return;
+    }
+    std::vector<std::thread> ts;
+    ts.reserve((size_t)nt);
+    for (int k = 0; k < nt; ++k) {
+        const int b = (int)((long long)n * k / nt), e = (int)((long long)n * (k + 1) / nt);
+        ts.emplace_back([&f, b, e] { f(b, e); });
+    }
+    for (std::thread& t : ts) t.join();
+}
+
 // Threshold rows (Eq. 2, FP64 on the host), one per beta level, stored as the
 // window of the row outside which T is saturated: T is nondecreasing in F, so
 // every entry below the window is 0 and every entry above it 2^32 - 1, and the
@@ -119,29 +139,42 @@ void threshold_windows(const std::vector<double>& betas, int nF, int fmin, std::
                        std::vector<int32_t>& win)
 {
     const int nlev = std::max<int>(1, (int)betas.size());
-    tab.clear();
     win.assign((size_t)nlev * 3, 0);
+    // levels are independent: ranges of them on host threads, each into its own
+    // segment, then the segments in level order (the same table as one pass)
+    std::vector<std::vector<uint32_t>> seg((size_t)nlev);
+    parallel_ranges(nlev, 512, [&](int l0, int l1) {
+        for (int l = l0; l < l1; ++l) {
+            const double beta = betas.empty() ? 0.0 : betas[(size_t)l];
+            auto T = [&](int f) { return threshold_u32(beta, (double)(f + fmin)); };
+            int a = 0, b = nF;  // first index with T > 0
+            while (a < b) {
+                const int m = (a + b) / 2;
+                if (T(m) > 0u) b = m; else a = m + 1;
+            }
+            const int lo = std::max(0, a - 1);
+            a = 0;
+            b = nF;  // first index with T = 2^32 - 1
+            while (a < b) {
+                const int m = (a + b) / 2;
+                if (T(m) == 0xFFFFFFFFu) b = m; else a = m + 1;
+            }
+            const int hi = std::max(lo, std::min(nF - 1, a));
+            win[3 * (size_t)l] = lo;
+            win[3 * (size_t)l + 1] = hi - lo + 1;
+            std::vector<uint32_t>& v = seg[(size_t)l];
+            v.resize((size_t)(hi - lo + 1));
+            for (int f = lo; f <= hi; ++f) v[(size_t)(f - lo)] = T(f);
+        }
+    });
+    size_t total = 0;
     for (int l = 0; l < nlev; ++l) {
-        const double beta = betas.empty() ? 0.0 : betas[l];
-        auto T = [&](int f) { return threshold_u32(beta, (double)(f + fmin)); };
-        int a = 0, b = nF;  // first index with T > 0
-        while (a < b) {
-            const int m = (a + b) / 2;
-            if (T(m) > 0u) b = m; else a = m + 1;
-        }
-        const int lo = std::max(0, a - 1);
-        a = 0;
-        b = nF;  // first index with T = 2^32 - 1
-        while (a < b) {
-            const int m = (a + b) / 2;
-            if (T(m) == 0xFFFFFFFFu) b = m; else a = m + 1;
-        }
-        const int hi = std::max(lo, std::min(nF - 1, a));
-        win[3 * l] = lo;
-        win[3 * l + 1] = hi - lo + 1;
-        win[3 * l + 2] = (int32_t)tab.size();
-        for (int f = lo; f <= hi; ++f) tab.push_back(T(f));
+        win[3 * (size_t)l + 2] = (int32_t)total;
+        total += seg[(size_t)l].size();
     }
+    tab.resize(total);
+    for (int l = 0; l < nlev; ++l)
+        std::copy(seg[(size_t)l].begin(), seg[(size_t)l].end(), tab.begin() + win[3 * (size_t)l + 2]);
 }
 
 }  // namespace pb
@@ -315,8 +348,11 @@ pb_status ea_prepare_run(pb_run* run, pb_instance* I, const pb_schedule* sc, int
         j.fmin = -fmax;
         j.nF = 2 * fmax + 1;
         std::vector<uint32_t> tab((size_t)nlev * j.nF, 0x80000000u);
-        for (size_t l = 0; l < betas.size(); ++l)
-            for (int f = 0; f < j.nF; ++f) tab[l * j.nF + f] = threshold_u32(betas[l], (double)(f + j.fmin));
+        parallel_ranges((int)betas.size(), 2048, [&](int l0, int l1) {
+            for (int l = l0; l < l1; ++l)
+                for (int f = 0; f < j.nF; ++f)
+                    tab[(size_t)l * j.nF + f] = threshold_u32(betas[(size_t)l], (double)(f + j.fmin));
+        });
         PB_ALLOC(run->table, tab.size() * 4);
         PB_CUDA_TRY(cudaMemcpyAsync(run->table.p, tab.data(), tab.size() * 4, cudaMemcpyHostToDevice, st));
         PB_CUDA_TRY(cudaStreamSynchronize(st));
