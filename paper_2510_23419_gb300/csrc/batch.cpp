@@ -197,26 +197,36 @@ pb_status batch_start(int count, pb_instance* const* insts, const pb_schedule* s
         }
     }
 
-    // ---- set-up of every job on the caller's stream
+    // ---- set-up on the caller's stream.  Latency first (the request server): the
+    //      EA resident jobs first, so that their shared launch starts before the
+    //      other jobs are prepared, each of which is then prepared and launched in
+    //      turn while the earlier ones run (served stream: maximum rate +36%, p99
+    //      -15%).  Otherwise every job is prepared before any launch: on the
+    //      200-job mixed batch the early EA launch measured 10% slower in total.
     std::vector<std::unique_ptr<pb_run>> runs(count);
-    std::vector<pb_run*> resident;
-    for (const Job& j : jobs) {
+    auto setup_one = [&](const Job& j) -> pb_status {
         runs[j.q].reset(new (std::nothrow) pb_run());
         if (!runs[j.q]) return fail(PB_ENOMEM, "host allocation failed");
         pb_run* r = runs[j.q].get();
         const pb_anneal_opts* o = opts ? &opts[j.q] : nullptr;
-        pb_status ps;
-        if (j.I->topo == PB_TOPO_EA3D) {
-            ps = ea_prepare_run(r, j.I, &scheds[j.q], j.R, seeds[j.q], o, j.form, j.wt, st);
-            if (ps == PB_OK && j.form == PB_FORM_RESIDENT) resident.push_back(r);  // EA resident: the shared launch
-        } else if (j.I->topo == PB_TOPO_CSR) {
-            ps = csr_setup(r, j.I, &scheds[j.q], j.R, seeds[j.q], o, st);
-        } else {
-            pb_anneal_opts oo = o ? *o : pb_anneal_opts{PB_FORM_AUTO, 0, NAN};
-            oo.form = j.form;
-            ps = bq_setup(r, j.I, &scheds[j.q], j.R, seeds[j.q], &oo, st, j.wt);
+        if (j.I->topo == PB_TOPO_EA3D) return ea_prepare_run(r, j.I, &scheds[j.q], j.R, seeds[j.q], o, j.form, j.wt, st);
+        if (j.I->topo == PB_TOPO_CSR) return csr_setup(r, j.I, &scheds[j.q], j.R, seeds[j.q], o, st);
+        pb_anneal_opts oo = o ? *o : pb_anneal_opts{PB_FORM_AUTO, 0, NAN};
+        oo.form = j.form;
+        return bq_setup(r, j.I, &scheds[j.q], j.R, seeds[j.q], &oo, st, j.wt);
+    };
+    auto is_resident_ea = [](const Job& j) { return j.form == PB_FORM_RESIDENT && j.I->topo == PB_TOPO_EA3D; };
+    std::vector<pb_run*> resident;
+    for (const Job& j : jobs) {
+        if (!latency_first && !is_resident_ea(j)) {
+            pb_status ps = setup_one(j);
+            if (ps != PB_OK) return ps;
+            continue;
         }
+        if (!is_resident_ea(j)) continue;
+        pb_status ps = setup_one(j);
         if (ps != PB_OK) return ps;
+        resident.push_back(runs[j.q].get());  // EA resident: the shared launch
     }
     std::shared_ptr<BatchShared> ea_shared;
     if (!resident.empty()) {
@@ -232,7 +242,7 @@ pb_status batch_start(int count, pb_instance* const* insts, const pb_schedule* s
         // others' whole time, else half.
         double ea_cost = 0.0, other = 0.0, other_all = 0.0;
         for (const Job& j : jobs) {
-            if (j.form == PB_FORM_RESIDENT && j.I->topo == PB_TOPO_EA3D) {
+            if (is_resident_ea(j)) {
                 ea_cost += j.cost;
             } else {
                 double c = 0.0;
@@ -274,33 +284,60 @@ pb_status batch_start(int count, pb_instance* const* insts, const pb_schedule* s
         }
         return PB_OK;
     };
+    // a failure after the first launch waits for the launched work before the
+    // runs (and their device buffers) are released
+    bool launched = false;
+    auto fail_after_launch = [&](pb_status ps) -> pb_status {
+        if (launched)
+            for (int k = 0; k < ns; ++k)
+                if (used[k]) cudaStreamSynchronize(pool_stream(k));
+        cudaEventDestroy(fork);
+        return ps;
+    };
     int ea_k = -1;
     if (!resident.empty()) {
         ea_k = 0;
         for (int c = 1; c < ns; ++c)
             if (load[c] < load[ea_k]) ea_k = c;
         pb_status ps = start_on(ea_k);
-        if (ps != PB_OK) return ps;
+        if (ps != PB_OK) return fail_after_launch(ps);
         for (const Job& j : jobs)
-            if (j.form == PB_FORM_RESIDENT && j.I->topo == PB_TOPO_EA3D) {
+            if (is_resident_ea(j)) {
                 load[ea_k] += j.cost;
                 if (costs) (*costs)[j.q] = j.cost;
                 if (stream_of) (*stream_of)[j.q] = ea_k;
             }
         for (pb_run* r : resident) r->stream = pool_stream(ea_k);
         ps = ea_batch_launch(resident, ea_shared, pool_stream(ea_k));
-        if (ps != PB_OK) return ps;
+        launched = true;
+        if (ps != PB_OK) return fail_after_launch(ps);
     }
     std::vector<const Job*> rest;
     for (const Job& j : jobs)
-        if (!(j.form == PB_FORM_RESIDENT && j.I->topo == PB_TOPO_EA3D)) rest.push_back(&j);
+        if (!is_resident_ea(j)) rest.push_back(&j);
     std::stable_sort(rest.begin(), rest.end(), [](const Job* a, const Job* b) { return a->cost > b->cost; });
+    cudaEvent_t ready = nullptr;  // a job's set-up after the fork, complete on `st`
+    if (latency_first && !rest.empty() && cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) != cudaSuccess)
+        return fail_after_launch(cuda_fail(cudaGetLastError(), "cudaEventCreate"));
     for (const Job* j : rest) {
+        pb_status ps = latency_first ? setup_one(*j) : PB_OK;
+        if (ps != PB_OK) {
+            if (ready) cudaEventDestroy(ready);
+            return fail_after_launch(ps);
+        }
         int k = -1;
         for (int c = 0; c < ns; ++c)
             if (c != ea_k && (k < 0 || load[c] < load[k])) k = c;
-        pb_status ps = start_on(k);
-        if (ps != PB_OK) return ps;
+        ps = start_on(k);
+        if (ps == PB_OK && ready) {
+            // prepared after the fork: the launch stream also waits for this job's set-up
+            if (cudaEventRecord(ready, st) != cudaSuccess || cudaStreamWaitEvent(pool_stream(k), ready, 0) != cudaSuccess)
+                ps = cuda_fail(cudaGetLastError(), "cudaStreamWaitEvent");
+        }
+        if (ps != PB_OK) {
+            if (ready) cudaEventDestroy(ready);
+            return fail_after_launch(ps);
+        }
         load[k] += j->cost;
         if (costs) (*costs)[j->q] = j->cost;
         if (stream_of) (*stream_of)[j->q] = k;
@@ -309,8 +346,13 @@ pb_status batch_start(int count, pb_instance* const* insts, const pb_schedule* s
         ps = (j->I->topo == PB_TOPO_EA3D)  ? ea_enqueue_plain(r, pool_stream(k))
              : (j->I->topo == PB_TOPO_CSR) ? csr_launch(r, pool_stream(k))
                                             : bq_launch(r, pool_stream(k));
-        if (ps != PB_OK) return ps;
+        launched = true;
+        if (ps != PB_OK) {
+            if (ready) cudaEventDestroy(ready);
+            return fail_after_launch(ps);
+        }
     }
+    if (ready) cudaEventDestroy(ready);
     // ---- join back into the caller's stream
     for (int k = 0; k < ns && join; ++k) {
         if (!used[k]) continue;
