@@ -244,6 +244,10 @@ __device__ __forceinline__ void bq_copy_flagged(const BqJob& job, int r0, const 
 __global__ void __launch_bounds__(256) bq_sweep_end_kernel(BqJob job, int s_arg, int init, const int32_t* sp_read,
                                                           int32_t* sp_write)
 {
+    // a programmatic dependent of the half-sweep before it in tensor-form runs that
+    // set BqJob::pdl (otherwise both instructions do nothing)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int s = sp_read ? *sp_read : s_arg;
     // read by the next sweep's launches; a max, because in stop mode the block that sees the
     // last replica reach the target raises it to S
@@ -528,8 +532,18 @@ cudaError_t bq_launch_cc_half(const BqJob& job, int side, int s, const int32_t* 
 cudaError_t bq_launch_sweep_end(const BqJob& job, int s, int init, const int32_t* sp_read, int32_t* sp_write,
                                 cudaStream_t st)
 {
-    bq_sweep_end_kernel<<<job.Rpad / kEndReps, 256, 0, st>>>(job, s, init, sp_read, sp_write);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(job.Rpad / kEndReps));
+    cfg.blockDim = dim3(256);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    if (job.pdl && sp_read) {  // inside a tensor-form sweep loop: a programmatic dependent of its half-sweep
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+    }
+    return cudaLaunchKernelEx(&cfg, bq_sweep_end_kernel, job, s, init, sp_read, sp_write);
 }
 
 cudaError_t bq_launch_best_flush(const BqJob& job, cudaStream_t st)

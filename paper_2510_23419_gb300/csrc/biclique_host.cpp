@@ -296,6 +296,12 @@ static pb_status bq_prepare(pb_run* run, pb_instance* I, const pb_schedule* sc, 
                                            (uint64_t)j.Rpad, (uint64_t)j.ld * esz,
                                            kBqTcReps / 2));  // half a tile per cluster CTA
         PB_CUDA_TRY(bq_tc_set_smem());
+        // Runs whose half-sweeps fill every cluster chain their sweep loop's launches
+        // by programmatic dependent launch (the next launch's CTAs take the SMs as the
+        // previous one's leave).  Smaller runs, typical of batches and the request
+        // server, keep whole-kernel ordering: there, CTAs waiting for their
+        // predecessor would hold SMs other jobs could use.
+        j.pdl = bq_tc_fills_device(n, j.Rpad, pm1 ? 0 : 1) ? 1 : 0;
     }
     if (resident) {
         run->res_smem = bq_res_smem_bytes(I->jtype, n, pm1 ? run->res_tab : 0);

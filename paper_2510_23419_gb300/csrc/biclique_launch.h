@@ -57,6 +57,8 @@ struct BqJob {
     const int32_t* win;     // PM1 [levels][3]: threshold window (lo, width, off) of each beta level
     int32_t tabmode;        // tensor form: where the decisions read the windows (widest level decides)
     int32_t tile_split;     // tensor form: 1 = a sparse last round of tiles is split into 128-replica tiles
+    int32_t pdl;            // tensor form: the sweep loop's launches are programmatic dependents of the one
+                            // before (set for runs whose half-sweep fills every cluster)
     uint64_t wait_ns;       // tensor form: limit of every device-side wait (ns of the global timer)
     int32_t stall_loads;    // tensor form, failure-path tests only: the load warp issues no loads
 };

@@ -329,6 +329,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                       const __grid_constant__ CUtensorMap tmB, BqJob job, int side, int s_arg, const int32_t* sp,
                       int decide, float* fields_out, int* err)
 {
+    // Launched as a programmatic dependent of the sweep loop's previous kernel: wait
+    // for it (its spins, partials and sweep counter) before reading anything it
+    // writes, and let the next launch start its CTAs as this one's leave.  Without
+    // such a dependency both instructions do nothing.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int s = sp ? *sp : s_arg;
     if (decide && s >= job.S) return;  // uniform over the grid: before any barrier or allocation
     TabWindow win{0, 0, 1};
@@ -758,15 +764,31 @@ cudaError_t bq_launch_tc_half(const BqTcMaps& maps, int bsel, const BqJob& job, 
     const CUtensorMap& A = side == 0 ? maps.a[0] : maps.a[2];
     const CUtensorMap& A2 = side == 0 ? maps.a[1] : maps.a[3];
     const CUtensorMap& B = maps.b[bsel];
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    if (job.pdl && sp) {  // inside the sweep loop: a programmatic dependent of the launch before it
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+    }
     if (kind == 0 && job.tabmode == 2)
-        bq_tc_half_kernel<0, 2><<<grid, kThreads, smem, st>>>(A, A2, B, job, side, s, sp, decide, fields_out, err);
-    else if (kind == 0 && job.tabmode == 1)
-        bq_tc_half_kernel<0, 1><<<grid, kThreads, smem, st>>>(A, A2, B, job, side, s, sp, decide, fields_out, err);
-    else if (kind == 0)
-        bq_tc_half_kernel<0, 0><<<grid, kThreads, smem, st>>>(A, A2, B, job, side, s, sp, decide, fields_out, err);
-    else
-        bq_tc_half_kernel<1, 0><<<grid, kThreads, smem, st>>>(A, A2, B, job, side, s, sp, decide, fields_out, err);
-    return cudaGetLastError();
+        return cudaLaunchKernelEx(&cfg, bq_tc_half_kernel<0, 2>, A, A2, B, job, side, s, sp, decide, fields_out, err);
+    if (kind == 0 && job.tabmode == 1)
+        return cudaLaunchKernelEx(&cfg, bq_tc_half_kernel<0, 1>, A, A2, B, job, side, s, sp, decide, fields_out, err);
+    if (kind == 0)
+        return cudaLaunchKernelEx(&cfg, bq_tc_half_kernel<0, 0>, A, A2, B, job, side, s, sp, decide, fields_out, err);
+    return cudaLaunchKernelEx(&cfg, bq_tc_half_kernel<1, 0>, A, A2, B, job, side, s, sp, decide, fields_out, err);
+}
+
+bool bq_tc_fills_device(int n, int Rpad, int kind)
+{
+    const int nrp = (((n + TBM - 1) / TBM) + 1) / 2;
+    return nrp * (Rpad / TBN) >= tc_active_clusters(kind);
 }
 
 int bq_tc_clusters(int n, int Rpad, int kind, bool split)

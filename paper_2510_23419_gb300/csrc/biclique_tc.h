@@ -33,5 +33,8 @@ cudaError_t bq_launch_tc_half(const BqTcMaps& maps, int bsel, const BqJob& job, 
 // CTA pairs a half-sweep launch of an n x n biclique with Rpad replicas occupies
 // (kind 0 e4m3, 1 split BF16; split: the last round's tiles halved).
 int bq_tc_clusters(int n, int Rpad, int kind, bool split);
+// Whether a half-sweep launch of an n x n biclique with Rpad replicas has at
+// least one 256-replica tile for every CTA pair that fits on the device.
+bool bq_tc_fills_device(int n, int Rpad, int kind);
 
 }  // namespace pb

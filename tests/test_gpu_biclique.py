@@ -223,6 +223,41 @@ def test_tensor_full_size_sampled(pb, orc):
         assert abs(g["best_E"][r] - e) <= 1e-9 * abs(e)
 
 
+@pytest.mark.parametrize("stop", [False, True])
+def test_tensor_chained_launches_equal_cudacore(pb, stop):
+    """n = 4096 with 1280 replicas: 80 tiles of 256 replicas, at least one per CTA pair, so the
+    tensor form chains its sweep loop's launches as programmatic dependents.  +-1 couplings:
+    its trajectories equal the FP32 CUDA-core form's bit for bit (both exact), with and
+    without the stop rule (a target about half the replicas reach)."""
+    n, R, S = 4096, 1280, 6
+    J = pb.pb_generate_biclique(n, pb.PB_DIST_PM1, 61)
+    inst = pb.pb_create_instance(pb.PB_TOPO_BICLIQUE, J, None, n=n)
+    sc = pb.make_schedule(pb.PB_SCHED_LINEAR, S, 0.35, 3.5)
+    try:
+        out = {}
+        for form in (pb.PB_FORM_CUDACORE, pb.PB_FORM_TENSOR):
+            target = float("nan")
+            if stop:
+                run = pb.pb_anneal(inst, sc, R, 63, pb.make_opts(pb.PB_FORM_CUDACORE))
+                target = float(np.median(pb.pb_energy(run, R)[1]))
+                pb.pb_run_destroy(run)
+            opts = pb.make_opts(form, target, pb.PB_FLAG_STOP_AT_TARGET) if stop else pb.make_opts(form)
+            run = pb.pb_anneal(inst, sc, R, 63, opts)
+            try:
+                fe, be, bs = pb.pb_energy(run, R)
+                out[form] = dict(fe=fe, be=be, bs=bs, fs=pb.pb_final_states(run, R, 2 * n),
+                                 bst=pb.pb_best_states(run, R, 2 * n), ts=pb.pb_target_sweeps(run, R))
+            finally:
+                pb.pb_run_destroy(run)
+    finally:
+        pb.pb_instance_destroy(inst)
+    a, b = out[pb.PB_FORM_CUDACORE], out[pb.PB_FORM_TENSOR]
+    for k in ("fe", "be", "bs", "fs", "bst", "ts"):
+        assert np.array_equal(a[k], b[k]), k
+    if stop:
+        assert 0 < (a["ts"] >= 0).sum() < R
+
+
 def test_tensor_largest_biclique(pb):
     """n = 16384 per side, the largest biclique the library takes, on tensor cores with
     300 replicas (a ragged replica tile): a ferromagnet (J = +1) at beta = 2 from random
