@@ -395,9 +395,10 @@ __device__ void ea_tile(const EaJob& job, int tile, unsigned char* smem)
     __syncthreads();
 }
 
-// One persistent kernel per coupling type: a kernel holding both types' tiles
-// gets one register allocation for all of them, and the FP32 tiles' pressure
-// then costs the +-1 tiles spill traffic.  The tile code comes with the work
+// One persistent kernel per coupling type in a batch (for FP32, one of two
+// variants, EaKernel): a kernel holding both types' tiles gets one register
+// allocation for all of them, and the FP32 tiles' pressure then costs the +-1
+// tiles spill traffic.  The tile code comes with the work
 // item (a branch on the job's own fields also led the compiler to spill).
 // Every CTA lets a programmatically dependent launch (the other type's kernel
 // of the same batch) start at once, so that kernel's CTAs take the SMs this

@@ -45,7 +45,6 @@ enum EaTilePath : int32_t {
     kEaPathFast16 = 2,         // L = 16, WT = 4
     kEaPathFast8 = 3,          // L = 8, WT = 16
     kEaPathGeneric = 4,        // any other even L <= 32
-    kEaPathGen24 = 5,          // (unused: L = 24, WT = 1 takes the compile-time tile kEaPathFast24)
     kEaPathGen12 = 6,          // generic tile with compile-time L = 12, WT = 4 (+-1 kernel; FP32: generic)
     kEaPathFast24 = 7,         // compile-time tile L = 24, WT = 1 (576 of the CTA's threads hold sites)
 };
