@@ -265,15 +265,20 @@ __global__ void __launch_bounds__(256) bq_sweep_end_kernel(BqJob job, int s_arg,
         // then added in the fixed order k = 0..7
         const int k = threadIdx.x >> 5, r = r0 + (threadIdx.x & 31);
         const int rows = 2 * job.nblk;
+        // side 0's rows hold -h.a and stay zero without a field: start at side 1's
+        // rows then, when nblk is a multiple of kSub (always in the tensor form), so
+        // that warp k adds the same side-1 rows in the same order, after the same
+        // zeros: the same sums
+        const int first = (job.inst.has_h || job.nblk % kSub) ? 0 : job.nblk;
         if (pm1) {
             const int32_t* p = static_cast<const int32_t*>(job.part);
             int32_t E = 0;
-            for (int b = k; b < rows; b += kSub) E += p[(size_t)b * job.Rpad + r];
+            for (int b = first + k; b < rows; b += kSub) E += p[(size_t)b * job.Rpad + r];
             s_pi[k][threadIdx.x & 31] = E;
         } else {
             const float* p = static_cast<const float*>(job.part);
             float E = 0.0f;
-            for (int b = k; b < rows; b += kSub) E += p[(size_t)b * job.Rpad + r];
+            for (int b = first + k; b < rows; b += kSub) E += p[(size_t)b * job.Rpad + r];
             s_pf[k][threadIdx.x & 31] = E;
         }
     }
