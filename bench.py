@@ -170,6 +170,19 @@ def oracle_sample(sweeps: int):
     return upd, dt
 
 
+def oracle_config1():
+    """The CPU oracle on the whole small-cube run shape (EA L = 6, +-1 bonds from seed 1,
+    h = 0, linear beta 0.1 -> 3.0, 1000 sweeps, 64 replicas, seed 42), single-threaded,
+    as it stands; returns (updates, seconds)."""
+    from oracle import oracle as orc
+    L, R, S = 6, 64, 1000
+    J = orc.gen_ea(L, orc.DIST_PM1, 1)
+    betas = orc.schedule(orc.SCHED_LINEAR, 0.1, 3.0, S)
+    t0 = time.perf_counter()
+    orc.anneal_ea(L, J, None, betas, R, 42)
+    return L ** 3 * R * S, time.perf_counter() - t0
+
+
 def _oracle_replica(task):
     """One host core's share of the all-cores CPU baseline: replica r of each job
     for the first `sweeps` sweeps (the oracle as it stands, single-threaded)."""
@@ -1058,6 +1071,10 @@ def main():
         line["cpu_baseline"]["all_cores"] = {
             "value": ua / wa, "unit": UNIT, "cores": cores, "kind": "oracle, one process per core",
             "sample": f"replicas 0..{cores - 1} (one per process) of each of the 4 jobs, first 3000 sweeps"}
+        uc, tc = oracle_config1()
+        line["cpu_baseline"]["config1"] = {
+            "value": uc / tc, "unit": UNIT, "seconds": tc, "cores": 1, "kind": "oracle",
+            "sample": "the whole small-cube run (EA L = 6, 64 replicas, 1000 sweeps), as config1 times it on the GPU"}
     for i in insts:
         pb.pb_instance_destroy(i)
     if rank == 0:
